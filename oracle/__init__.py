@@ -1,0 +1,44 @@
+"""Oracle: a plain, slow, FP64 CPU restatement of the GMRES(s)-smoothed multigrid
+inversion of the complex-stretched-grid (CSG) Helmholtz preconditioner and of the
+outer flexible GMRES solve (Reps, Vanroose, bin Zubair, arXiv:1012.5379).
+
+THIS PACKAGE IS TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  The
+product path (``paper_1012_5379_gb300``) never imports, links or runs anything here,
+and this package imports nothing from the product: the two share no code.
+
+Every function cites the passage of the paper it follows (section, equation, lemma,
+table).  Where the paper is silent or garbled, the reading taken is stated in the
+docstring.  Arithmetic is complex128 throughout; NumPy array operations and a few
+LAPACK calls (``numpy.linalg.solve`` / ``lstsq``) serve as library primitives.
+
+Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
+
+* ``spacings`` / ``coefficients_1d`` / ``apply_operator``: pinned (quadrature-built
+  node coordinates + Lagrange second-difference matrix, closed-form Dirichlet
+  eigenpairs, e^{-2i theta} rotation identity, exactness on complex quadratics).
+* ``restrict_fw`` / ``prolong``: pinned (P = 2^d R^T, exactness on linear fields).
+* ``gmres_sweep``: pinned (brute-force Krylov least squares, residual monotonicity).
+* ``coarse_solve``: pinned (independently assembled matrix times solution).
+* ``vcycle``: pinned as a stationary iteration converging to the direct solve and by
+  the paper's contraction bound (soft); the V-cycle output itself, cycle by cycle,
+  has no printed value to compare with: beyond those properties its parity is
+  unpinned.
+* ``fgmres``: pinned (sparse direct solve, manufactured solution, paper Table 2
+  iteration counts as a soft band).
+"""
+from .helmholtz import (  # noqa: F401
+    Level,
+    build_hierarchy,
+    coarse_solve,
+    coefficients_1d,
+    complex_map,
+    fgmres,
+    gmres_sweep,
+    level_sizes,
+    prolong,
+    restrict_fw,
+    spacings,
+    apply_operator,
+    vcycle,
+)

@@ -1,0 +1,70 @@
+"""Soft pins of the whole oracle (grid, operator, GMRES(s) smoother, V-cycle, FGMRES)
+against the iteration counts the paper prints (tests/golden/paper_tables.json).
+
+The paper runs on the unit square of interior points with an ECS layer of n/4
+intervals on each side (Sec. 4.4), kh = 0.625, a point source in the middle.  On the
+normalised box [0, 1] this is N + 1 = 1.5 n intervals, a layer fraction of 1/6 and a
+wavenumber 1.5 k.  Counts must fall within +-30% of the printed ones.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1012_5379_gb300 import inputs as I
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+TG = np.pi / 6
+
+
+def paper_levels(k, nint, tb):
+    n = int(nint * 1.5) - 1
+    return O.build_hierarchy(2, n, tb, TG, 1.0 / 6.0, k=1.5 * k), I.point_source(2, n)
+
+
+@pytest.mark.parametrize("col", [0, 1])
+@pytest.mark.parametrize("cyc", ["1,0", "1,1", "2,1"])
+def test_table2_fgmres_iterations(cyc, col):
+    t2 = GOLD["table2"]
+    k, nint = t2["k"][col], t2["interior_intervals"][col]
+    nu1, nu2 = map(int, cyc.split(","))
+    levels, b = paper_levels(k, nint, np.deg2rad(10.3132))
+    _, info = O.fgmres(levels[0].apply_h, lambda v: O.vcycle(levels, v, nu1, nu2, 3), b, tol=1e-7)
+    want = t2["iters"][cyc][col]
+    assert info.converged
+    assert 0.7 * want <= info.iters <= 1.3 * want, (info.iters, want)
+
+
+@pytest.mark.parametrize("col,nint", [(0, 32), (1, 64)])
+@pytest.mark.parametrize("key", ["1,0,3", "1,1,2", "1,1,3", "1,1,4", "2,1,3"])
+def test_table1_vcycle_counts(key, col, nint):
+    t1 = GOLD["table1"]
+    nu1, nu2, s = map(int, key.split(","))
+    levels, b = paper_levels(t1["k"][col], nint, 0.18)
+    x = np.zeros_like(b)
+    r0 = np.linalg.norm(b)
+    cycles = None
+    for it in range(1, 40):
+        x = x + O.vcycle(levels, b - levels[0].apply(x), nu1, nu2, s)
+        if np.linalg.norm(b - levels[0].apply(x)) / r0 < 1e-7:
+            cycles = it
+            break
+    want = t1["cycles"][key][col]
+    assert cycles is not None and 0.7 * want <= cycles <= 1.3 * want, (cycles, want)
+
+
+@pytest.mark.parametrize("cyc", ["1,0", "1,1", "2,1"])
+def test_average_vcycle_rate_bound(cyc):
+    """Averaged rate over successive cycles at or below the printed bound (soft:
+    +10% slack)."""
+    nu1, nu2 = map(int, cyc.split(","))
+    levels, b = paper_levels(40, 64, 0.18)
+    x = np.zeros_like(b)
+    res = [np.linalg.norm(b)]
+    for _ in range(8):
+        x = x + O.vcycle(levels, b - levels[0].apply(x), nu1, nu2, 3)
+        res.append(np.linalg.norm(b - levels[0].apply(x)))
+    rate = (res[-1] / res[0]) ** (1 / 8)
+    assert rate <= 1.1 * GOLD["vcycle_rate"]["bound"][cyc], rate
