@@ -1,0 +1,156 @@
+/*
+ * helm.h -- C ABI of the GB300 (sm_103a) solver for the Helmholtz equation with
+ * exterior-complex-scaled (ECS) absorbing layers, preconditioned by the complex
+ * stretched grid (CSG) operator inverted with one GMRES(s)-smoothed multigrid
+ * V-cycle, inside an outer FP64 flexible GMRES.
+ *
+ * Method: B. Reps, W. Vanroose, H. bin Zubair, "GMRES-based multigrid for the complex
+ * scaled preconditioner for the indefinite Helmholtz equation", arXiv:1012.5379.
+ *   - problem  H u = -(Laplacian + phi) u = chi                (Sec. 1, Eq. helm)
+ *   - grids    interior spacing h e^{i theta_beta}, layer spacing h e^{i theta_gamma}
+ *              (Sec. 2, Eq. csggrid; layers on both sides per Remark 2.2)
+ *   - operator three-point non-uniform second difference per axis, Kronecker sum in
+ *              d dimensions, M = L^CSG - phi, H = L^ECS - phi   (Sec. 2, Eq. csg_dis,
+ *              Lemma 2.1)
+ *   - smoother GMRES(s) on every level, V(nu1, nu2) cycle, rediscretised coarse
+ *              operators (Sec. 3.1, Prop. 3.1)
+ *   - outer    flexible GMRES, one V-cycle per iteration from a zero guess (Sec. 5)
+ *
+ * Conventions for every entry point:
+ *   - Complex vectors are interleaved (re, im) arrays of n^dim complex numbers in
+ *     natural order: x fastest, then y, then z (C order of an (n,)*dim array).
+ *   - Device pointers must be allocated on the current CUDA device; the caller owns
+ *     them.  Host pointers are plain (pinned or pageable) host memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  All device work is enqueued on it.
+ *   - Return value: HELM_OK (0) or a negative HELM_E* code; helm_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.  No C++
+ *     exception crosses this boundary.
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HELM_OK 0
+#define HELM_EINVAL -1   /* invalid argument (sizes, angles, tolerance, NULL pointer) */
+#define HELM_ENOMEM -2   /* device allocation failed or serving budget exceeded */
+#define HELM_ENOCONV -3  /* maxit reached before tol; x holds the last iterate */
+#define HELM_ENUMERIC -4 /* NaN/Inf in a residual norm */
+#define HELM_ETIMEOUT -5 /* a bounded wait ran out (serving poll) */
+#define HELM_ECUDA -6    /* CUDA runtime error */
+#define HELM_EAGAIN -7   /* serving: request not finished yet */
+
+/* preconditioner precision */
+#define HELM_C64 1   /* complex FP32 storage and arithmetic (FP32 accumulation) */
+#define HELM_C128 2  /* complex FP64 */
+
+typedef struct helm_handle helm_handle;
+
+/* Grid: the unit interval per axis, n interior nodes, spacing h = 1/(n+1); u = 0 on
+ * the outer edge of the layers.  n must be >= 3 and coarsening proceeds while n+1 is
+ * even and n > coarsest_n (so n = 2^L - 1 gives L-1 levels down to 3).
+ * ecs_frac: layer width on each side as a fraction of the box, 0 < ecs_frac < 0.5.
+ * theta_gamma: ECS layer angle in radians, 0 <= theta_gamma < pi/2. */
+typedef struct {
+  int dim;            /* 2 or 3 */
+  int n;              /* interior nodes per axis (same on every axis) */
+  double ecs_frac;    /* default 0.125 */
+  double theta_gamma; /* default 0.5 */
+} helm_grid;
+
+/* Options.  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  int nu1;          /* pre-smoothing GMRES(s) sweeps per level      [1] */
+  int nu2;          /* post-smoothing sweeps per level               [1] */
+  int s;            /* GMRES steps per sweep, 1..4                   [3] */
+  int coarsest_n;   /* stop coarsening at this size or below         [3] */
+  int precond_prec; /* HELM_C64 or HELM_C128                         [HELM_C64] */
+  int restart;      /* outer FGMRES restart length m, 0 = none       [0] */
+  int maxit;        /* max preconditioner applications per solve     [400] */
+} helm_opts;
+
+typedef struct {
+  int iters;           /* preconditioner applications (outer iterations) */
+  int restarts;        /* completed FGMRES cycles */
+  double rel_res_est;  /* Arnoldi estimate |g_{j+1}| / ||b|| at exit */
+  double rel_res_true; /* ||b - H x|| / ||b|| recomputed in FP64 at exit */
+  int status;          /* HELM_OK, HELM_ENOCONV or HELM_ENUMERIC */
+} helm_info;
+
+/* Build the CSG hierarchy (Sec. 3.1, Prop. 3.1) and the ECS operator H for one
+ * problem, and allocate its workspace on the current device.
+ *   phi:  device pointer to n^dim floats holding phi = k(x)^2 at the interior nodes
+ *         (natural order), or NULL for a constant wavenumber `k` (phi = k^2).  The
+ *         field is copied; coarse levels sample it at their nodes.
+ *   theta_beta: CSG interior angle in radians, 0 <= theta_beta < pi/2 (Sec. 2).
+ *   opts may be NULL (all defaults).
+ * Errors: HELM_EINVAL (dim, n, angles, ecs_frac, opts out of range), HELM_ENOMEM,
+ * HELM_ECUDA.  The call synchronises `stream` before returning. */
+int helm_setup(const helm_grid* grid, const float* phi, double k, double theta_beta,
+               const helm_opts* opts, void* stream, helm_handle** out);
+
+/* Release a handle and all device memory it owns (NULL is a no-op). */
+void helm_destroy(helm_handle* h);
+
+/* z ~ (M^CSG)^{-1} r by one V(nu1, nu2) cycle from a zero initial guess (Sec. 3.2,
+ * Sec. 5).  r and z are device arrays of n^dim complex numbers in precision `prec`
+ * (HELM_C64: float pairs, HELM_C128: double pairs), independent of the handle's
+ * internal precision (converted on the way in and out).  Asynchronous on `stream`. */
+int helm_precond_apply(helm_handle* h, const void* r, void* z, int prec, void* stream);
+
+/* w = M^CSG v (prec = HELM_C64/HELM_C128, which = 0) or w = H v (which = 1) on the
+ * finest level (Sec. 2, Eq. csg_dis).  Asynchronous on `stream`.  Exposed for
+ * verification of the stencil. */
+int helm_apply_operator(helm_handle* h, int which, const void* v, void* w, int prec, void* stream);
+
+/* Solve H x = b with right-preconditioned FGMRES(m) (Sec. 5) to
+ * ||b - H x|| / ||b|| <= tol, recomputed in FP64.
+ *   b: device, n^dim complex128 (read only).
+ *   x: device, n^dim complex128; on entry the initial guess, on exit the solution.
+ *   info: filled on return (may be NULL).
+ * Blocks the calling thread until the solve finishes (it reads convergence flags
+ * from the device each iteration).  Returns HELM_OK, HELM_ENOCONV (maxit reached,
+ * x holds the last iterate), HELM_ENUMERIC, HELM_EINVAL or HELM_ECUDA. */
+int helm_solve(helm_handle* h, const double* b, double* x, double tol, helm_info* info,
+               void* stream);
+
+/* As helm_solve, but b and x are HOST arrays: b is copied to the device, the solve
+ * runs from a zero initial guess, and the solution is copied back into x. */
+int helm_solve_host(helm_handle* h, const double* b_host, double* x_host, double tol,
+                    helm_info* info, void* stream);
+
+/* Solve `count` independent problems together: every V-cycle level is one launch
+ * over all problems that have that level, and the outer FGMRES steps of all
+ * problems share launches.  Problems may differ in n, k, phi and theta_beta, but
+ * must share dim, precond_prec, nu1, nu2 and s, and have n + 1 a power of two.  Each
+ * problem's result is bitwise the same as when it is solved alone (reductions are
+ * per problem in a fixed order).
+ *   b[i], x[i]: device arrays as in helm_solve for handle hs[i].
+ *   infos: array of `count` (may be NULL).
+ * Returns HELM_OK if every problem converged, HELM_ENOCONV / HELM_ENUMERIC if at
+ * least one did not (see infos[i].status), or an argument/CUDA error. */
+int helm_batch_solve(helm_handle* const* hs, int count, const double* const* b,
+                     double* const* x, double tol, helm_info* infos, void* stream);
+
+/* Bytes of device memory the handle holds. */
+int helm_workspace_bytes(const helm_handle* h, size_t* bytes);
+
+/* Levels of the hierarchy and their sizes (sizes may be NULL). */
+int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes);
+
+/* Thread-local text of the last error on the calling thread ("" if none). */
+const char* helm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

@@ -1,0 +1,158 @@
+// extern "C" boundary of libhelm.so (include/helm.h).  Every entry point validates
+// its arguments, catches C++ exceptions and reports failures through a status code
+// and a thread-local message.
+#include <cuda_runtime.h>
+
+#include <exception>
+#include <new>
+#include <vector>
+#include <string>
+
+#include "../../include/helm.h"
+#include "engine.h"
+
+namespace helm {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace helm
+
+using helm::Handle;
+
+#define HELM_GUARD(...)                                   \
+  try {                                                   \
+    helm::set_error("");                                  \
+    __VA_ARGS__                                           \
+  } catch (const std::bad_alloc&) {                       \
+    helm::set_error("host allocation failed");            \
+    return HELM_ENOMEM;                                   \
+  } catch (const std::exception& e) {                     \
+    helm::set_error(e.what());                            \
+    return HELM_ECUDA;                                    \
+  } catch (...) {                                         \
+    helm::set_error("unknown exception");                 \
+    return HELM_ECUDA;                                    \
+  }
+
+struct helm_handle {
+  Handle* h;
+};
+
+extern "C" {
+
+int helm_setup(const helm_grid* grid, const float* phi, double k, double theta_beta, const helm_opts* opts,
+               void* stream, helm_handle** out) {
+  HELM_GUARD({
+    if (!out) { helm::set_error("out must not be NULL"); return HELM_EINVAL; }
+    *out = nullptr;
+    Handle* h = nullptr;
+    int rc = helm::setup_handle(grid, phi, k, theta_beta, opts, (cudaStream_t)stream, &h);
+    if (rc != HELM_OK) return rc;
+    *out = new helm_handle{h};
+    return HELM_OK;
+  })
+}
+
+void helm_destroy(helm_handle* h) {
+  if (!h) return;
+  try {
+    delete h->h;
+  } catch (...) {
+  }
+  delete h;
+}
+
+int helm_precond_apply(helm_handle* h, const void* r, void* z, int prec, void* stream) {
+  HELM_GUARD({
+    if (!h) { helm::set_error("NULL handle"); return HELM_EINVAL; }
+    return helm::precond_apply(h->h, r, z, prec, (cudaStream_t)stream);
+  })
+}
+
+int helm_apply_operator(helm_handle* h, int which, const void* v, void* w, int prec, void* stream) {
+  HELM_GUARD({
+    if (!h) { helm::set_error("NULL handle"); return HELM_EINVAL; }
+    if (which != 0 && which != 1) { helm::set_error("which must be 0 (M) or 1 (H)"); return HELM_EINVAL; }
+    return helm::apply_operator(h->h, which, v, w, prec, (cudaStream_t)stream);
+  })
+}
+
+int helm_solve(helm_handle* h, const double* b, double* x, double tol, helm_info* info, void* stream) {
+  HELM_GUARD({
+    if (!h) { helm::set_error("NULL handle"); return HELM_EINVAL; }
+    Handle* hs[1] = {h->h};
+    const double* bs[1] = {b};
+    double* xs[1] = {x};
+    return helm::solve_group(hs, 1, bs, xs, tol, info, (cudaStream_t)stream);
+  })
+}
+
+int helm_solve_host(helm_handle* h, const double* b_host, double* x_host, double tol, helm_info* info,
+                    void* stream) {
+  HELM_GUARD({
+    if (!h || !b_host || !x_host) { helm::set_error("NULL argument"); return HELM_EINVAL; }
+    Handle* hh = h->h;
+    const size_t npts = hh->dim == 3 ? (size_t)hh->n * hh->n * hh->n : (size_t)hh->n * hh->n;
+    const size_t bytes = npts * 2 * sizeof(double);
+    cudaStream_t st = (cudaStream_t)stream;
+    double *db = nullptr, *dx = nullptr;
+    if (cudaMalloc(&db, bytes) != cudaSuccess || cudaMalloc(&dx, bytes) != cudaSuccess) {
+      cudaFree(db);
+      helm::set_error("device allocation for host solve failed");
+      return HELM_ENOMEM;
+    }
+    int rc = HELM_OK;
+    if (cudaMemcpyAsync(db, b_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(dx, 0, bytes, st) != cudaSuccess) {
+      helm::set_error("host to device copy failed");
+      rc = HELM_ECUDA;
+    }
+    if (rc == HELM_OK) {
+      Handle* hs[1] = {hh};
+      const double* bs[1] = {db};
+      double* xs[1] = {dx};
+      rc = helm::solve_group(hs, 1, bs, xs, tol, info, st);
+      if (rc == HELM_OK || rc == HELM_ENOCONV || rc == HELM_ENUMERIC) {
+        if (cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+          helm::set_error("device to host copy failed");
+          rc = HELM_ECUDA;
+        }
+      }
+    }
+    cudaFree(db);
+    cudaFree(dx);
+    return rc;
+  })
+}
+
+int helm_batch_solve(helm_handle* const* hs, int count, const double* const* b, double* const* x, double tol,
+                     helm_info* infos, void* stream) {
+  HELM_GUARD({
+    if (!hs || count <= 0) { helm::set_error("empty batch"); return HELM_EINVAL; }
+    std::vector<Handle*> inner(count);
+    for (int i = 0; i < count; ++i) {
+      if (!hs[i]) { helm::set_error("NULL handle in batch"); return HELM_EINVAL; }
+      inner[i] = hs[i]->h;
+    }
+    return helm::solve_group(inner.data(), count, b, x, tol, infos, (cudaStream_t)stream);
+  })
+}
+
+int helm_workspace_bytes(const helm_handle* h, size_t* bytes) {
+  if (!h || !bytes) { helm::set_error("NULL argument"); return HELM_EINVAL; }
+  *bytes = h->h->bytes;
+  return HELM_OK;
+}
+
+int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes) {
+  if (!h || !nlevels) { helm::set_error("NULL argument"); return HELM_EINVAL; }
+  const auto& lev = h->h->lev;
+  *nlevels = (int)lev.size();
+  if (sizes)
+    for (int i = 0; i < (int)lev.size() && i < max_sizes; ++i) sizes[i] = lev[i].n;
+  return HELM_OK;
+}
+
+const char* helm_last_error(void) { return helm::g_last_error.c_str(); }
+
+}  // extern "C"

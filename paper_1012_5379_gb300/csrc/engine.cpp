@@ -1,0 +1,634 @@
+// Host engine: builds the CSG hierarchy of a problem (Sec. 3.1, Prop. 3.1), groups
+// problems for batched launches, and drives the V-cycle (Sec. 3.1-3.2) and the outer
+// flexible GMRES (Sec. 5).
+#include "engine.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <sstream>
+
+#include "geometry.h"
+
+namespace helm {
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      std::ostringstream os_;                                                            \
+      os_ << #expr << ": " << cudaGetErrorString(e_) << " (" << __FILE__ << ":" << __LINE__ << ")"; \
+      set_error(os_.str());                                                              \
+      return e_ == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA;                 \
+    }                                                                                    \
+  } while (0)
+
+static size_t elem_bytes(int prec) { return prec == HELM_C128 ? sizeof(double2) : sizeof(float2); }
+
+
+// Sizes of the tiles of the marching kernels: 2D warps march `rows` rows, chosen to
+// give about four CTAs per SM on a single problem; 3D CTAs march 16 planes.
+static TileCfg default_tiles(int dim, int P) {
+  TileCfg c;
+  if (dim == 2) {
+    int rows = (int)((long long)P * P / (32LL * WARPS2 * 608));
+    rows = std::max(2, std::min(32, rows & ~1));
+    c.rows = rows;
+  } else {
+    c.rows = P >= 128 ? 16 : 8;
+  }
+  return c;
+}
+
+static int coarse_threshold(int dim) { return dim == 2 ? 31 : 7; }
+
+// Tiles of the finest tile configuration (2 rows / planes per march).
+static int max_tiles(int dim, int P) {
+  TileCfg c;
+  c.rows = 2;
+  return tiles_per_problem(dim, P, c);
+}
+
+template <typename T>
+static int dev_alloc(Handle* h, T** p, size_t bytes) {
+  void* q = nullptr;
+  CUDA_TRY(cudaMalloc(&q, std::max<size_t>(bytes, 16)));
+  h->allocs.push_back(q);
+  h->bytes += bytes;
+  *p = reinterpret_cast<T*>(q);
+  return HELM_OK;
+}
+
+#define TRY(expr)                 \
+  do {                            \
+    int r_ = (expr);              \
+    if (r_ != HELM_OK) return r_; \
+  } while (0)
+
+int setup_handle(const helm_grid* grid, const float* phi, double k, double theta_beta, const helm_opts* opts,
+                 cudaStream_t st, Handle** out) {
+  if (!grid || !out) { set_error("grid and out must not be NULL"); return HELM_EINVAL; }
+  std::unique_ptr<Handle> h(new Handle());
+  h->dim = grid->dim;
+  h->n = grid->n;
+  h->ecs = grid->ecs_frac > 0 ? grid->ecs_frac : 0.125;
+  h->theta_gamma = grid->theta_gamma;
+  h->theta_beta = theta_beta;
+  h->k = k;
+  h->has_phi = phi != nullptr;
+  helm_opts o{};
+  if (opts) o = *opts;
+  h->nu1 = o.nu1 > 0 ? o.nu1 : (opts && o.nu1 == 0 && o.nu2 > 0 ? 0 : 1);
+  h->nu2 = o.nu2 > 0 ? o.nu2 : (opts && o.nu2 == 0 && o.nu1 > 0 ? 0 : 1);
+  h->s = o.s > 0 ? o.s : 3;
+  h->coarsest = o.coarsest_n > 0 ? o.coarsest_n : 3;
+  h->prec = o.precond_prec ? o.precond_prec : HELM_C64;
+  h->restart = o.restart > 0 ? o.restart : 0;
+  h->maxit = o.maxit > 0 ? o.maxit : 400;
+  if (h->dim != 2 && h->dim != 3) { set_error("dim must be 2 or 3"); return HELM_EINVAL; }
+  if (h->n < 1 || h->n > (h->dim == 2 ? 32767 : 2047)) { set_error("n out of range"); return HELM_EINVAL; }
+  if (!(h->ecs > 0 && h->ecs < 0.5)) { set_error("ecs_frac must be in (0, 0.5)"); return HELM_EINVAL; }
+  if (!(h->theta_gamma >= 0 && h->theta_gamma < M_PI / 2)) { set_error("theta_gamma must be in [0, pi/2)"); return HELM_EINVAL; }
+  if (!(theta_beta >= 0 && theta_beta < M_PI / 2)) { set_error("theta_beta must be in [0, pi/2)"); return HELM_EINVAL; }
+  if (h->s > SMAX) { set_error("s must be in 1..4"); return HELM_EINVAL; }
+  if (h->nu1 > 8 || h->nu2 > 8) { set_error("nu1, nu2 must be <= 8"); return HELM_EINVAL; }
+  if (h->prec != HELM_C64 && h->prec != HELM_C128) { set_error("precond_prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
+  if (!phi && !std::isfinite(k)) { set_error("k must be finite"); return HELM_EINVAL; }
+  const std::vector<int> sizes = level_sizes(h->n, h->coarsest);
+  const int nlev = (int)sizes.size();
+  const int cm = h->dim == 3 ? sizes.back() * sizes.back() * sizes.back() : sizes.back() * sizes.back();
+  if (cm > 128) {
+    set_error("coarsest grid has more than 128 unknowns: n+1 must be divisible by a larger power of two, or lower coarsest_n");
+    return HELM_EINVAL;
+  }
+  h->m = h->restart > 0 ? std::min(h->restart, h->maxit) : h->maxit;
+  const size_t eb = elem_bytes(h->prec);
+
+  // ------------------------------------------------ levels
+  h->lev.resize(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    HostLevel& L = h->lev[l];
+    L.n = sizes[l];
+    L.P = L.n + 1;
+    L.np = h->dim == 3 ? (size_t)L.P * L.P * L.P : (size_t)L.P * L.P;
+    const TileCfg cfg = default_tiles(h->dim, L.P);
+    if (l == 0) h->cfg = cfg;
+    L.ntiles = tiles_per_problem(h->dim, L.P, h->cfg);
+    L.nflat = (int)std::max<size_t>(1, std::min<size_t>(1024, (L.np + 1023) / 1024));
+    TRY(dev_alloc(h.get(), &L.b, L.np * eb));
+    TRY(dev_alloc(h.get(), &L.xa, L.np * eb));
+    TRY(dev_alloc(h.get(), &L.xb, L.np * eb));
+    TRY(dev_alloc(h.get(), &L.r0, L.np * eb));
+    for (int j = 0; j < h->s; ++j) TRY(dev_alloc(h.get(), &L.p[j], L.np * eb));
+    for (void* v : {L.b, L.xa, L.xb, L.r0}) CUDA_TRY(cudaMemsetAsync(v, 0, L.np * eb, st));
+    for (int j = 0; j < h->s; ++j) CUDA_TRY(cudaMemsetAsync(L.p[j], 0, L.np * eb, st));
+    TRY(dev_alloc(h.get(), &L.sc, sizeof(SweepScalars)));
+    CUDA_TRY(cudaMemsetAsync(L.sc, 0, sizeof(SweepScalars), st));
+    // partial-sum slots for the largest tile count any group configuration uses
+    const size_t nparts = std::max<size_t>(std::max(max_tiles(h->dim, L.P), L.nflat), 1);
+    TRY(dev_alloc(h.get(), &L.part, nparts * NPART * sizeof(double)));
+    // coefficients of M on this level (rediscretisation with spacing 2^l h)
+    std::vector<cplx> a, d, c;
+    stencil_coefficients(grid_spacings(L.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
+    std::vector<double2> c64(3 * L.n);
+    for (int i = 0; i < L.n; ++i) {
+      c64[i] = make_double2(a[i].real(), a[i].imag());
+      c64[L.n + i] = make_double2(d[i].real(), d[i].imag());
+      c64[2 * L.n + i] = make_double2(c[i].real(), c[i].imag());
+    }
+    TRY(dev_alloc(h.get(), &L.coef64, 3 * L.n * sizeof(double2)));
+    CUDA_TRY(cudaMemcpyAsync(L.coef64, c64.data(), 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
+    TRY(dev_alloc(h.get(), &L.coef, 3 * L.n * eb));
+    if (h->prec == HELM_C128) {
+      CUDA_TRY(cudaMemcpyAsync(L.coef, c64.data(), 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
+    } else {
+      std::vector<float2> c32(3 * L.n);
+      for (int i = 0; i < 3 * L.n; ++i) c32[i] = make_float2((float)c64[i].x, (float)c64[i].y);
+      CUDA_TRY(cudaMemcpyAsync(L.coef, c32.data(), 3 * L.n * sizeof(float2), cudaMemcpyHostToDevice, st));
+    }
+    // phi sampled at this level's nodes (node x of level l is fine node (x+1) 2^l - 1)
+    if (phi) {
+      TRY(dev_alloc(h.get(), &L.phi, L.np * sizeof(float)));
+      scatter_phi(h->dim, L.n, 1 << l, h->n, phi, L.phi, st);
+      CUDA_TRY(cudaGetLastError());
+    } else {
+      L.phic = k * k;
+    }
+  }
+  // ------------------------------------------------ coarsest LU (FP64)
+  {
+    const HostLevel& Lc = h->lev.back();
+    std::vector<cplx> a, d, c;
+    stencil_coefficients(grid_spacings(Lc.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
+    std::vector<double> phic(cm, Lc.phic);
+    if (phi) {
+      std::vector<float> pad(Lc.np);
+      CUDA_TRY(cudaMemcpyAsync(pad.data(), Lc.phi, Lc.np * sizeof(float), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      for (int z = 0; z < (h->dim == 3 ? Lc.n : 1); ++z)
+        for (int y = 0; y < Lc.n; ++y)
+          for (int x = 0; x < Lc.n; ++x)
+            phic[(z * Lc.n + y) * Lc.n + x] = pad[((size_t)z * Lc.P + y) * Lc.P + x];
+    }
+    std::vector<cplx> A = dense_operator(h->dim, Lc.n, a, d, c, phic);
+    std::vector<int> perm;
+    if (!lu_factor(A, cm, perm)) { set_error("coarsest operator is singular"); return HELM_ENUMERIC; }
+    std::vector<double2> Ad(A.size());
+    for (size_t i = 0; i < A.size(); ++i) Ad[i] = make_double2(A[i].real(), A[i].imag());
+    h->lu_m = cm;
+    TRY(dev_alloc(h.get(), &h->lu, Ad.size() * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->piv, cm * sizeof(int)));
+    CUDA_TRY(cudaMemcpyAsync(h->lu, Ad.data(), Ad.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->piv, perm.data(), cm * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  // ------------------------------------------------ H and the outer storage
+  {
+    const HostLevel& L0 = h->lev[0];
+    std::vector<cplx> a, d, c;
+    stencil_coefficients(grid_spacings(h->n, h->ecs, h->theta_gamma, 0.0), a, d, c);
+    std::vector<double2> hc(3 * h->n);
+    for (int i = 0; i < h->n; ++i) {
+      hc[i] = make_double2(a[i].real(), a[i].imag());
+      hc[h->n + i] = make_double2(d[i].real(), d[i].imag());
+      hc[2 * h->n + i] = make_double2(c[i].real(), c[i].imag());
+    }
+    TRY(dev_alloc(h.get(), &h->hcoef, hc.size() * sizeof(double2)));
+    CUDA_TRY(cudaMemcpyAsync(h->hcoef, hc.data(), hc.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    h->vs = L0.np;
+    h->ntiles0 = L0.ntiles;
+    h->chunks = (int)std::max<size_t>(1, std::min<size_t>(256, (h->vs + 2047) / 2048));
+    const int m = h->m;
+    TRY(dev_alloc(h.get(), &h->bpad, h->vs * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->xpad, h->vs * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->w, h->vs * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->V, (size_t)(m + 1) * h->vs * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->Z, (size_t)m * h->vs * eb));
+    TRY(dev_alloc(h.get(), &h->Hm, (size_t)(m + 1) * m * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->g, (size_t)(m + 1) * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->cs, (size_t)(m + 1) * sizeof(double)));
+    TRY(dev_alloc(h.get(), &h->sn, (size_t)(m + 1) * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->y, (size_t)(m + 1) * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->hcol, (size_t)(m + 1) * sizeof(double2)));
+    TRY(dev_alloc(h.get(), &h->vscale, (size_t)(m + 1) * sizeof(double)));
+    const size_t op = std::max<size_t>(std::max<size_t>((size_t)max_tiles(h->dim, L0.P) * NPART,
+                                                        (size_t)h->chunks * NPART),
+                                       (size_t)h->chunks * 2 * (m + 1));
+    TRY(dev_alloc(h.get(), &h->opart, op * sizeof(double)));
+    TRY(dev_alloc(h.get(), &h->st, sizeof(OuterState)));
+    CUDA_TRY(cudaMemsetAsync(h->w, 0, h->vs * sizeof(double2), st));
+    CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(OuterState), st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  *out = h.release();
+  return HELM_OK;
+}
+
+// ------------------------------------------------------------------ groups
+template <typename C>
+static LevelDev<C> make_leveldev(const Handle& h, int l) {
+  const HostLevel& L = h.lev[l];
+  LevelDev<C> d;
+  std::memset(&d, 0, sizeof(d));
+  d.n = L.n;
+  d.P = L.P;
+  d.ntiles = L.ntiles;
+  d.s = h.s;
+  d.b = (C*)L.b;
+  d.xa = (C*)L.xa;
+  d.xb = (C*)L.xb;
+  d.r0 = (C*)L.r0;
+  for (int j = 0; j < SMAX; ++j) d.p[j] = (C*)L.p[j];
+  d.ca = (const C*)L.coef;
+  d.cd = (const C*)L.coef + L.n;
+  d.cc = (const C*)L.coef + 2 * L.n;
+  d.phi = L.phi;
+  d.phic = L.phic;
+  d.sc = L.sc;
+  d.part = L.part;
+  if (l + 1 < (int)h.lev.size()) {
+    const HostLevel& Lc = h.lev[l + 1];
+    d.nc = Lc.n;
+    d.Pc = Lc.P;
+    d.bc = (C*)Lc.b;
+    d.xcb = (const C*)Lc.xb;
+    d.scc = Lc.sc;
+  }
+  return d;
+}
+
+template <typename C>
+static OuterDev<C> make_outerdev(const Handle& h) {
+  OuterDev<C> o;
+  std::memset(&o, 0, sizeof(o));
+  o.n = h.n;
+  o.P = h.n + 1;
+  o.ntiles = h.ntiles0;
+  o.ca = h.hcoef;
+  o.cd = h.hcoef + h.n;
+  o.cc = h.hcoef + 2 * h.n;
+  o.phi = h.lev[0].phi;
+  o.phic = h.lev[0].phic;
+  o.bpad = h.bpad;
+  o.xpad = h.xpad;
+  o.w = h.w;
+  o.V = h.V;
+  o.Z = (C*)h.Z;
+  o.b0 = (C*)h.lev[0].b;
+  o.zout = (const C*)h.lev[0].xb;
+  o.s = h.s;
+  o.vs = h.vs;
+  o.Hm = h.Hm;
+  o.g = h.g;
+  o.cs = h.cs;
+  o.sn = h.sn;
+  o.y = h.y;
+  o.hcol = h.hcol;
+  o.vscale = h.vscale;
+  o.part = h.opart;
+  o.st = h.st;
+  o.sc0 = h.lev[0].sc;
+  return o;
+}
+
+template <typename C>
+struct Group {
+  int dim = 2, nu1 = 1, nu2 = 1, s = 3, Lmax = 0, tc = 0, nprob = 0;
+  TileCfg cfg{8};
+  std::vector<Handle*> hs;
+  struct Depth { int n = 0, cnt = 0, ntiles = 0, nflat = 0; LevelDev<C>* d = nullptr; };
+  std::vector<Depth> depth;      // t < tc
+  LevelDev<C>* dcoarse = nullptr;  // [prob][Lmax - tc]
+  int nlev_c = 0;
+  CoarseLU* dlu = nullptr;
+  struct Sub { int n = 0, cnt = 0, ntiles = 0, chunks = 1, m = 1; TileCfg cfg{8}; OuterDev<C>* d = nullptr; };
+  std::vector<Sub> outer;
+  LevelDev<C>* lev0 = nullptr;   // level-0 descriptors of all problems (single problem: [0])
+  int lev0_nflat = 1;
+  void* dmem = nullptr;
+  ~Group() { if (dmem) cudaFree(dmem); }
+};
+
+template <typename C>
+static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* g) {
+  g->hs.assign(hs, hs + count);
+  g->nprob = count;
+  const Handle& h0 = *hs[0];
+  g->dim = h0.dim;
+  g->nu1 = h0.nu1;
+  g->nu2 = h0.nu2;
+  g->s = h0.s;
+  g->cfg = h0.cfg;
+  for (int p = 0; p < count; ++p) {
+    const Handle& h = *hs[p];
+    if (h.dim != h0.dim || h.prec != h0.prec || h.nu1 != h0.nu1 || h.nu2 != h0.nu2 || h.s != h0.s ||
+        h.lev.back().n != h0.lev.back().n) {
+      set_error("batched problems must share dim, precision, nu1, nu2, s and the coarsest size");
+      return HELM_EINVAL;
+    }
+    g->Lmax = std::max(g->Lmax, (int)h.lev.size());
+  }
+  std::vector<int> off(count);
+  int maxoff = 0;
+  for (int p = 0; p < count; ++p) {
+    off[p] = g->Lmax - (int)hs[p]->lev.size();
+    maxoff = std::max(maxoff, off[p]);
+  }
+  // first depth handled by the single-CTA coarse kernel
+  int tthr = g->Lmax - 1;
+  {
+    // sizes by depth (from the deepest-reaching problem)
+    const Handle* big = nullptr;
+    for (int p = 0; p < count; ++p) if (off[p] == 0) big = hs[p];
+    for (int t = 0; t < g->Lmax; ++t)
+      if (big->lev[t].n <= coarse_threshold(g->dim)) { tthr = t; break; }
+  }
+  g->tc = std::min(std::max(tthr, maxoff), g->Lmax - 1);
+  g->nlev_c = g->Lmax - g->tc;
+  // tile config of a group: the first problem's
+  for (int p = 0; p < count; ++p)
+    if (hs[p]->cfg.rows != g->cfg.rows && off[p] == 0) g->cfg = hs[p]->cfg;
+  // host descriptor arrays
+  std::vector<std::vector<LevelDev<C>>> dep(g->tc);
+  g->depth.resize(g->tc);
+  for (int t = 0; t < g->tc; ++t) {
+    for (int p = 0; p < count; ++p) {
+      if (off[p] > t) continue;
+      const int l = t - off[p];
+      dep[t].push_back(make_leveldev<C>(*hs[p], l));
+      typename Group<C>::Depth& D = g->depth[t];
+      const HostLevel& L = hs[p]->lev[l];
+      if (D.cnt > 0 && D.n != L.n) { set_error("batched problems must have n + 1 a power of two"); return HELM_EINVAL; }
+      D.n = L.n;
+      D.cnt += 1;
+      D.ntiles = tiles_per_problem(g->dim, L.P, g->cfg);
+      D.nflat = L.nflat;
+      if (D.ntiles > L.ntiles && L.ntiles > 0 && hs[p]->cfg.rows != g->cfg.rows) {
+        set_error("inconsistent tile configuration in batch");
+        return HELM_EINVAL;
+      }
+    }
+  }
+  std::vector<LevelDev<C>> coarse;
+  std::vector<CoarseLU> lus;
+  for (int p = 0; p < count; ++p) {
+    for (int t = g->tc; t < g->Lmax; ++t) coarse.push_back(make_leveldev<C>(*hs[p], t - off[p]));
+    CoarseLU c;
+    c.m = hs[p]->lu_m;
+    c.lu = hs[p]->lu;
+    c.piv = hs[p]->piv;
+    lus.push_back(c);
+  }
+  std::vector<LevelDev<C>> lev0;
+  for (int p = 0; p < count; ++p) lev0.push_back(make_leveldev<C>(*hs[p], 0));
+  g->lev0_nflat = hs[0]->lev[0].nflat;
+  // outer subgroups by top size
+  std::vector<std::vector<OuterDev<C>>> subs;
+  for (int p = 0; p < count; ++p) {
+    const Handle& h = *hs[p];
+    int si = -1;
+    for (size_t q = 0; q < g->outer.size(); ++q) if (g->outer[q].n == h.n) si = (int)q;
+    if (si < 0) {
+      typename Group<C>::Sub S;
+      S.n = h.n;
+      S.cfg = h.cfg;
+      S.ntiles = tiles_per_problem(g->dim, h.n + 1, h.cfg);
+      S.chunks = h.chunks;
+      S.m = h.m;
+      g->outer.push_back(S);
+      subs.emplace_back();
+      si = (int)g->outer.size() - 1;
+    }
+    g->outer[si].cnt += 1;
+    g->outer[si].m = std::max(g->outer[si].m, h.m);
+    subs[si].push_back(make_outerdev<C>(h));
+  }
+  // one device allocation for every descriptor array
+  size_t bytes = 0;
+  for (int t = 0; t < g->tc; ++t) bytes += dep[t].size() * sizeof(LevelDev<C>);
+  bytes += coarse.size() * sizeof(LevelDev<C>) + lus.size() * sizeof(CoarseLU) + lev0.size() * sizeof(LevelDev<C>);
+  for (auto& v : subs) bytes += v.size() * sizeof(OuterDev<C>);
+  bytes += 64 * (g->tc + subs.size() + 4);
+  CUDA_TRY(cudaMalloc(&g->dmem, bytes));
+  char* cur = (char*)g->dmem;
+  auto put = [&](const void* src, size_t nb) -> void* {
+    void* dst = cur;
+    if (nb) cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, st);
+    cur += (nb + 63) / 64 * 64;
+    return dst;
+  };
+  for (int t = 0; t < g->tc; ++t) g->depth[t].d = (LevelDev<C>*)put(dep[t].data(), dep[t].size() * sizeof(LevelDev<C>));
+  g->dcoarse = (LevelDev<C>*)put(coarse.data(), coarse.size() * sizeof(LevelDev<C>));
+  g->dlu = (CoarseLU*)put(lus.data(), lus.size() * sizeof(CoarseLU));
+  g->lev0 = (LevelDev<C>*)put(lev0.data(), lev0.size() * sizeof(LevelDev<C>));
+  for (size_t q = 0; q < subs.size(); ++q) g->outer[q].d = (OuterDev<C>*)put(subs[q].data(), subs[q].size() * sizeof(OuterDev<C>));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return HELM_OK;
+}
+
+// One V(nu1, nu2) cycle from a zero guess on every problem of the group (Sec. 3.1).
+template <typename C>
+static void run_vcycle(const Group<C>& g, cudaStream_t st) {
+  const int dim = g.dim;
+  for (int t = 0; t < g.tc; ++t) {
+    const auto& D = g.depth[t];
+    if (g.nu1 == 0) {
+      launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, g.cfg, true, true, true, st);
+      continue;
+    }
+    for (int sw = 0; sw < g.nu1; ++sw) {
+      for (int J = 1; J <= g.s; ++J) launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, g.cfg, sw == 0, true, st);
+      if (sw < g.nu1 - 1)
+        launch_update_flat<C>(dim, UPD_RESIDUAL, D.d, D.cnt, D.nflat, sw == 0, 0, sw == 0, st);
+      else
+        launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, g.cfg, sw == 0, sw == 0, false, st);
+    }
+  }
+  launch_coarse<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, st);
+  for (int t = g.tc - 1; t >= 0; --t) {
+    const auto& D = g.depth[t];
+    launch_prolong<C>(dim, g.nu2 > 0, D.d, D.cnt, g.nu2 > 0 ? D.ntiles : D.nflat, g.cfg, st);
+    for (int sw = 0; sw < g.nu2; ++sw) {
+      const bool last = (sw == g.nu2 - 1);
+      for (int J = 1; J <= g.s; ++J)
+        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, g.cfg, false, J < g.s || !last, st);
+      launch_update_flat<C>(dim, last ? UPD_XONLY : UPD_RESIDUAL, D.d, D.cnt, D.nflat, false, 1, false, st);
+    }
+  }
+}
+
+template <typename C>
+static const LevelDev<C>* level0_desc(const Group<C>& g) {
+  return g.lev0;
+}
+
+template <typename C>
+static Group<C>* cached_group(Handle* h, cudaStream_t st, int* rc) {
+  if (!h->group_cache) {
+    Group<C>* g = new Group<C>();
+    Handle* hs[1] = {h};
+    *rc = build_group<C>(hs, 1, st, g);
+    if (*rc != HELM_OK) { delete g; return nullptr; }
+    h->group_cache = g;
+  }
+  *rc = HELM_OK;
+  return (Group<C>*)h->group_cache;
+}
+
+template <typename C>
+static int precond_apply_t(Handle* h, const void* r, void* z, int prec, cudaStream_t st) {
+  int rc;
+  Group<C>* g = cached_group<C>(h, st, &rc);
+  if (!g) return rc;
+  launch_load_input<C>(h->dim, g->lev0, g->lev0_nflat, r, prec, st);
+  run_vcycle<C>(*g, st);
+  launch_store_output<C>(h->dim, h->n, g->lev0, z, prec, st);
+  CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
+int precond_apply(Handle* h, const void* r, void* z, int prec, cudaStream_t st) {
+  if (!h || !r || !z) { set_error("NULL argument"); return HELM_EINVAL; }
+  if (prec != HELM_C64 && prec != HELM_C128) { set_error("prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
+  return h->prec == HELM_C128 ? precond_apply_t<double2>(h, r, z, prec, st) : precond_apply_t<float2>(h, r, z, prec, st);
+}
+
+int apply_operator(Handle* h, int which, const void* v, void* w, int prec, cudaStream_t st) {
+  if (!h || !v || !w) { set_error("NULL argument"); return HELM_EINVAL; }
+  if (prec != HELM_C64 && prec != HELM_C128) { set_error("prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
+  const HostLevel& L0 = h->lev[0];
+  const double2* c = which == 1 ? h->hcoef : L0.coef64;
+  apply_operator_dense(h->dim, h->n, c, c + h->n, c + 2 * h->n, L0.phi, L0.phic, v, w, prec, st);
+  CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
+// ------------------------------------------------------------------ FGMRES driver
+template <typename C>
+static void run_iteration(const Group<C>& g, cudaStream_t st) {
+  run_vcycle<C>(g, st);
+  for (const auto& o : g.outer) outer_apply_h<C>(g.dim, o.d, o.cnt, o.ntiles, o.cfg, st);
+  for (const auto& o : g.outer) outer_dots<C>(o.d, o.cnt, o.chunks, o.m, st);
+  for (const auto& o : g.outer) outer_vnew<C>(o.d, o.cnt, o.chunks, o.m, false, st);
+}
+
+// Cycle end (acts only on problems whose cycle ended): y = R^{-1} g, x += Z y, true
+// residual, and v_0 of the next cycle.
+template <typename C>
+static void run_cycle_end(const Group<C>& g, cudaStream_t st) {
+  for (const auto& o : g.outer) outer_backsolve<C>(o.d, o.cnt, st);
+  for (const auto& o : g.outer) outer_solution<C>(o.d, o.cnt, o.chunks, o.m, st);
+  for (const auto& o : g.outer) outer_residual<C>(g.dim, o.d, o.cnt, o.ntiles, o.cfg, st);
+  for (const auto& o : g.outer) outer_vnew<C>(o.d, o.cnt, o.chunks, o.m, true, st);
+}
+
+template <typename C>
+static int solve_t(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
+                   helm_info* infos, cudaStream_t st) {
+  // inputs and state
+  for (int p = 0; p < count; ++p) {
+    Handle* h = hs[p];
+    convert_dense_to_padded_c128(h->dim, h->n, (const double2*)b[p], h->bpad, st);
+    convert_dense_to_padded_c128(h->dim, h->n, (const double2*)x[p], h->xpad, st);
+    OuterState s0;
+    std::memset(&s0, 0, sizeof(s0));
+    s0.m = h->m;
+    s0.maxit = h->maxit;
+    s0.tol = tol;
+    s0.bnorm = -1.0;
+    s0.need_residual = 1;
+    CUDA_TRY(cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(cudaGetLastError());
+  std::vector<Handle*> active(hs, hs + count);
+  std::vector<OuterState> host(count);
+  OuterState* pin = nullptr;
+  CUDA_TRY(cudaMallocHost(&pin, sizeof(OuterState) * count));
+  std::unique_ptr<OuterState, decltype(&cudaFreeHost)> pin_guard(pin, &cudaFreeHost);
+  std::unique_ptr<Group<C>> own;
+  Group<C>* g = nullptr;
+  auto rebuild = [&]() -> int {
+    if (count == 1) {
+      int rc;
+      g = cached_group<C>(active[0], st, &rc);
+      return rc;
+    }
+    own.reset(new Group<C>());
+    g = own.get();
+    return build_group<C>(active.data(), (int)active.size(), st, g);
+  };
+  TRY(rebuild());
+  run_cycle_end<C>(*g, st);  // first true residual and v_0 of every problem
+  int max_maxit = 0;
+  for (int p = 0; p < count; ++p) max_maxit = std::max(max_maxit, hs[p]->maxit);
+  for (int guard = 0; guard <= 2 * max_maxit + 4; ++guard) {
+    for (int p = 0; p < count; ++p)
+      CUDA_TRY(cudaMemcpyAsync(pin + p, hs[p]->st, sizeof(OuterState), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<Handle*> still;
+    for (int p = 0; p < count; ++p) {
+      host[p] = pin[p];
+      if (!host[p].done && std::find(active.begin(), active.end(), hs[p]) != active.end()) still.push_back(hs[p]);
+    }
+    if (still.empty()) break;
+    if (still.size() != active.size()) {
+      active = still;
+      TRY(rebuild());
+    }
+    run_iteration<C>(*g, st);
+    run_cycle_end<C>(*g, st);
+    CUDA_TRY(cudaGetLastError());
+  }
+  int rc_all = HELM_OK;
+  for (int p = 0; p < count; ++p) {
+    Handle* h = hs[p];
+    const OuterState& s = host[p];
+    if (s.bnorm == 0.0) {
+      // b = 0: the solution is x = 0 whatever the initial guess
+      const size_t npts = h->dim == 3 ? (size_t)h->n * h->n * h->n : (size_t)h->n * h->n;
+      CUDA_TRY(cudaMemsetAsync(x[p], 0, npts * sizeof(double2), st));
+    } else {
+      convert_padded_to_dense_c128(h->dim, h->n, h->xpad, (double2*)x[p], st);
+    }
+    int status = s.done == 1 ? HELM_OK : (s.done == 3 ? HELM_ENUMERIC : HELM_ENOCONV);
+    if (infos) {
+      infos[p].iters = s.iters;
+      infos[p].restarts = s.restarts;
+      infos[p].rel_res_est = s.rel_est;
+      infos[p].rel_res_true = s.rel_true;
+      infos[p].status = status;
+    }
+    if (status != HELM_OK && rc_all == HELM_OK) rc_all = status;
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return rc_all;
+}
+
+int solve_group(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
+                helm_info* infos, cudaStream_t st) {
+  if (!hs || count <= 0 || !b || !x) { set_error("invalid batch arguments"); return HELM_EINVAL; }
+  if (!(tol > 0.0) || !std::isfinite(tol)) { set_error("tol must be positive"); return HELM_EINVAL; }
+  for (int p = 0; p < count; ++p)
+    if (!hs[p] || !b[p] || !x[p]) { set_error("NULL handle or vector in batch"); return HELM_EINVAL; }
+  const int prec = hs[0]->prec;
+  return prec == HELM_C128 ? solve_t<double2>(hs, count, b, x, tol, infos, st)
+                           : solve_t<float2>(hs, count, b, x, tol, infos, st);
+}
+
+static void destroy_group_cache(Handle* h) {
+  if (!h->group_cache) return;
+  if (h->prec == HELM_C128) delete (Group<double2>*)h->group_cache;
+  else delete (Group<float2>*)h->group_cache;
+  h->group_cache = nullptr;
+}
+
+Handle::~Handle() {
+  destroy_group_cache(this);
+  for (void* p : allocs) cudaFree(p);
+}
+
+}  // namespace helm

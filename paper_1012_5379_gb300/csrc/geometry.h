@@ -1,0 +1,18 @@
+// Host geometry of the complex stretched grids and the coarsest dense LU.
+#pragma once
+#include <complex>
+#include <vector>
+
+namespace helm {
+
+typedef std::complex<double> cplx;
+
+std::vector<cplx> grid_spacings(int n, double ecs, double theta_gamma, double theta_beta);
+void stencil_coefficients(const std::vector<cplx>& sp, std::vector<cplx>& a, std::vector<cplx>& d,
+                          std::vector<cplx>& c);
+std::vector<cplx> dense_operator(int dim, int n, const std::vector<cplx>& a, const std::vector<cplx>& d,
+                                 const std::vector<cplx>& c, const std::vector<double>& phi);
+bool lu_factor(std::vector<cplx>& A, int m, std::vector<int>& perm);
+std::vector<int> level_sizes(int n, int coarsest);
+
+}  // namespace helm

@@ -1,0 +1,186 @@
+// Internal data structures shared by the host engine and the sm_103a kernels.
+//
+// Vector layout ("padded"): a level with n interior nodes per axis stores P^d
+// elements, P = n + 1, with interior node (x, y, z) (0-based, < n) at
+// (z * P + y) * P + x.  Positions with a coordinate equal to n are ghosts and hold
+// zero; every kernel that writes a vector writes zero there.  P is a power of two for
+// n = 2^L - 1, so rows are aligned.  Kernels bounds-check every neighbour load, so
+// nothing outside [0, P^d) is ever touched.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __CUDACC__
+#define HELM_HD __host__ __device__
+#else
+#define HELM_HD
+#endif
+
+namespace helm {
+
+constexpr int SMAX = 4;            // max GMRES(s) steps per smoothing sweep
+constexpr int NPART = 2 * SMAX + 4;  // doubles per partial-sum slot of a sweep pass
+
+// Per (problem, level) state of the current GMRES(s) sweep, FP64, device memory.
+// Raw vectors R_0 = r0 (initial residual of the sweep), R_j = p_j = M v_j.  Every
+// Arnoldi vector is kept as coefficients over the raw vectors:
+//   v_j = sum_{k<j} Cf[j][k] R_k   (j = 1..s).
+struct SweepScalars {
+  double beta2;                        // ||R_0||^2
+  int m;                               // Krylov steps of this sweep (0: nothing to do)
+  int s;                               // requested steps
+  double2 G[SMAX + 1][SMAX + 1];       // G[k][j] = <R_k, R_j>, k <= j
+  double2 Cf[SMAX + 1][SMAX + 1];      // Arnoldi vectors over raw vectors
+  double2 Hh[SMAX + 1][SMAX];          // Hessenberg matrix of the sweep
+  double2 xcoef[SMAX + 1];             // x_new = x_old + sum_k xcoef[k] R_k
+  double2 rcoef[SMAX + 1];             // r_new = sum_k rcoef[k] R_k
+  unsigned int counter;                // last-block-done counter
+  int status;                          // nonzero: NaN/Inf seen
+};
+
+// One level of one problem, as seen by the kernels (device memory).
+template <typename C>
+struct LevelDev {
+  int n, P;               // interior nodes per axis, pitch n+1
+  int nc, Pc;             // next coarser level (0 on the coarsest)
+  int ntiles;             // tiles of this level per problem (for reductions)
+  int s;                  // GMRES steps per sweep
+  C* b;                   // right-hand side of this level
+  C* xa;                  // iterate after pre-smoothing
+  C* xb;                  // iterate after coarse correction and post-smoothing (output)
+  C* r0;                  // initial residual of a post-smoothing sweep
+  C* p[SMAX];             // p_j = M v_j
+  C* bc;                  // coarser level's b (restriction target)
+  const C* xcb;           // coarser level's output (prolongation source)
+  const C* ca;            // 1D coefficients of u_{i-1}  (length n)
+  const C* cd;            // 1D coefficients of u_i
+  const C* cc;            // 1D coefficients of u_{i+1}
+  const float* phi;       // phi field in padded layout, or nullptr
+  double phic;            // constant phi when phi == nullptr
+  SweepScalars* sc;       // this level's sweep state
+  SweepScalars* scc;      // coarser level's sweep state
+  double* part;           // partial sums: ntiles * NPART doubles
+};
+
+// Dense LU factors of the coarsest operator (FP64), row-major, with pivots.
+struct CoarseLU {
+  int m;                  // unknowns (n^d)
+  const double2* lu;      // m*m
+  const int* piv;         // m
+};
+
+// Outer FGMRES state of one problem (FP64, device memory).
+struct OuterState {
+  int j;                  // index of the Arnoldi vector being preconditioned
+  int m;                  // restart length (columns of Hbar)
+  int iters;              // total preconditioner applications
+  int maxit;
+  int done;               // 0 running, 1 converged, 2 maxit, 3 numeric, 4 breakdown
+  int cycle_end;          // 1: the current cycle must end (solve and recompute)
+  int restarts;
+  int status;
+  double tol;
+  double bnorm;           // ||b||
+  double beta;            // ||r0|| of the current cycle
+  double rel_est;         // |g_{j+1}| / ||b||
+  double rel_true;        // last true relative residual
+  double hnext;           // h_{j+1,j} of the last column
+  double wnorm2;          // ||w||^2 of the last column
+  unsigned int counter;   // last-block counter
+  int need_residual;      // 1: the true residual must be recomputed (start or cycle end)
+  int fresh;              // 1: a new cycle starts, v_0 must be formed
+  int pad;
+};
+
+// Per-problem pointers of the outer solve (device memory).
+template <typename C>
+struct OuterDev {
+  int n, P, ntiles;
+  const double2* ca; const double2* cd; const double2* cc;  // H coefficients
+  const float* phi; double phic;
+  double2* bpad;          // b in padded layout
+  double2* xpad;          // x in padded layout
+  double2* w;             // scratch: H z_j, then residual
+  double2* V;             // (m+1) Arnoldi vectors, padded, stride vs
+  C* Z;                   // m preconditioned vectors, padded, stride vs
+  C* b0;                  // V-cycle input of level 0 (precision C)
+  const C* zout;          // V-cycle output of level 0 (precision C)
+  int s;                  // GMRES steps per smoothing sweep
+  size_t vs;              // elements per vector (P^d)
+  double2* Hm;            // (m+1) x m Hessenberg, column-major
+  double2* g;             // m+1
+  double* cs; double2* sn;// Givens rotations
+  double2* y;             // m
+  double2* hcol;          // m+1 reduced dots of the current column
+  double* vscale;         // m+1: v_i = vscale[i] * V[i] (V stored unnormalised)
+  double* part;           // partial sums
+  OuterState* st;
+  SweepScalars* sc0;      // level-0 sweep state (set by the kernel that writes b0)
+};
+
+// Tile configuration of the marching kernels.
+struct TileCfg {
+  int rows;   // 2D: rows marched per warp (even); 3D: planes marched per CTA (even)
+};
+
+constexpr int WARPS2 = 8;     // 2D: warps per CTA (each marches its own rows)
+constexpr int WY3 = 8;        // 3D: owned y rows per CTA (plus 2 halo warps)
+
+HELM_HD inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+inline int tiles_per_problem(int dim, int P, TileCfg cfg) {
+  if (dim == 2) return ceil_div(P, 32) * ceil_div(P, WARPS2 * cfg.rows);
+  return ceil_div(P, 32) * ceil_div(P, WY3) * ceil_div(P, cfg.rows);
+}
+
+// ---------------------------------------------------------------- launchers
+enum UpdateMode { UPD_RESTRICT = 0, UPD_RESIDUAL = 1, UPD_XONLY = 2 };
+
+// V-cycle passes (vcycle_c64.cu / vcycle_c128.cu), C = float2 or double2.
+template <typename C>
+void launch_arnoldi(int dim, int J, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
+                    bool store_p, cudaStream_t st);
+template <typename C>
+void launch_restrict(int dim, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
+                     bool x_from_zero, bool nosmooth, cudaStream_t st);
+template <typename C>
+void launch_update_flat(int dim, UpdateMode mode, const LevelDev<C>* levs, int nprob, int ntiles, bool r0_is_b,
+                        int xsel, bool x_from_zero, cudaStream_t st);
+template <typename C>
+void launch_prolong(int dim, bool with_residual, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg,
+                    cudaStream_t st);
+template <typename C>
+void launch_coarse(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
+                   int nu1, int nu2, cudaStream_t st);
+// level-0 input from a natural-layout vector of precision in_prec (HELM_C64/HELM_C128)
+template <typename C>
+void launch_load_input(int dim, const LevelDev<C>* levs, int ntiles, const void* src, int in_prec, cudaStream_t st);
+template <typename C>
+void launch_store_output(int dim, int n, const LevelDev<C>* levs, void* dst, int out_prec, cudaStream_t st);
+
+// Outer FP64 kernels (outer.cu).
+template <typename C>
+void outer_residual(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCfg cfg, cudaStream_t st);
+template <typename C>
+void outer_apply_h(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCfg cfg, cudaStream_t st);
+template <typename C>
+void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t st);
+template <typename C>
+void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start, cudaStream_t st);
+template <typename C>
+void outer_backsolve(const OuterDev<C>* od, int nprob, cudaStream_t st);
+template <typename C>
+void outer_solution(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t st);
+
+// Layout conversions and the stand-alone operator (convert.cu).
+void convert_dense_to_padded_c128(int dim, int n, const double2* src, double2* dst, cudaStream_t st);
+void convert_padded_to_dense_c128(int dim, int n, const double2* src, double2* dst, cudaStream_t st);
+void scatter_phi(int dim, int n_level, int stride, int n_fine, const float* phi_dense_fine, float* phi_pad_level,
+                 cudaStream_t st);
+// w = A v on the finest level, A given by 1D coefficients (prec: HELM_C64/HELM_C128),
+// natural layout in and out.
+void apply_operator_dense(int dim, int n, const double2* ca, const double2* cd, const double2* cc,
+                          const float* phi_pad, double phic, const void* v, void* w, int prec, cudaStream_t st);
+
+}  // namespace helm

@@ -1,0 +1,469 @@
+// Outer flexible GMRES in FP64 (Sec. 5: FGMRES [Saad 1993] on H u = b, right-
+// preconditioned by one V-cycle on M^CSG; the preconditioned vectors z_j are stored
+// because the GMRES-smoothed V-cycle is not a fixed linear operator).
+//
+// Per iteration j:  w = H z_j (FP64 stencil, z_j in the preconditioner precision)
+//                   h_ij = <v_i, w>                      (one multi-dot pass)
+//                   u = w - sum h_ij v_i, h_{j+1,j} = ||u|| (explicit, same pass)
+//                   Givens update of the least-squares residual |g_{j+1}|
+// u is stored unnormalised, v_{j+1} = u / h_{j+1,j} lives as u with a scale factor
+// vscale[j+1] applied to every coefficient that touches it; u (in the
+// preconditioner precision) is the next V-cycle input.  The explicit norm replaces
+// sqrt(||w||^2 - sum |h|^2), whose cancellation made the basis lose orthogonality
+// once the preconditioned operator is close to the identity.
+// At a cycle end: y = R^{-1} g, x += Z y, true residual b - H x recomputed in FP64.
+#include "device_common.cuh"
+#include "vcycle.cuh"
+
+namespace helm {
+
+template <typename C>
+__device__ __forceinline__ double2 ldd(const C* p, int x, int y, int z, int n, int P) {
+  return inside(x, y, z, n) ? to_d(__ldg(p + pidx(x, y, z, P))) : make_double2(0, 0);
+}
+
+struct HCoef { double2 a, d, c; };
+__device__ __forceinline__ HCoef ldh(const double2* ca, const double2* cd, const double2* cc, int i, int n) {
+  HCoef r;
+  if ((unsigned)i < (unsigned)n) { r.a = __ldg(ca + i); r.d = __ldg(cd + i); r.c = __ldg(cc + i); }
+  else { r.a = r.d = r.c = make_double2(0, 0); }
+  return r;
+}
+
+// MODE 0: w = b - H x (true residual; also ||b||^2 on the first call)
+// MODE 1: w = H z_j, with z_j read from the V-cycle output buffer and archived into Z[j]
+template <typename C, int MODE>
+__device__ __forceinline__ const C* stencil_src(const OuterDev<C>& O, const OuterState* st);
+template <>
+__device__ __forceinline__ const float2* stencil_src<float2, 0>(const OuterDev<float2>& O, const OuterState*) { return nullptr; }
+template <>
+__device__ __forceinline__ const double2* stencil_src<double2, 0>(const OuterDev<double2>& O, const OuterState*) { return nullptr; }
+template <>
+__device__ __forceinline__ const float2* stencil_src<float2, 1>(const OuterDev<float2>& O, const OuterState*) { return O.zout; }
+template <>
+__device__ __forceinline__ const double2* stencil_src<double2, 1>(const OuterDev<double2>& O, const OuterState*) { return O.zout; }
+
+template <typename C, int MODE>
+__device__ __forceinline__ void outer_stencil_epilogue(const OuterDev<C>& O, OuterState* st, const double* tot) {
+  if (MODE == 0) {
+    if (st->bnorm < 0.0) st->bnorm = sqrt(tot[1]);
+    const double beta = sqrt(tot[0]);
+    st->beta = beta;
+    st->rel_true = st->bnorm > 0.0 ? beta / st->bnorm : 0.0;
+    st->cycle_end = 0;
+    st->need_residual = 0;
+    st->j = 0;
+    if (!isfinite(beta)) { st->done = 3; st->status = -4; }
+    else if (st->bnorm == 0.0 || st->rel_true <= st->tol) { st->done = 1; st->status = 0; }
+    else if (st->iters >= st->maxit) { st->done = 2; st->status = -3; }
+    else {
+      for (int i = 0; i <= st->m; ++i) O.g[i] = make_double2(0, 0);
+      O.g[0] = make_double2(beta, 0);
+      st->hnext = beta;  // v_0 = r / beta
+      st->fresh = 1;
+    }
+  } else {
+    st->wnorm2 = tot[0];
+  }
+}
+
+template <typename C, int MODE>
+__global__ void __launch_bounds__(32 * WARPS2)
+k_hstencil2(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
+  __shared__ double sm[64];
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const OuterDev<C>& O = ods[prob];
+  OuterState* st = O.st;
+  if (MODE == 1 && (st->done || st->cycle_end)) return;
+  if (MODE == 0 && !st->need_residual) return;
+  const int n = O.n, P = O.P;
+  const int ntx = ceil_div(P, 32);
+  const int tx = tile % ntx, ty = tile / ntx;
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int x = tx * 32 + lane;
+  const int ybeg = (ty * WARPS2 + warp) * rows;
+  const int yend = min(ybeg + rows, P);
+  const C* u1 = stencil_src<C, MODE>(O, st);
+  C* zarch = O.Z + (size_t)st->j * O.vs;
+  const double2* u0 = O.xpad;
+  auto form = [&](int xx, int yy) -> double2 {
+    return MODE == 0 ? ldd(u0, xx, yy, 0, n, P) : ldd(u1, xx, yy, 0, n, P);
+  };
+  const HCoef cx = ldh(O.ca, O.cd, O.cc, x, n);
+  double accw = 0.0, accb = 0.0;
+  if (ybeg < P) {
+    double2 vm = form(x, ybeg - 1), v0 = form(x, ybeg);
+    for (int y = ybeg; y < yend; ++y) {
+      double2 vp = form(x, y + 1);
+      double2 vl = shfl_up_c(v0, 1), vr = shfl_down_c(v0, 1);
+      if (lane == 0) vl = form(x - 1, y);
+      if (lane == 31) vr = form(x + 1, y);
+      if (x < P) {
+        double2 out = make_double2(0, 0);
+        if (x < n && y < n) {
+          const HCoef cy = ldh(O.ca, O.cd, O.cc, y, n);
+          double2 diag = cadd(cx.d, cy.d);
+          diag.x -= O.phi ? (double)__ldg(O.phi + pidx(x, y, 0, P)) : O.phic;
+          double2 p = cmul(diag, v0);
+          p = cfma(cx.a, vl, p);
+          p = cfma(cx.c, vr, p);
+          p = cfma(cy.a, vm, p);
+          p = cfma(cy.c, vp, p);
+          if (MODE == 0) {
+            double2 bv = __ldg(O.bpad + pidx(x, y, 0, P));
+            out = csub(bv, p);
+            accb += dabs2(bv);
+          } else {
+            out = p;
+          }
+          accw += dabs2(out);
+        }
+        O.w[pidx(x, y, 0, P)] = out;
+        if (MODE == 1) zarch[pidx(x, y, 0, P)] = u1[pidx(x, y, 0, P)];
+      }
+      vm = v0;
+      v0 = vp;
+    }
+  }
+  double red[2] = {accw, accb}, tot[2];
+  if (grid_sum_last<2>(red, O.part, tile, ntiles, &st->counter, sm, tot)) {
+    if (flat_tid() == 0) outer_stencil_epilogue<C, MODE>(O, st, tot);
+  }
+}
+
+template <typename C, int MODE>
+__global__ void __launch_bounds__(32 * (WY3 + 2))
+k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
+  __shared__ double sm[64];
+  __shared__ double2 sv[2][WY3 + 2][32];
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const OuterDev<C>& O = ods[prob];
+  OuterState* st = O.st;
+  if (MODE == 1 && (st->done || st->cycle_end)) return;
+  if (MODE == 0 && !st->need_residual) return;
+  const int n = O.n, P = O.P;
+  const int ntx = ceil_div(P, 32), nty = ceil_div(P, WY3);
+  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const bool owned = (w >= 1 && w <= WY3);
+  const int x = tx * 32 + lane;
+  const int y = ty * WY3 - 1 + w;
+  const int zbeg = tz * rows;
+  const int zend = min(zbeg + rows, P);
+  const C* u1 = stencil_src<C, MODE>(O, st);
+  C* zarch = O.Z + (size_t)st->j * O.vs;
+  const double2* u0 = O.xpad;
+  auto form = [&](int xx, int yy, int zz) -> double2 {
+    return MODE == 0 ? ldd(u0, xx, yy, zz, n, P) : ldd(u1, xx, yy, zz, n, P);
+  };
+  const HCoef cx = ldh(O.ca, O.cd, O.cc, x, n), cy = ldh(O.ca, O.cd, O.cc, y, n);
+  double accw = 0.0, accb = 0.0;
+  if (zbeg < P) {
+    double2 vm = form(x, y, zbeg - 1), v0 = form(x, y, zbeg);
+    for (int z = zbeg; z < zend; ++z) {
+      double2 vp = form(x, y, z + 1);
+      sv[z & 1][w][lane] = v0;
+      __syncthreads();
+      if (owned) {
+        double2 vs = sv[z & 1][w - 1][lane], vn = sv[z & 1][w + 1][lane];
+        double2 vl = shfl_up_c(v0, 1), vr = shfl_down_c(v0, 1);
+        if (lane == 0) vl = form(x - 1, y, z);
+        if (lane == 31) vr = form(x + 1, y, z);
+        if (x < P && y < P) {
+          double2 out = make_double2(0, 0);
+          if (inside(x, y, z, n)) {
+            const HCoef cz = ldh(O.ca, O.cd, O.cc, z, n);
+            double2 diag = cadd(cadd(cx.d, cy.d), cz.d);
+            diag.x -= O.phi ? (double)__ldg(O.phi + pidx(x, y, z, P)) : O.phic;
+            double2 p = cmul(diag, v0);
+            p = cfma(cx.a, vl, p);
+            p = cfma(cx.c, vr, p);
+            p = cfma(cy.a, vs, p);
+            p = cfma(cy.c, vn, p);
+            p = cfma(cz.a, vm, p);
+            p = cfma(cz.c, vp, p);
+            if (MODE == 0) {
+              double2 bv = __ldg(O.bpad + pidx(x, y, z, P));
+              out = csub(bv, p);
+              accb += dabs2(bv);
+            } else {
+              out = p;
+            }
+            accw += dabs2(out);
+          }
+          O.w[pidx(x, y, z, P)] = out;
+          if (MODE == 1) zarch[pidx(x, y, z, P)] = u1[pidx(x, y, z, P)];
+        }
+      }
+      vm = v0;
+      v0 = vp;
+    }
+  }
+  double red[2] = {accw, accb}, tot[2];
+  if (grid_sum_last<2>(red, O.part, tile, ntiles, &st->counter, sm, tot)) {
+    if (flat_tid() == 0) outer_stencil_epilogue<C, MODE>(O, st, tot);
+  }
+}
+
+// ------------------------------------------------------------------ multi-dot
+// h_i = <v_i, w>, i = 0..j, over a grid of `chunks` CTAs per problem; each warp keeps
+// its running sums per i in shared memory (fixed order), the block combines warps,
+// and the last block combines blocks and performs the Givens update.
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_PPT = 8;   // points per thread per chunk
+
+template <typename C>
+__global__ void __launch_bounds__(DOT_THREADS)
+k_dots(const OuterDev<C>* __restrict__ ods, int chunks) {
+  extern __shared__ double2 swarp[];  // [8][m+1]
+  __shared__ int s_last;
+  const int prob = blockIdx.x / chunks, cta = blockIdx.x - prob * chunks;
+  const OuterDev<C>& O = ods[prob];
+  OuterState* st = O.st;
+  if (st->done || st->cycle_end) return;
+  const int j = st->j, M1 = st->m + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < 8 * M1; i += DOT_THREADS) swarp[i] = make_double2(0, 0);
+  __syncthreads();
+  const size_t npts = O.vs;
+  const size_t per_chunk = (size_t)DOT_THREADS * DOT_PPT;
+  for (size_t base = (size_t)cta * per_chunk; base < npts; base += (size_t)chunks * per_chunk) {
+    double2 wv[DOT_PPT];
+#pragma unroll
+    for (int q = 0; q < DOT_PPT; ++q) {
+      size_t idx = base + (size_t)q * DOT_THREADS + tid;
+      wv[q] = idx < npts ? __ldcg(O.w + idx) : make_double2(0, 0);
+    }
+    for (int i = 0; i <= j; ++i) {
+      const double2* v = O.V + (size_t)i * O.vs;
+      double2 acc = make_double2(0, 0);
+#pragma unroll
+      for (int q = 0; q < DOT_PPT; ++q) {
+        size_t idx = base + (size_t)q * DOT_THREADS + tid;
+        if (idx < npts) acc = cdotacc(__ldcg(v + idx), wv[q], acc);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) swarp[warp * M1 + i] = cadd(swarp[warp * M1 + i], acc);
+    }
+  }
+  __syncthreads();
+  // combine warps (fixed order) and publish this block's partials
+  for (int i = tid; i <= j; i += DOT_THREADS) {
+    double2 s = make_double2(0, 0);
+    for (int ww = 0; ww < 8; ++ww) s = cadd(s, swarp[ww * M1 + i]);
+    O.part[((size_t)cta * M1 + i) * 2] = s.x;
+    O.part[((size_t)cta * M1 + i) * 2 + 1] = s.y;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&st->counter, 1u) == (unsigned)chunks - 1u);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = tid; i <= j; i += DOT_THREADS) {
+    double2 s = make_double2(0, 0);
+    for (int c = 0; c < chunks; ++c)
+      s = cadd(s, make_double2(__ldcg(O.part + ((size_t)c * M1 + i) * 2), __ldcg(O.part + ((size_t)c * M1 + i) * 2 + 1)));
+    O.hcol[i] = s;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  st->counter = 0u;
+  double2* Hc = O.Hm + (size_t)j * M1;
+  for (int i = 0; i <= j; ++i) {
+    const double sc = O.vscale[i];
+    const double2 h = make_double2(O.hcol[i].x * sc, O.hcol[i].y * sc);
+    O.hcol[i] = h;
+    Hc[i] = h;
+  }
+}
+
+// ------------------------------------------------------------------ new Arnoldi vector
+// Givens update of column j once h_{j+1,j} is known (last block of k_vnew).
+template <typename C>
+__device__ void givens_step(const OuterDev<C>& O, OuterState* st, int j, double hn) {
+  const int M1 = st->m + 1;
+  double2* Hc = O.Hm + (size_t)j * M1;
+  Hc[j + 1] = make_double2(hn, 0);
+  for (int i = 0; i < j; ++i) {
+    const double c = O.cs[i];
+    const double2 s = O.sn[i];
+    const double2 t0 = Hc[i], t1 = Hc[i + 1];
+    Hc[i] = cadd(make_double2(c * t0.x, c * t0.y), cmul(s, t1));
+    Hc[i + 1] = csub(make_double2(c * t1.x, c * t1.y), cmul(dconj(s), t0));
+  }
+  const double2 a = Hc[j], b = Hc[j + 1];
+  const double na = sqrt(dabs2(a)), nb = sqrt(dabs2(b));
+  const double r = hypot(na, nb);
+  double c;
+  double2 sn;
+  if (r == 0.0) { c = 1.0; sn = make_double2(0, 0); }
+  else if (na == 0.0) { c = 0.0; sn = make_double2(1, 0); }
+  else {
+    c = na / r;
+    sn = cmul(make_double2(a.x / na, a.y / na), dconj(b));
+    sn = make_double2(sn.x / r, sn.y / r);
+  }
+  O.cs[j] = c;
+  O.sn[j] = sn;
+  Hc[j] = cadd(make_double2(c * a.x, c * a.y), cmul(sn, b));
+  Hc[j + 1] = make_double2(0, 0);
+  const double2 g0 = O.g[j];
+  O.g[j] = make_double2(c * g0.x, c * g0.y);
+  O.g[j + 1] = cmul(make_double2(-sn.x, sn.y), g0);
+}
+
+// start = 1: v_0 = w / beta (w holds the true residual).
+// start = 0: u = w - sum_{i<=j} h_i v_i stored as V[j+1] with ||u|| reduced here;
+// the last block sets h_{j+1,j} = ||u||, vscale[j+1] = 1/||u||, performs the Givens
+// update and decides whether the cycle ends.  Both write the next V-cycle input b0
+// (precision C) and start level 0's first sweep from its norm.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_vnew(const OuterDev<C>* __restrict__ ods, int chunks, int start) {
+  extern __shared__ double2 sh[];  // m+1
+  __shared__ double sm[64];
+  const int prob = blockIdx.x / chunks, cta = blockIdx.x - prob * chunks;
+  const OuterDev<C>& O = ods[prob];
+  OuterState* st = O.st;
+  if (st->done || (!start && st->cycle_end) || (start && !st->fresh)) return;
+  const int j = start ? -1 : st->j;
+  const int tid = threadIdx.x;
+  for (int i = tid; i <= j; i += blockDim.x) {
+    const double sc = O.vscale[i];
+    sh[i] = make_double2(O.hcol[i].x * sc, O.hcol[i].y * sc);
+  }
+  __syncthreads();
+  const double inv = start ? 1.0 / st->beta : 1.0;
+  const int jn = j + 1;
+  double2* vout = O.V + (size_t)jn * O.vs;
+  double accu = 0.0;
+  typename CT<C>::R accb = 0;
+  for (size_t idx = (size_t)cta * blockDim.x + tid; idx < O.vs; idx += (size_t)chunks * blockDim.x) {
+    double2 wv = __ldcg(O.w + idx);
+    for (int i = 0; i <= j; ++i) {
+      const double2 vi = __ldcg(O.V + (size_t)i * O.vs + idx);
+      wv = csub(wv, cmul(sh[i], vi));
+    }
+    wv = make_double2(wv.x * inv, wv.y * inv);
+    vout[idx] = wv;
+    accu += dabs2(wv);
+    C c = from_d<C>(wv);
+    O.b0[idx] = c;
+    accb += cabs2(c);
+  }
+  double red[2] = {accu, (double)accb}, tot[2];
+  if (grid_sum_last<2>(red, O.part, cta, chunks, &st->counter, sm, tot)) {
+    if (flat_tid() == 0) {
+      sweep_begin(O.sc0, tot[1], O.s);
+      if (start) {
+        O.vscale[0] = 1.0;
+        st->fresh = 0;
+        st->j = 0;
+      } else {
+        const double hn = sqrt(tot[0]);
+        O.vscale[jn] = hn > 0.0 ? 1.0 / hn : 0.0;
+        givens_step(O, st, j, hn);
+        st->iters += 1;
+        st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
+        const bool breakdown = !(hn > 1e-14 * st->beta);
+        if (!isfinite(st->rel_est)) { st->done = 3; st->status = -4; st->cycle_end = 1; }
+        else if (st->rel_est <= st->tol || st->iters >= st->maxit || j + 1 >= st->m || breakdown) st->cycle_end = 1;
+        else st->j = jn;
+      }
+    }
+  }
+}
+
+// y = R^{-1} g over the current cycle's columns (one warp per problem).
+template <typename C>
+__global__ void k_backsolve(const OuterDev<C>* __restrict__ ods) {
+  const OuterDev<C>& O = ods[blockIdx.x];
+  OuterState* st = O.st;
+  if (!st->cycle_end) return;
+  const int k = st->j + 1;  // columns in this cycle
+  const int M1 = st->m + 1;
+  const int lane = threadIdx.x;
+  if (lane == 0) { st->need_residual = 1; st->restarts += 1; }
+  for (int i = lane; i < k; i += 32) O.y[i] = O.g[i];
+  __syncwarp();
+  for (int c = k - 1; c >= 0; --c) {
+    if (lane == 0) {
+      const double2 d = O.Hm[(size_t)c * M1 + c];
+      O.y[c] = dabs2(d) > 0.0 ? ddiv(O.y[c], d) : make_double2(0, 0);
+    }
+    __syncwarp();
+    const double2 yc = O.y[c];
+    for (int i = lane; i < c; i += 32) O.y[i] = csub(O.y[i], cmul(O.Hm[(size_t)c * M1 + i], yc));
+    __syncwarp();
+  }
+}
+
+// x += sum_i y_i z_i (FP64 accumulation of the stored preconditioned vectors).
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_solution(const OuterDev<C>* __restrict__ ods, int chunks) {
+  extern __shared__ double2 sh[];
+  const int prob = blockIdx.x / chunks, cta = blockIdx.x - prob * chunks;
+  const OuterDev<C>& O = ods[prob];
+  OuterState* st = O.st;
+  if (!st->cycle_end) return;
+  const int k = st->j + 1;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = O.y[i];
+  __syncthreads();
+  for (size_t idx = (size_t)cta * blockDim.x + threadIdx.x; idx < O.vs; idx += (size_t)chunks * blockDim.x) {
+    double2 xv = O.xpad[idx];
+    for (int i = 0; i < k; ++i) xv = cfma(sh[i], to_d(__ldcg(O.Z + (size_t)i * O.vs + idx)), xv);
+    O.xpad[idx] = xv;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename C>
+void outer_residual(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCfg cfg, cudaStream_t s) {
+  if (dim == 2) k_hstencil2<C, 0><<<nprob * ntiles, dim3(32, WARPS2), 0, s>>>(od, ntiles, cfg.rows);
+  else k_hstencil3<C, 0><<<nprob * ntiles, dim3(32, WY3 + 2), 0, s>>>(od, ntiles, cfg.rows);
+}
+template <typename C>
+void outer_apply_h(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCfg cfg, cudaStream_t s) {
+  if (dim == 2) k_hstencil2<C, 1><<<nprob * ntiles, dim3(32, WARPS2), 0, s>>>(od, ntiles, cfg.rows);
+  else k_hstencil3<C, 1><<<nprob * ntiles, dim3(32, WY3 + 2), 0, s>>>(od, ntiles, cfg.rows);
+}
+template <typename C>
+void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t s) {
+  const size_t smem = (size_t)8 * (m + 1) * sizeof(double2);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(k_dots<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  k_dots<C><<<nprob * chunks, DOT_THREADS, smem, s>>>(od, chunks);
+}
+template <typename C>
+void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start, cudaStream_t s) {
+  k_vnew<C><<<nprob * chunks, 256, (size_t)(m + 1) * sizeof(double2), s>>>(od, chunks, start ? 1 : 0);
+}
+template <typename C>
+void outer_backsolve(const OuterDev<C>* od, int nprob, cudaStream_t s) {
+  k_backsolve<C><<<nprob, 32, 0, s>>>(od);
+}
+template <typename C>
+void outer_solution(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t s) {
+  k_solution<C><<<nprob * chunks, 256, (size_t)(m + 1) * sizeof(double2), s>>>(od, chunks);
+}
+
+#define HELM_OUTER_INST(C)                                                                              \
+  template void outer_residual<C>(int, const OuterDev<C>*, int, int, TileCfg, cudaStream_t);           \
+  template void outer_apply_h<C>(int, const OuterDev<C>*, int, int, TileCfg, cudaStream_t);            \
+  template void outer_dots<C>(const OuterDev<C>*, int, int, int, cudaStream_t);                        \
+  template void outer_vnew<C>(const OuterDev<C>*, int, int, int, bool, cudaStream_t);                  \
+  template void outer_backsolve<C>(const OuterDev<C>*, int, cudaStream_t);                             \
+  template void outer_solution<C>(const OuterDev<C>*, int, int, int, cudaStream_t);
+HELM_OUTER_INST(float2)
+HELM_OUTER_INST(double2)
+
+}  // namespace helm

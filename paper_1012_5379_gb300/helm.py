@@ -1,0 +1,209 @@
+"""ctypes binding of libhelm.so (include/helm.h): argument marshalling only.
+
+Every computation runs in the library's sm_103a kernels; this module converts torch
+tensors to raw pointers and the current CUDA stream, and turns status codes into
+exceptions.  It raises ``HelmError`` if the library is missing instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhelm.so")
+
+HELM_OK = 0
+HELM_EINVAL = -1
+HELM_ENOMEM = -2
+HELM_ENOCONV = -3
+HELM_ENUMERIC = -4
+HELM_ETIMEOUT = -5
+HELM_ECUDA = -6
+HELM_EAGAIN = -7
+HELM_C64 = 1
+HELM_C128 = 2
+
+_STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ENOCONV", -4: "HELM_ENUMERIC",
+           -5: "HELM_ETIMEOUT", -6: "HELM_ECUDA", -7: "HELM_EAGAIN"}
+
+# names declared in include/helm.h (checked by the CPU test suite)
+EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_operator", "helm_solve",
+           "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_last_error")
+
+
+class HelmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class helm_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
+                ("theta_gamma", ctypes.c_double)]
+
+
+class helm_opts(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("s", ctypes.c_int), ("coarsest_n", ctypes.c_int),
+                ("precond_prec", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int)]
+
+
+class helm_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_res_est", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhelm.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise HelmError(HELM_ECUDA, f"{path} is missing: build it with `python -m paper_1012_5379_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.helm_setup.argtypes = [ctypes.POINTER(helm_grid), vp, dp, dp, ctypes.POINTER(helm_opts), vp,
+                               ctypes.POINTER(vp)]
+    lib.helm_setup.restype = ip
+    lib.helm_destroy.argtypes = [vp]
+    lib.helm_destroy.restype = None
+    lib.helm_precond_apply.argtypes = [vp, vp, vp, ip, vp]
+    lib.helm_precond_apply.restype = ip
+    lib.helm_apply_operator.argtypes = [vp, ip, vp, vp, ip, vp]
+    lib.helm_apply_operator.restype = ip
+    lib.helm_solve.argtypes = [vp, vp, vp, dp, ctypes.POINTER(helm_info), vp]
+    lib.helm_solve.restype = ip
+    lib.helm_solve_host.argtypes = [vp, vp, vp, dp, ctypes.POINTER(helm_info), vp]
+    lib.helm_solve_host.restype = ip
+    lib.helm_batch_solve.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp), dp,
+                                     ctypes.POINTER(helm_info), vp]
+    lib.helm_batch_solve.restype = ip
+    lib.helm_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.helm_workspace_bytes.restype = ip
+    lib.helm_levels.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
+    lib.helm_levels.restype = ip
+    lib.helm_last_error.argtypes = []
+    lib.helm_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code: int, allow=(HELM_OK,)) -> int:
+    if code not in allow:
+        raise HelmError(code, load().helm_last_error().decode())
+    return code
+
+
+def _stream(stream) -> int:
+    if stream is not None:
+        return int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t) -> int:
+    return t if isinstance(t, int) else t.data_ptr()
+
+
+@dataclass
+class Info:
+    iters: int
+    restarts: int
+    rel_res_est: float
+    rel_res_true: float
+    status: int
+
+    @staticmethod
+    def of(ci: helm_info) -> "Info":
+        return Info(ci.iters, ci.restarts, ci.rel_res_est, ci.rel_res_true, ci.status)
+
+
+class Handle:
+    """One Helmholtz problem: grid, wavenumber, CSG angle, hierarchy and workspace
+    (helm_setup / helm_destroy)."""
+
+    def __init__(self, dim: int, n: int, theta_beta: float, k: Optional[float] = None, phi=None,
+                 theta_gamma: float = 0.5, ecs_frac: float = 0.125, nu1: int = 1, nu2: int = 1, s: int = 3,
+                 coarsest_n: int = 3, precision: str = "c64", restart: int = 0, maxit: int = 400, stream=None):
+        lib = load()
+        self.dim, self.n = dim, n
+        self.precision = precision
+        g = helm_grid(dim, n, ecs_frac, theta_gamma)
+        o = helm_opts(nu1, nu2, s, coarsest_n, HELM_C128 if precision == "c128" else HELM_C64, restart, maxit)
+        h = ctypes.c_void_p()
+        phi_ptr = None if phi is None else _ptr(phi)
+        self._phi = phi  # keep the caller's field alive during setup
+        _check(lib.helm_setup(ctypes.byref(g), phi_ptr, float(k if k is not None else 0.0), float(theta_beta),
+                              ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def ptr(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().helm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def levels(self) -> list:
+        n = ctypes.c_int()
+        sizes = (ctypes.c_int * 32)()
+        _check(load().helm_levels(self._h, ctypes.byref(n), sizes, 32))
+        return list(sizes[: n.value])
+
+    def workspace_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(load().helm_workspace_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def precond_apply(self, r, z, stream=None):
+        """z ~ (M^CSG)^{-1} r by one V-cycle (torch complex64/complex128 CUDA tensors)."""
+        prec = HELM_C128 if str(r.dtype).endswith("complex128") else HELM_C64
+        _check(load().helm_precond_apply(self._h, _ptr(r), _ptr(z), prec, _stream(stream)))
+        return z
+
+    def apply_operator(self, v, w, which: str = "M", stream=None):
+        prec = HELM_C128 if str(v.dtype).endswith("complex128") else HELM_C64
+        _check(load().helm_apply_operator(self._h, 1 if which == "H" else 0, _ptr(v), _ptr(w), prec,
+                                          _stream(stream)))
+        return w
+
+    def solve(self, b, x, tol: float, stream=None) -> Info:
+        """FGMRES solve of H x = b (complex128 CUDA tensors; x holds the initial guess)."""
+        ci = helm_info()
+        _check(load().helm_solve(self._h, _ptr(b), _ptr(x), float(tol), ctypes.byref(ci), _stream(stream)),
+               allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
+        return Info.of(ci)
+
+    def solve_host(self, b_host, x_host, tol: float, stream=None) -> Info:
+        """As solve, with host arrays (numpy complex128 or pinned torch tensors)."""
+        ci = helm_info()
+        bp = b_host.ctypes.data if hasattr(b_host, "ctypes") else _ptr(b_host)
+        xp = x_host.ctypes.data if hasattr(x_host, "ctypes") else _ptr(x_host)
+        _check(load().helm_solve_host(self._h, bp, xp, float(tol), ctypes.byref(ci), _stream(stream)),
+               allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
+        return Info.of(ci)
+
+
+def batch_solve(handles: Sequence[Handle], bs, xs, tol: float, stream=None):
+    """helm_batch_solve over several handles; returns a list of Info."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+    bp = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    infos = (helm_info * n)()
+    _check(load().helm_batch_solve(hs, n, bp, xp, float(tol), infos, _stream(stream)),
+           allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
+    return [Info.of(infos[i]) for i in range(n)]
