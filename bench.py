@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the GMRES(3)-smoothed CSG multigrid preconditioner inside the FP64
+flexible GMRES solve (arXiv:1012.5379), on GB300.
+
+Metric: V-cycle Mpts/s = fine-grid unknowns x V-cycles / second over whole solves to
+relative residual 1e-6 (one V-cycle per outer iteration).  A step is one pass of the
+whole hot path over one batch of synthetic input: the full FGMRES solve of the
+2D 1023^2, k = 160 problem with a unit-variance complex normal source for each CSG
+angle theta_beta in {0.1, 0.2, 0.3, 0.5} (complex64 V-cycle, FP64 outer).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: replicas only (each rank solves its own copy of the sweep; the only
+collectives are a barrier and the max-over-ranks time).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1012_5379_gb300 import inputs as I  # noqa: E402
+
+METRIC = "V-cycle Mpts/s"
+UNIT = "Mpts/s"
+TOL = 1e-6
+N = 1023
+K = 160.0
+BETAS = I.LARGE_2D_BETAS
+FP64_PEAK_TFLOPS = 1.25   # the profiling recipe's nominal GB300 FP64 rate (no measured figure exists)
+
+
+def workload_config():
+    return {"workload": "2D Helmholtz 1023^2 interior, k=160 (kh=0.156), unit-variance complex normal source "
+                        "(seed 1001), ECS layer 1/8 per side at 0.5 rad, CSG theta_beta swept over "
+                        "{0.1,0.2,0.3,0.5}; V(1,1) GMRES(3) multigrid in complex64 down to 3x3, FP64 FGMRES "
+                        "(no restart) to rel. residual 1e-6; one step = the four solves",
+            "n": N, "dim": 2, "k": K, "betas": list(BETAS), "tol": TOL, "levels": 9,
+            "l2": "flushed between steps (256 MiB write) outside the per-step event timing; the FGMRES "
+                  "basis (> 1 GB per solve) exceeds L2 anyway"}
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(", ") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        loaded = [v for v in sm if v > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kernel_class: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else null)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel_class)
+    except Exception:
+        return None
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for f in rec.get("sources", []):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return rec.get("dram_bytes_per_launch") if h.hexdigest() == rec.get("sources_sha256") else None
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1012_5379_gb300 import helm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    b_np = I.random_source(2, N, 1001)
+    b = torch.from_numpy(b_np).to(dev)
+    handles = [helm.Handle(2, N, tb, k=K, precision="c64", maxit=args.maxit) for tb in BETAS]
+    xs = [torch.zeros_like(b) for _ in BETAS]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        iters = []
+        for h, x in zip(handles, xs):
+            x.zero_()
+            info = h.solve(b, x, TOL)
+            if info.status != 0:
+                raise RuntimeError(f"solve did not converge: {info}")
+            iters.append(info.iters)
+        return iters
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up; the first warm-up step times every kernel class to find the dominant one
+    classes = {}
+    for w in range(args.warmup):
+        if w == 0:
+            helm.profile_begin("")
+        step()
+        if w == 0:
+            classes = helm.profile_end()
+    dominant = max(classes, key=lambda c: classes[c]["ms"]) if classes else "out.dots"
+
+    sampler = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = helm.launch_count()
+    helm.profile_begin(dominant)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    all_iters = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        all_iters.append(step())
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = helm.profile_end()
+    launches = helm.launch_count() - launches0
+    clocks = sampler.stop()
+    ms_steps = [a.elapsed_time(c) for a, c in ev]
+    ms_total = float(sum(ms_steps))
+    pts = float(N * N)
+    work = pts * sum(sum(i) for i in all_iters)
+    if world > 1:
+        t = torch.tensor([ms_total, work], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        ms_total, work = float(tmax[0].item()), float(t[1].item())
+    value = work / (ms_total * 1e-3) / 1e6
+
+    # roofline of the dominant kernel class, live from the timed region
+    pk = peaks()
+    d = prof.get(dominant, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+    nl = max(d["launches"], 1)
+    if dominant.startswith("out.dots") or dominant.startswith("out.vnew"):
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for(dominant), "kernel": dominant,
+                "peak_source": "recipe nominal FP64 (no measured FP64 figure)",
+                "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / nl,
+                "algorithmic_flops_per_launch": d["flops"] / nl}
+    else:
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+        peak = pk.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_for(dominant), "kernel": dominant,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "recipe fallback",
+                "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / nl,
+                "algorithmic_bytes_per_launch": d["bytes"] / nl}
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if args.e2e_steps > 0:
+        bh = torch.empty(b.shape, dtype=torch.complex128, pin_memory=True)
+        bh.copy_(torch.from_numpy(b_np))
+        xh = torch.empty_like(bh, pin_memory=True)
+        bh_np, xh_np = bh.numpy(), xh.numpy()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ework = 0.0
+        for _ in range(args.e2e_steps):
+            for h in handles:
+                info = h.solve_host(bh_np, xh_np, TOL)
+                ework += pts * info.iters
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([et, ework], dtype=torch.float64, device=dev)
+            dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+            et, ework = float(t[0].item()), float(t[1].item())
+        e2e = {"value": ework / et / 1e6, "unit": UNIT, "h2d_bytes_per_step": len(BETAS) * N * N * 16,
+               "d2h_bytes_per_step": len(BETAS) * N * N * 16, "steps": args.e2e_steps,
+               "api": "helm_solve_host"}
+
+    if rank != 0:
+        return None
+    iters = all_iters[-1]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+c128", "data": "synthetic",
+            "config": workload_config(), "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks, "iters_per_beta": dict(zip([str(t) for t in BETAS], iters)),
+            "solves_per_s": len(BETAS) * args.steps * world / (ms_total * 1e-3),
+            "ms_steps": ms_steps, "kernel_classes_warmup": classes}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+    else:
+        line["cpu_baseline"] = None
+    return line
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+def oracle_sample(theta_beta, iters):
+    """The oracle's FGMRES on the same problem, stopped after `iters` outer iterations
+    (one V-cycle each); returns (seconds, V-cycles)."""
+    import oracle as O
+    levels = O.build_hierarchy(2, N, theta_beta, I.THETA_GAMMA, I.ECS_FRAC, k=K)
+    b = I.random_source(2, N, 1001)
+    t0 = time.perf_counter()
+    _, info = O.fgmres(levels[0].apply_h, lambda v: O.vcycle(levels, v), b, tol=TOL, maxit=iters)
+    return time.perf_counter() - t0, info.iters
+
+
+def cpu_baseline(iters):
+    sec, its = oracle_sample(0.3, iters)
+    return {"value": N * N * its / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"NumPy FP64 oracle FGMRES on the same 1023^2 problem at theta_beta=0.3, stopped after "
+                      f"{its} outer iterations ({sec:.1f} s), single-threaded"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    its_per_step = max(1, args.cpu_iters // 2)
+    for _ in range(args.warmup):
+        oracle_sample(0.3, 1)
+    secs, work = 0.0, 0.0
+    for s in range(args.steps):
+        sec, its = oracle_sample(BETAS[s % len(BETAS)], its_per_step)
+        secs += sec
+        work += N * N * its
+    value = work / secs / 1e6
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the NumPy FP64 oracle FGMRES on the 1023^2 problem for one "
+                                       f"theta_beta, stopped after {its_per_step} outer iterations"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_precond(args):
+    """V-cycles only (helm_precond_apply), for profiler captures of the V-cycle
+    kernels on a chosen grid: --dim D --n N --reps R."""
+    import torch
+
+    from paper_1012_5379_gb300 import helm
+    dev = torch.device("cuda", 0)
+    n, dim = args.n, args.dim
+    k = 0.156 * (n + 1)
+    # maxit = 1: no FGMRES basis is allocated, the device holds the hierarchy only
+    h = helm.Handle(dim, n, 0.3, k=k, precision="c64", maxit=1)
+    r = torch.from_numpy(I.random_source(dim, n, 1001)).to(dev).to(torch.complex64)
+    z = torch.empty_like(r)
+    for _ in range(args.reps):
+        h.precond_apply(r, z)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.reps):
+        h.precond_apply(r, z)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.reps
+    print(json.dumps({"mode": "precond", "dim": dim, "n": n, "ms_per_vcycle": 1e3 * dt,
+                      "mpts_per_s": n ** dim / dt / 1e6}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--maxit", type=int, default=300)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["solve", "precond"], default="solve")
+    ap.add_argument("--dim", type=int, default=2)
+    ap.add_argument("--n", type=int, default=4095)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    if args.mode == "precond":
+        from paper_1012_5379_gb300 import build
+        build.build()
+        run_precond(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        from paper_1012_5379_gb300 import build
+        build.build()
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,25 @@ int helm_workspace_bytes(const helm_handle* h, size_t* bytes);
 /* Levels of the hierarchy and their sizes (sizes may be NULL). */
 int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes);
 
+/* Kernels this library has launched in the process so far (all handles, all
+ * streams).  The paper has no counterpart: this is launch accounting for
+ * benchmarks. */
+unsigned long long helm_launch_count(void);
+
+/* Start timing every kernel launch whose class name starts with `prefix` ("" = all
+ * classes) with CUDA events on its launching stream.  Class names: "vc.arnoldi.l0",
+ * "vc.restrict.l0", "vc.prolong.l0", "vc.update.l0" (finest level), the same with
+ * ".lc" (coarser grid-wide levels), "vc.coarse", "out.apply_h", "out.dots",
+ * "out.vnew", "out.cycle_end", "io.*".  Process-wide, not thread-safe; the paper has
+ * no counterpart (benchmark instrumentation). */
+int helm_profile_begin(const char* prefix);
+
+/* Stop timing, wait for the recorded events and write a JSON object
+ * {"class": {"launches": n, "ms": total, "bytes": algorithmic bytes, "flops": ...}}
+ * into buf (NUL-terminated, truncated to cap).  Returns HELM_OK, or HELM_EINVAL if
+ * buf is NULL or cap is 0. */
+int helm_profile_end(char* buf, size_t cap);
+
 /* Thread-local text of the last error on the calling thread ("" if none). */
 const char* helm_last_error(void);
 

@@ -5,11 +5,14 @@
 
 #include <exception>
 #include <new>
+#include <algorithm>
 #include <vector>
 #include <string>
 
 #include "../../include/helm.h"
 #include "engine.h"
+#include "profiler.h"
+#include <cstring>
 
 namespace helm {
 static thread_local std::string g_last_error;
@@ -151,6 +154,26 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes) {
   if (sizes)
     for (int i = 0; i < (int)lev.size() && i < max_sizes; ++i) sizes[i] = lev[i].n;
   return HELM_OK;
+}
+
+unsigned long long helm_launch_count(void) { return helm::launch_count(); }
+
+int helm_profile_begin(const char* prefix) {
+  HELM_GUARD({
+    helm::profile_begin(prefix ? prefix : "");
+    return HELM_OK;
+  })
+}
+
+int helm_profile_end(char* buf, size_t cap) {
+  HELM_GUARD({
+    if (!buf || cap == 0) { helm::set_error("buf must be non-NULL with cap > 0"); return HELM_EINVAL; }
+    std::string js = helm::profile_end();
+    const size_t n = std::min(js.size(), cap - 1);
+    std::memcpy(buf, js.data(), n);
+    buf[n] = 0;
+    return HELM_OK;
+  })
 }
 
 const char* helm_last_error(void) { return helm::g_last_error.c_str(); }

@@ -12,6 +12,7 @@
 #include <sstream>
 
 #include "geometry.h"
+#include "profiler.h"
 
 namespace helm {
 
@@ -304,7 +305,13 @@ struct Group {
   LevelDev<C>* dcoarse = nullptr;  // [prob][Lmax - tc]
   int nlev_c = 0;
   CoarseLU* dlu = nullptr;
-  struct Sub { int n = 0, cnt = 0, ntiles = 0, chunks = 1, m = 1; TileCfg cfg{8}; OuterDev<C>* d = nullptr; };
+  struct Sub {
+    int n = 0, cnt = 0, ntiles = 0, chunks = 1, m = 1;
+    TileCfg cfg{8};
+    OuterDev<C>* d = nullptr;
+    std::vector<Handle*> members;
+    double sum_j1 = 0;   // sum of (j + 1) over members at the last state read (profiling)
+  };
   std::vector<Sub> outer;
   LevelDev<C>* lev0 = nullptr;   // level-0 descriptors of all problems (single problem: [0])
   int lev0_nflat = 1;
@@ -403,6 +410,7 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
       si = (int)g->outer.size() - 1;
     }
     g->outer[si].cnt += 1;
+    g->outer[si].members.push_back(hs[p]);
     g->outer[si].m = std::max(g->outer[si].m, h.m);
     subs[si].push_back(make_outerdev<C>(h));
   }
@@ -431,31 +439,60 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
 }
 
 // One V(nu1, nu2) cycle from a zero guess on every problem of the group (Sec. 3.1).
+// Algorithmic bytes per launch count every vector the pass must read or write once
+// (E bytes per complex value), plus 4 bytes per point for a phi field.
 template <typename C>
 static void run_vcycle(const Group<C>& g, cudaStream_t st) {
   const int dim = g.dim;
+  const double E = sizeof(C);
+  const double cf = 1.0 / (dim == 3 ? 8.0 : 4.0);
   for (int t = 0; t < g.tc; ++t) {
     const auto& D = g.depth[t];
+    const double pts = (double)D.cnt * (dim == 3 ? (double)(D.n + 1) * (D.n + 1) * (D.n + 1) : (double)(D.n + 1) * (D.n + 1));
+    const bool fine = (t == 0);
+    const double ph = g.hs[0]->has_phi ? 4.0 : 0.0;
     if (g.nu1 == 0) {
+      Launch L(fine ? "vc.restrict.l0" : "vc.restrict.lc", st, pts * E * (2.0 + cf), 0);
       launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, g.cfg, true, true, true, st);
       continue;
     }
     for (int sw = 0; sw < g.nu1; ++sw) {
-      for (int J = 1; J <= g.s; ++J) launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, g.cfg, sw == 0, true, st);
-      if (sw < g.nu1 - 1)
+      for (int J = 1; J <= g.s; ++J) {
+        Launch L(fine ? "vc.arnoldi.l0" : "vc.arnoldi.lc", st, pts * (E * (J + 1) + ph), pts * (8.0 * (2 * dim + 1) + 8.0 * J + 4));
+        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, g.cfg, sw == 0, true, st);
+      }
+      if (sw < g.nu1 - 1) {
+        Launch L(fine ? "vc.update.l0" : "vc.update.lc", st, pts * E * (g.s + 3.0 + (sw == 0 ? 0 : 1)), 0);
         launch_update_flat<C>(dim, UPD_RESIDUAL, D.d, D.cnt, D.nflat, sw == 0, 0, sw == 0, st);
-      else
+      } else {
+        Launch L(fine ? "vc.restrict.l0" : "vc.restrict.lc", st, pts * E * (g.s + 2.0 + cf + (sw == 0 ? 0 : 1)), 0);
         launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, g.cfg, sw == 0, sw == 0, false, st);
+      }
     }
   }
-  launch_coarse<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, st);
+  {
+    Launch L("vc.coarse", st, 0, 0);
+    launch_coarse<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, st);
+  }
   for (int t = g.tc - 1; t >= 0; --t) {
     const auto& D = g.depth[t];
-    launch_prolong<C>(dim, g.nu2 > 0, D.d, D.cnt, g.nu2 > 0 ? D.ntiles : D.nflat, g.cfg, st);
+    const double pts = (double)D.cnt * (dim == 3 ? (double)(D.n + 1) * (D.n + 1) * (D.n + 1) : (double)(D.n + 1) * (D.n + 1));
+    const bool fine = (t == 0);
+    const double ph = g.hs[0]->has_phi ? 4.0 : 0.0;
+    {
+      Launch L(fine ? "vc.prolong.l0" : "vc.prolong.lc", st,
+               g.nu2 > 0 ? pts * (E * (4.0 + cf) + ph) : pts * E * (2.0 + cf), 0);
+      launch_prolong<C>(dim, g.nu2 > 0, D.d, D.cnt, g.nu2 > 0 ? D.ntiles : D.nflat, g.cfg, st);
+    }
     for (int sw = 0; sw < g.nu2; ++sw) {
       const bool last = (sw == g.nu2 - 1);
-      for (int J = 1; J <= g.s; ++J)
-        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, g.cfg, false, J < g.s || !last, st);
+      for (int J = 1; J <= g.s; ++J) {
+        const bool store = J < g.s || !last;
+        Launch L(fine ? "vc.arnoldi.l0" : "vc.arnoldi.lc", st, pts * (E * (J + (store ? 1 : 0)) + ph),
+                 pts * (8.0 * (2 * dim + 1) + 8.0 * J + 4));
+        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, g.cfg, false, store, st);
+      }
+      Launch L(fine ? "vc.update.l0" : "vc.update.lc", st, pts * E * (last ? g.s + 2.0 : g.s + 4.0), 0);
       launch_update_flat<C>(dim, last ? UPD_XONLY : UPD_RESIDUAL, D.d, D.cnt, D.nflat, false, 1, false, st);
     }
   }
@@ -484,9 +521,15 @@ static int precond_apply_t(Handle* h, const void* r, void* z, int prec, cudaStre
   int rc;
   Group<C>* g = cached_group<C>(h, st, &rc);
   if (!g) return rc;
-  launch_load_input<C>(h->dim, g->lev0, g->lev0_nflat, r, prec, st);
+  {
+    Launch L("io.load", st, 0, 0);
+    launch_load_input<C>(h->dim, g->lev0, g->lev0_nflat, r, prec, st);
+  }
   run_vcycle<C>(*g, st);
-  launch_store_output<C>(h->dim, h->n, g->lev0, z, prec, st);
+  {
+    Launch L("io.store", st, 0, 0);
+    launch_store_output<C>(h->dim, h->n, g->lev0, z, prec, st);
+  }
   CUDA_TRY(cudaGetLastError());
   return HELM_OK;
 }
@@ -502,24 +545,46 @@ int apply_operator(Handle* h, int which, const void* v, void* w, int prec, cudaS
   if (prec != HELM_C64 && prec != HELM_C128) { set_error("prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
   const HostLevel& L0 = h->lev[0];
   const double2* c = which == 1 ? h->hcoef : L0.coef64;
+  Launch L("io.apply", st, 0, 0);
   apply_operator_dense(h->dim, h->n, c, c + h->n, c + 2 * h->n, L0.phi, L0.phic, v, w, prec, st);
   CUDA_TRY(cudaGetLastError());
   return HELM_OK;
 }
 
 // ------------------------------------------------------------------ FGMRES driver
+// Outer FP64 kernels: bytes and flops per point of each pass (j+1 basis vectors).
+template <typename C>
+static double sub_points(const typename Group<C>::Sub& o, int dim) {
+  const double P = o.n + 1;
+  return (double)o.cnt * (dim == 3 ? P * P * P : P * P);
+}
+
 template <typename C>
 static void run_iteration(const Group<C>& g, cudaStream_t st) {
   run_vcycle<C>(g, st);
-  for (const auto& o : g.outer) outer_apply_h<C>(g.dim, o.d, o.cnt, o.ntiles, o.cfg, st);
-  for (const auto& o : g.outer) outer_dots<C>(o.d, o.cnt, o.chunks, o.m, st);
-  for (const auto& o : g.outer) outer_vnew<C>(o.d, o.cnt, o.chunks, o.m, false, st);
+  const double E = sizeof(C);
+  for (const auto& o : g.outer) {
+    Launch L("out.apply_h", st, sub_points<C>(o, g.dim) * (16.0 + 2 * E + (g.hs[0]->has_phi ? 4.0 : 0.0)),
+             sub_points<C>(o, g.dim) * (8.0 * (2 * g.dim + 1) + 4));
+    outer_apply_h<C>(g.dim, o.d, o.cnt, o.ntiles, o.cfg, st);
+  }
+  for (const auto& o : g.outer) {
+    const double pts1 = sub_points<C>(o, g.dim) / o.cnt;
+    Launch L("out.dots", st, pts1 * 16.0 * (o.sum_j1 + o.cnt), pts1 * 8.0 * o.sum_j1);
+    outer_dots<C>(o.d, o.cnt, o.chunks, o.m, st);
+  }
+  for (const auto& o : g.outer) {
+    const double pts1 = sub_points<C>(o, g.dim) / o.cnt;
+    Launch L("out.vnew", st, pts1 * (16.0 * (o.sum_j1 + 2 * o.cnt) + E * o.cnt), pts1 * 8.0 * (o.sum_j1 + o.cnt));
+    outer_vnew<C>(o.d, o.cnt, o.chunks, o.m, false, st);
+  }
 }
 
 // Cycle end (acts only on problems whose cycle ended): y = R^{-1} g, x += Z y, true
 // residual, and v_0 of the next cycle.
 template <typename C>
 static void run_cycle_end(const Group<C>& g, cudaStream_t st) {
+  Launch L("out.cycle_end", st, 0, 0, 4 * (int)g.outer.size());
   for (const auto& o : g.outer) outer_backsolve<C>(o.d, o.cnt, st);
   for (const auto& o : g.outer) outer_solution<C>(o.d, o.cnt, o.chunks, o.m, st);
   for (const auto& o : g.outer) outer_residual<C>(g.dim, o.d, o.cnt, o.ntiles, o.cfg, st);
@@ -532,8 +597,11 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
   // inputs and state
   for (int p = 0; p < count; ++p) {
     Handle* h = hs[p];
-    convert_dense_to_padded_c128(h->dim, h->n, (const double2*)b[p], h->bpad, st);
-    convert_dense_to_padded_c128(h->dim, h->n, (const double2*)x[p], h->xpad, st);
+    {
+      Launch L("io.convert", st, 0, 0, 2);
+      convert_dense_to_padded_c128(h->dim, h->n, (const double2*)b[p], h->bpad, st);
+      convert_dense_to_padded_c128(h->dim, h->n, (const double2*)x[p], h->xpad, st);
+    }
     OuterState s0;
     std::memset(&s0, 0, sizeof(s0));
     s0.m = h->m;
@@ -579,6 +647,11 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
       active = still;
       TRY(rebuild());
     }
+    for (int p = 0; p < count; ++p) hs[p]->last_j = host[p].j;
+    for (auto& o : g->outer) {
+      o.sum_j1 = 0;
+      for (Handle* m : o.members) o.sum_j1 += m->last_j + 1;
+    }
     run_iteration<C>(*g, st);
     run_cycle_end<C>(*g, st);
     CUDA_TRY(cudaGetLastError());
@@ -592,6 +665,7 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
       const size_t npts = h->dim == 3 ? (size_t)h->n * h->n * h->n : (size_t)h->n * h->n;
       CUDA_TRY(cudaMemsetAsync(x[p], 0, npts * sizeof(double2), st));
     } else {
+      Launch L("io.convert", st, 0, 0);
       convert_padded_to_dense_c128(h->dim, h->n, h->xpad, (double2*)x[p], st);
     }
     int status = s.done == 1 ? HELM_OK : (s.done == 3 ? HELM_ENUMERIC : HELM_ENOCONV);

@@ -58,6 +58,7 @@ struct Handle {
   OuterState* st = nullptr;
   int chunks = 1;
   int ntiles0 = 1;
+  int last_j = 0;              // outer iteration index at the last state read
   size_t bytes = 0;
   std::vector<void*> allocs;
   void* group_cache = nullptr;   // single-problem group (engine-owned)

@@ -31,7 +31,8 @@ _STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ENOCONV
 
 # names declared in include/helm.h (checked by the CPU test suite)
 EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_operator", "helm_solve",
-           "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_last_error")
+           "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_last_error",
+           "helm_launch_count", "helm_profile_begin", "helm_profile_end")
 
 
 class HelmError(RuntimeError):
@@ -89,6 +90,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_levels.restype = ip
     lib.helm_last_error.argtypes = []
     lib.helm_last_error.restype = ctypes.c_char_p
+    lib.helm_launch_count.argtypes = []
+    lib.helm_launch_count.restype = ctypes.c_ulonglong
+    lib.helm_profile_begin.argtypes = [ctypes.c_char_p]
+    lib.helm_profile_begin.restype = ip
+    lib.helm_profile_end.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.helm_profile_end.restype = ip
     _lib = lib
     return lib
 
@@ -195,6 +202,23 @@ class Handle:
         _check(load().helm_solve_host(self._h, bp, xp, float(tol), ctypes.byref(ci), _stream(stream)),
                allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
         return Info.of(ci)
+
+
+def launch_count() -> int:
+    """Kernels launched by libhelm.so so far in this process."""
+    return int(load().helm_launch_count())
+
+
+def profile_begin(prefix: str = "") -> None:
+    _check(load().helm_profile_begin(prefix.encode()))
+
+
+def profile_end() -> dict:
+    """Per-class launches, total CUDA-event milliseconds, algorithmic bytes, flops."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().helm_profile_end(buf, len(buf)))
+    return json.loads(buf.value.decode())
 
 
 def batch_solve(handles: Sequence[Handle], bs, xs, tol: float, stream=None):
