@@ -146,6 +146,31 @@ int helm_workspace_bytes(const helm_handle* h, size_t* bytes);
 /* Levels of the hierarchy and their sizes (sizes may be NULL). */
 int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes);
 
+/* One V(nu1, nu2) cycle, z ~ (M^CSG)^{-1} r, for a small grid without allocating any
+ * device memory.  For callers that cannot let a library call cudaMalloc: programs
+ * whose device memory is reserved up front by a pooling allocator, and
+ * latency-critical loops that cannot afford the implicit device synchronisation of
+ * cudaMalloc/cudaFree.  The paper has no counterpart: this is an interface variant
+ * of helm_precond_apply.
+ *   grid, theta_beta, opts: as for helm_setup (constant wavenumber k only; opts may be
+ *     NULL; restart and maxit are ignored; precond_prec selects the arithmetic).
+ *   r, z: device arrays of n^dim complex numbers in precision `prec`, natural order.
+ * All working memory lives in one fixed 4 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits.  Grids whose
+ * hierarchy does not fit are rejected with HELM_EINVAL and a message giving the
+ * bytes needed: 2D n <= 127 and 3D n <= 31 fit in HELM_C64, 2D n <= 127 and 3D n <= 15
+ * in HELM_C128; the coarsest level may hold at most 32 unknowns.
+ * The first call on a device resolves the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  Each
+ * call clears the array, copies a few kilobytes of set-up data from host stack memory
+ * (which synchronises `stream`) and enqueues three kernels on `stream`.  Every call
+ * shares the one array: calls whose kernels overlap on the GPU (other streams, other
+ * host threads) race and corrupt each other; serialise them on one stream.
+ * The whole cycle runs in a single CTA, so it is meant for small grids. */
+int helm_precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta,
+                               const helm_opts* opts, const void* r, void* z, int prec,
+                               void* stream);
+
 /* Kernels this library has launched in the process so far (all handles, all
  * streams).  The paper has no counterpart: this is launch accounting for
  * benchmarks. */

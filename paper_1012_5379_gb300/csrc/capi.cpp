@@ -156,6 +156,11 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes) {
   return HELM_OK;
 }
 
+int helm_precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, const helm_opts* opts,
+                               const void* r, void* z, int prec, void* stream) {
+  HELM_GUARD({ return helm::precond_apply_noalloc(grid, k, theta_beta, opts, r, z, prec, (cudaStream_t)stream); })
+}
+
 unsigned long long helm_launch_count(void) { return helm::launch_count(); }
 
 int helm_profile_begin(const char* prefix) {

@@ -69,6 +69,8 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
                  cudaStream_t st, Handle** out);
 int precond_apply(Handle* h, const void* r, void* z, int prec, cudaStream_t st);
 int apply_operator(Handle* h, int which, const void* v, void* w, int prec, cudaStream_t st);
+int precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, const helm_opts* opts,
+                          const void* r, void* z, int prec, cudaStream_t st);
 int solve_group(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
                 helm_info* infos, cudaStream_t st);
 

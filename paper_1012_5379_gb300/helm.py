@@ -32,7 +32,7 @@ _STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ENOCONV
 # names declared in include/helm.h (checked by the CPU test suite)
 EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_operator", "helm_solve",
            "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_last_error",
-           "helm_launch_count", "helm_profile_begin", "helm_profile_end")
+           "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc")
 
 
 class HelmError(RuntimeError):
@@ -90,6 +90,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_levels.restype = ip
     lib.helm_last_error.argtypes = []
     lib.helm_last_error.restype = ctypes.c_char_p
+    lib.helm_precond_apply_noalloc.argtypes = [ctypes.POINTER(helm_grid), dp, dp, ctypes.POINTER(helm_opts), vp, vp,
+                                               ip, vp]
+    lib.helm_precond_apply_noalloc.restype = ip
     lib.helm_launch_count.argtypes = []
     lib.helm_launch_count.restype = ctypes.c_ulonglong
     lib.helm_profile_begin.argtypes = [ctypes.c_char_p]
@@ -202,6 +205,20 @@ class Handle:
         _check(load().helm_solve_host(self._h, bp, xp, float(tol), ctypes.byref(ci), _stream(stream)),
                allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
         return Info.of(ci)
+
+
+def precond_apply_noalloc(dim: int, n: int, theta_beta: float, k: float, r, z, theta_gamma: float = 0.5,
+                          ecs_frac: float = 0.125, nu1: int = 1, nu2: int = 1, s: int = 3, precision: str = "c64",
+                          stream=None):
+    """One V-cycle on a small grid through helm_precond_apply_noalloc: the library
+    allocates no device memory for it (its working memory is a fixed array inside the
+    library).  r, z: torch complex64/complex128 CUDA tensors of shape (n,)*dim."""
+    g = helm_grid(dim, n, ecs_frac, theta_gamma)
+    o = helm_opts(nu1, nu2, s, 3, HELM_C128 if precision == "c128" else HELM_C64, 0, 0)
+    prec = HELM_C128 if str(r.dtype).endswith("complex128") else HELM_C64
+    _check(load().helm_precond_apply_noalloc(ctypes.byref(g), float(k), float(theta_beta), ctypes.byref(o),
+                                             _ptr(r), _ptr(z), prec, _stream(stream)))
+    return z
 
 
 def launch_count() -> int:
