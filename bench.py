@@ -49,7 +49,7 @@ def workload_config():
     return {"workload": "2D Helmholtz 1023^2 interior, k=160 (kh=0.156), unit-variance complex normal source "
                         "(seed 1001), ECS layer 1/8 per side at 0.5 rad, CSG theta_beta swept over "
                         "{0.1,0.2,0.3,0.5}; V(1,1) GMRES(3) multigrid in complex64 down to 3x3, FP64 FGMRES "
-                        "(no restart) to rel. residual 1e-6; one step = the four solves",
+                        "(no restart) to rel. residual 1e-6; one step = the four solves, batched",
             "n": N, "dim": 2, "k": K, "betas": list(BETAS), "tol": TOL, "levels": 9,
             "l2": "flushed between steps (256 MiB write) outside the per-step event timing; the FGMRES "
                   "basis (> 1 GB per solve) exceeds L2 anyway"}
@@ -148,6 +148,16 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
     def step():
+        # the four independent theta_beta solves share every launch (helm_batch_solve)
+        for x in xs:
+            x.zero_()
+        infos = helm.batch_solve(handles, [b] * len(handles), xs, TOL)
+        for info in infos:
+            if info.status != 0:
+                raise RuntimeError(f"solve did not converge: {info}")
+        return [info.iters for info in infos]
+
+    def step_sequential():
         iters = []
         for h, x in zip(handles, xs):
             x.zero_()
@@ -221,21 +231,34 @@ def run_ours(args, rank, world, local_rank):
                 "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / nl,
                 "algorithmic_bytes_per_launch": d["bytes"] / nl}
 
+    # the same step solved one problem at a time (context: what batching buys)
+    seq = None
+    if args.sequential_steps > 0:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        swork = 0.0
+        for _ in range(args.sequential_steps):
+            swork += pts * sum(step_sequential())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq = {"value": swork / (e0.elapsed_time(e1) * 1e-3) / 1e6, "unit": UNIT,
+               "ms_per_step": e0.elapsed_time(e1) / args.sequential_steps, "api": "helm_solve, one problem at a time"}
+
     # end to end through the public API with host buffers (pinned)
     e2e = None
     if args.e2e_steps > 0:
         bh = torch.empty(b.shape, dtype=torch.complex128, pin_memory=True)
         bh.copy_(torch.from_numpy(b_np))
-        xh = torch.empty_like(bh, pin_memory=True)
-        bh_np, xh_np = bh.numpy(), xh.numpy()
+        xhs = [torch.empty_like(bh, pin_memory=True) for _ in handles]
+        bh_np, xh_nps = bh.numpy(), [x.numpy() for x in xhs]
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ework = 0.0
         for _ in range(args.e2e_steps):
-            for h in handles:
-                info = h.solve_host(bh_np, xh_np, TOL)
-                ework += pts * info.iters
+            infos = helm.batch_solve_host(handles, [bh_np] * len(handles), xh_nps, TOL)
+            ework += pts * sum(i.iters for i in infos)
         torch.cuda.synchronize()
         et = time.perf_counter() - t0
         if world > 1:
@@ -245,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
             et, ework = float(t[0].item()), float(t[1].item())
         e2e = {"value": ework / et / 1e6, "unit": UNIT, "h2d_bytes_per_step": len(BETAS) * N * N * 16,
                "d2h_bytes_per_step": len(BETAS) * N * N * 16, "steps": args.e2e_steps,
-               "api": "helm_solve_host"}
+               "api": "helm_batch_solve_host"}
 
     if rank != 0:
         return None
@@ -256,7 +279,8 @@ def run_ours(args, rank, world, local_rank):
             "config": workload_config(), "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "iters_per_beta": dict(zip([str(t) for t in BETAS], iters)),
             "solves_per_s": len(BETAS) * args.steps * world / (ms_total * 1e-3),
-            "ms_steps": ms_steps, "kernel_classes_warmup": classes}
+            "ms_steps": ms_steps, "kernel_classes_warmup": classes, "sequential": seq,
+            "solve_mode": "batched: the four theta_beta solves of a step share every launch (helm_batch_solve)"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
     else:
@@ -326,8 +350,15 @@ def run_precond(args):
         h.precond_apply(r, z)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.reps
+    helm.profile_begin("")
+    for _ in range(args.reps):
+        h.precond_apply(r, z)
+    classes = helm.profile_end()
     print(json.dumps({"mode": "precond", "dim": dim, "n": n, "ms_per_vcycle": 1e3 * dt,
-                      "mpts_per_s": n ** dim / dt / 1e6}), flush=True)
+                      "mpts_per_s": n ** dim / dt / 1e6,
+                      "classes_us_per_vcycle": {c: round(1e3 * v["ms"] / args.reps, 1) for c, v in classes.items()},
+                      "launches_per_vcycle": {c: v["launches"] // args.reps for c, v in classes.items()}}),
+          flush=True)
 
 
 def main():
@@ -338,6 +369,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--maxit", type=int, default=300)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--sequential-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["solve", "precond"], default="solve")

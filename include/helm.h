@@ -140,6 +140,13 @@ int helm_solve_host(helm_handle* h, const double* b_host, double* x_host, double
 int helm_batch_solve(helm_handle* const* hs, int count, const double* const* b,
                      double* const* x, double tol, helm_info* infos, void* stream);
 
+/* As helm_batch_solve, but b[i] and x[i] are HOST arrays: every b[i] is copied to
+ * the device, the problems are solved together from zero initial guesses, and
+ * every solution is copied back into x[i].  Allocates (and frees) device staging
+ * buffers for the vectors. */
+int helm_batch_solve_host(helm_handle* const* hs, int count, const double* const* b_host,
+                          double* const* x_host, double tol, helm_info* infos, void* stream);
+
 /* Bytes of device memory the handle holds. */
 int helm_workspace_bytes(const helm_handle* h, size_t* bytes);
 

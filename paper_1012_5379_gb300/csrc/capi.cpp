@@ -141,6 +141,53 @@ int helm_batch_solve(helm_handle* const* hs, int count, const double* const* b, 
   })
 }
 
+int helm_batch_solve_host(helm_handle* const* hs, int count, const double* const* b_host, double* const* x_host,
+                          double tol, helm_info* infos, void* stream) {
+  HELM_GUARD({
+    if (!hs || count <= 0 || !b_host || !x_host) { helm::set_error("empty batch or NULL arrays"); return HELM_EINVAL; }
+    std::vector<Handle*> inner(count);
+    std::vector<size_t> off(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+      if (!hs[i] || !b_host[i] || !x_host[i]) { helm::set_error("NULL handle or vector in batch"); return HELM_EINVAL; }
+      inner[i] = hs[i]->h;
+      const size_t n = inner[i]->n;
+      off[i + 1] = off[i] + (inner[i]->dim == 3 ? n * n * n : n * n) * 2;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double* dev = nullptr;
+    if (cudaMalloc(&dev, 2 * off[count] * sizeof(double)) != cudaSuccess) {
+      helm::set_error("device allocation for host batch failed");
+      return HELM_ENOMEM;
+    }
+    std::vector<const double*> db(count);
+    std::vector<double*> dx(count);
+    int rc = HELM_OK;
+    for (int i = 0; i < count && rc == HELM_OK; ++i) {
+      db[i] = dev + off[i];
+      dx[i] = dev + off[count] + off[i];
+      const size_t bytes = (off[i + 1] - off[i]) * sizeof(double);
+      if (cudaMemcpyAsync((void*)db[i], b_host[i], bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemsetAsync(dx[i], 0, bytes, st) != cudaSuccess) {
+        helm::set_error("host to device copy failed");
+        rc = HELM_ECUDA;
+      }
+    }
+    if (rc == HELM_OK) {
+      rc = helm::solve_group(inner.data(), count, db.data(), dx.data(), tol, infos, st);
+      if (rc == HELM_OK || rc == HELM_ENOCONV || rc == HELM_ENUMERIC) {
+        for (int i = 0; i < count; ++i)
+          if (cudaMemcpyAsync(x_host[i], dx[i], (off[i + 1] - off[i]) * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess)
+            rc = HELM_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = HELM_ECUDA;
+        if (rc == HELM_ECUDA) helm::set_error("device to host copy failed");
+      }
+    }
+    cudaFree(dev);
+    return rc;
+  })
+}
+
 int helm_workspace_bytes(const helm_handle* h, size_t* bytes) {
   if (!h || !bytes) { helm::set_error("NULL argument"); return HELM_EINVAL; }
   *bytes = h->h->bytes;

@@ -1,8 +1,9 @@
 // Device helpers: complex arithmetic on float2/double2, deterministic block and
-// grid reductions, and the FP64 scalar algebra of one GMRES(s) smoothing sweep.
+// grid reductions, and the scalar algebra of one GMRES(s) smoothing sweep.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include "helm_internal.h"
 
 namespace helm {
@@ -35,6 +36,13 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// c - a * b in four FMAs
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
 }
 // conj(a) * b + c
 __device__ __forceinline__ float2 cdotacc(float2 a, float2 b, float2 c) {
@@ -75,14 +83,22 @@ __device__ __forceinline__ double2 shfl_down_c(double2 v, int d) {
   return make_double2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
 }
 
+// ------------------------------------------------------------------ dependent launch
+// Programmatic dependent launch: a kernel lets the next kernel in the stream start
+// launching at once (its CTAs then run their prologue), and waits for the previous
+// kernel's completion and memory before reading anything that kernel wrote.  Both
+// are no-ops for a kernel launched without the programmatic attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ int flat_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
 __device__ __forceinline__ int block_threads() { return blockDim.x * blockDim.y * blockDim.z; }
 
 // Sum NV doubles over the block in a fixed order; thread 0 ends with the totals.
 // `sm` needs 32 * NV doubles.  Every thread of the block must call it.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* sm) {
   const int tid = flat_tid(), lane = tid & 31, warp = tid >> 5, nw = (block_threads() + 31) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
@@ -94,7 +110,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = lane < nw ? sm[lane * NV + i] : 0.0;
+    for (int i = 0; i < NV; ++i) v[i] = lane < nw ? sm[lane * NV + i] : (T)0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -107,11 +123,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
 // is the last of `ntiles` blocks of its problem to arrive.  If so, the returned
 // block reduces all slots in a fixed order (independent of arrival order) and
 // thread 0 holds the totals in `tot`.
-template <int NV>
-__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, int tile, int ntiles,
-                                              unsigned int* counter, double* sm, double (&tot)[NV]) {
+// Partial slots, the block sums and the final sum are all in T: FP32 for the
+// complex64 V-cycle, FP64 elsewhere.
+template <int NV, typename T>
+__device__ __forceinline__ bool grid_sum_last(T (&v)[NV], void* partv, int tile, int ntiles,
+                                              unsigned int* counter, T* sm, T (&tot)[NV]) {
   __shared__ int s_last;
-  block_sum<NV>(v, sm);
+  T* part = reinterpret_cast<T*>(partv);
+  block_sum<NV, T>(v, sm);
   const int tid = flat_tid();
   if (tid == 0) {
 #pragma unroll
@@ -123,13 +142,13 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, int
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  double acc[NV];
+  T acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int i = 0; i < NV; ++i) acc[i] = (T)0;
   for (int t = tid; t < ntiles; t += block_threads())
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (size_t)t * NPART + i);
-  block_sum<NV>(acc, sm);
+  block_sum<NV, T>(acc, sm);
 #pragma unroll
   for (int i = 0; i < NV; ++i) tot[i] = acc[i];
   if (tid == 0) *counter = 0u;
@@ -139,118 +158,188 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, int
 // ------------------------------------------------------------------ sweep algebra
 // Breakdown threshold on ||w||^2 / ||p_J||^2 after projection: below it the
 // Pythagorean norm is rounding noise of the working precision.
-template <typename C> struct SweepTau;
-template <> struct SweepTau<float2> { static constexpr double v = 1e-5; };
-template <> struct SweepTau<double2> { static constexpr double v = 1e-24; };
+template <typename T> struct SweepTau;
+template <> struct SweepTau<float> { static constexpr float v = 1e-5f; };
+template <> struct SweepTau<double> { static constexpr double v = 1e-24; };
 
-// Start a sweep whose initial residual R_0 has squared norm beta2.
-__device__ inline void sweep_begin(SweepScalars* sc, double beta2, int s) {
+__device__ __forceinline__ float2 fconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ double2 fconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ float fabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double fabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float2 fdiv(float2 a, float2 b) {
+  const float d = 1.0f / (b.x * b.x + b.y * b.y);
+  return make_float2((a.x * b.x + a.y * b.y) * d, (a.y * b.x - a.x * b.y) * d);
+}
+__device__ __forceinline__ double2 fdiv(double2 a, double2 b) { return ddiv(a, b); }
+
+template <typename T>
+__device__ __forceinline__ int sweep_words() {
+  return (int)(offsetof(SweepScalarsT<T>, counter) / sizeof(int));
+}
+
+// Start a sweep whose initial residual R_0 has squared norm beta2.  Only the fields
+// a sweep reads before writing are set (one thread).
+template <typename T>
+__device__ inline void sweep_begin(SweepScalarsT<T>* sc, T beta2, int s) {
+  typedef typename CplxOf<T>::T CR;
   sc->s = s;
   sc->beta2 = beta2;
-  for (int i = 0; i <= SMAX; ++i) {
-    sc->xcoef[i] = make_double2(0, 0);
-    sc->rcoef[i] = make_double2(0, 0);
-    for (int j = 0; j <= SMAX; ++j) {
-      sc->G[i][j] = make_double2(0, 0);
-      sc->Cf[i][j] = make_double2(0, 0);
-    }
-    for (int j = 0; j < SMAX; ++j) sc->Hh[i][j] = make_double2(0, 0);
-  }
-  sc->rcoef[0] = make_double2(1, 0);
+  sc->rcoef[0] = CT<CR>::make(1, 0);
   if (!isfinite(beta2)) {
     sc->status = 1;
     sc->m = 0;
     return;
   }
-  if (!(beta2 > 0.0)) {
+  if (!(beta2 > (T)0)) {
     sc->m = 0;
     return;
   }
   sc->m = s;
-  sc->G[0][0] = make_double2(beta2, 0);
-  sc->Cf[1][0] = make_double2(1.0 / sqrt(beta2), 0);
+  sc->G[0][0] = CT<CR>::make(beta2, 0);
+  sc->Cf[1][0] = CT<CR>::make((T)1 / sqrt(beta2), 0);
 }
 
-// min || beta e1 - Hbar y || for the (m+1) x m Hessenberg matrix, complex Givens.
-__device__ inline void sweep_lstsq(const double2 (*Hh)[SMAX], int m, double beta, double2* y) {
-  double2 R[SMAX + 1][SMAX];
-  double2 g[SMAX + 1];
-  for (int i = 0; i <= m; ++i) {
-    g[i] = make_double2(i == 0 ? beta : 0.0, 0);
-    for (int j = 0; j < m; ++j) R[i][j] = Hh[i][j];
+// min || beta e1 - Hbar y || for the (M+1) x M Hessenberg matrix, complex Givens.
+// M is a compile-time constant so every array stays in registers.
+template <typename T, int M>
+__device__ __forceinline__ void sweep_lstsq(const typename CplxOf<T>::T (*Hh)[SMAX], T beta,
+                                            typename CplxOf<T>::T* y) {
+  typedef typename CplxOf<T>::T CR;
+  CR R[M + 1][M];
+  CR g[M + 1];
+#pragma unroll
+  for (int i = 0; i <= M; ++i) {
+    g[i] = CT<CR>::make(i == 0 ? beta : (T)0, 0);
+#pragma unroll
+    for (int j = 0; j < M; ++j) R[i][j] = (i <= j + 1) ? Hh[i][j] : CT<CR>::make(0, 0);
   }
-  for (int j = 0; j < m; ++j) {
-    double2 a = R[j][j], b = R[j + 1][j];
-    double na = sqrt(dabs2(a)), nb = sqrt(dabs2(b));
-    double r = hypot(na, nb);
-    double c;
-    double2 s;
-    if (r == 0.0) { c = 1.0; s = make_double2(0, 0); }
-    else if (na == 0.0) { c = 0.0; s = make_double2(1, 0); }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const CR a = R[j][j], b = R[j + 1][j];
+    const T na = sqrt(fabs2(a)), nb = sqrt(fabs2(b));
+    const T r = sqrt(na * na + nb * nb);
+    T c;
+    CR s;
+    if (r == (T)0) { c = 1; s = CT<CR>::make(0, 0); }
+    else if (na == (T)0) { c = 0; s = CT<CR>::make(1, 0); }
     else {
-      c = na / r;
-      double2 ph = make_double2(a.x / na, a.y / na);
-      s = cmul(ph, dconj(b));
-      s = make_double2(s.x / r, s.y / r);
+      const T inv_na = (T)1 / na, inv_r = (T)1 / r;
+      c = na * inv_r;
+      s = cmul(CT<CR>::make(a.x * inv_na, a.y * inv_na), fconj(b));
+      s = CT<CR>::make(s.x * inv_r, s.y * inv_r);
     }
-    for (int l = j; l < m; ++l) {
-      double2 t0 = R[j][l], t1 = R[j + 1][l];
-      R[j][l] = cadd(make_double2(c * t0.x, c * t0.y), cmul(s, t1));
-      R[j + 1][l] = csub(make_double2(c * t1.x, c * t1.y), cmul(dconj(s), t0));
+#pragma unroll
+    for (int l = j; l < M; ++l) {
+      const CR t0 = R[j][l], t1 = R[j + 1][l];
+      R[j][l] = cadd(CT<CR>::make(c * t0.x, c * t0.y), cmul(s, t1));
+      R[j + 1][l] = csub(CT<CR>::make(c * t1.x, c * t1.y), cmul(fconj(s), t0));
     }
-    double2 g0 = g[j];
-    g[j] = make_double2(c * g0.x, c * g0.y);
-    g[j + 1] = cmul(make_double2(-s.x, s.y), g0);  // -conj(s) g0
+    const CR g0 = g[j];
+    g[j] = CT<CR>::make(c * g0.x, c * g0.y);
+    g[j + 1] = cmul(CT<CR>::make(-s.x, s.y), g0);  // -conj(s) g0
   }
-  for (int j = m - 1; j >= 0; --j) {
-    double2 acc = g[j];
-    for (int l = j + 1; l < m; ++l) acc = csub(acc, cmul(R[j][l], y[l]));
-    y[j] = (dabs2(R[j][j]) > 0.0) ? ddiv(acc, R[j][j]) : make_double2(0, 0);
+#pragma unroll
+  for (int j = M - 1; j >= 0; --j) {
+    CR acc = g[j];
+#pragma unroll
+    for (int l = j + 1; l < M; ++l) acc = csub(acc, cmul(R[j][l], y[l]));
+    y[j] = (fabs2(R[j][j]) > (T)0) ? fdiv(acc, R[j][j]) : CT<CR>::make(0, 0);
   }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void sweep_finish(SweepScalarsT<T>* sc) {
+  typedef typename CplxOf<T>::T CR;
+  sc->m = M;
+  CR y[M];
+  sweep_lstsq<T, M>(sc->Hh, sqrt(sc->beta2), y);
+#pragma unroll
+  for (int k = 0; k <= SMAX; ++k) { sc->xcoef[k] = CT<CR>::make(0, 0); sc->rcoef[k] = CT<CR>::make(0, 0); }
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    CR acc = CT<CR>::make(0, 0);
+#pragma unroll
+    for (int jj = k + 1; jj <= M; ++jj) acc = cadd(acc, cmul(y[jj - 1], sc->Cf[jj][k]));
+    sc->xcoef[k] = acc;
+  }
+  sc->rcoef[0] = CT<CR>::make(1, 0);
+#pragma unroll
+  for (int jj = 1; jj <= M; ++jj) sc->rcoef[jj] = CT<CR>::make(-y[jj - 1].x, -y[jj - 1].y);
 }
 
 // After Arnoldi pass J: red[2k..2k+1] = <R_k, p_J> (k < J), red[2J] = ||p_J||^2.
-__device__ inline void sweep_after_pass(SweepScalars* sc, int J, const double* red, double tau) {
-  double2 g[SMAX];
+// Works on `sc` in any memory space (the kernels pass a shared-memory copy).
+template <typename T, int J>
+__device__ __forceinline__ void sweep_after_pass(SweepScalarsT<T>* sc, const T* red) {
+  typedef typename CplxOf<T>::T CR;
+  CR g[J];
+#pragma unroll
   for (int k = 0; k < J; ++k) {
-    g[k] = make_double2(red[2 * k], red[2 * k + 1]);
+    g[k] = CT<CR>::make(red[2 * k], red[2 * k + 1]);
     sc->G[k][J] = g[k];
   }
-  const double gg = red[2 * J];
-  sc->G[J][J] = make_double2(gg, 0);
-  double2 h[SMAX + 1];
-  double hs = 0.0;
+  const T gg = red[2 * J];
+  sc->G[J][J] = CT<CR>::make(gg, 0);
+  CR h[J + 1];
+  T hs = 0;
+#pragma unroll
   for (int i = 1; i <= J; ++i) {
-    double2 acc = make_double2(0, 0);
-    for (int k = 0; k < i; ++k) acc = cadd(acc, cmul(dconj(sc->Cf[i][k]), g[k]));
+    CR acc = CT<CR>::make(0, 0);
+#pragma unroll
+    for (int k = 0; k < i; ++k) acc = cadd(acc, cmul(fconj(sc->Cf[i][k]), g[k]));
     h[i] = acc;
     sc->Hh[i - 1][J - 1] = acc;
-    hs += dabs2(acc);
+    hs += fabs2(acc);
   }
   if (!isfinite(gg) || !isfinite(hs)) sc->status = 1;
-  const double w2 = gg - hs;
-  const double hn = w2 > 0.0 ? sqrt(w2) : 0.0;
-  sc->Hh[J][J - 1] = make_double2(hn, 0);
-  const bool breakdown = !(w2 > tau * gg);
+  const T w2 = gg - hs;
+  const T hn = w2 > (T)0 ? sqrt(w2) : (T)0;
+  sc->Hh[J][J - 1] = CT<CR>::make(hn, 0);
+  const bool breakdown = !(w2 > SweepTau<T>::v * gg);
   if (breakdown || J == sc->s) {
-    const int m = J;
-    sc->m = m;
-    double2 y[SMAX];
-    sweep_lstsq(sc->Hh, m, sqrt(sc->beta2), y);
-    for (int k = 0; k <= SMAX; ++k) { sc->xcoef[k] = make_double2(0, 0); sc->rcoef[k] = make_double2(0, 0); }
-    for (int jj = 1; jj <= m; ++jj)
-      for (int k = 0; k < jj; ++k) sc->xcoef[k] = cadd(sc->xcoef[k], cmul(y[jj - 1], sc->Cf[jj][k]));
-    sc->rcoef[0] = make_double2(1, 0);
-    for (int jj = 1; jj <= m; ++jj) sc->rcoef[jj] = make_double2(-y[jj - 1].x, -y[jj - 1].y);
-  } else {
-    const double inv = 1.0 / hn;
+    sweep_finish<T, J>(sc);
+  } else if (J < SMAX) {
+    const T inv = (T)1 / hn;
+#pragma unroll
     for (int k = 0; k < J; ++k) {
-      double2 acc = make_double2(0, 0);
+      CR acc = CT<CR>::make(0, 0);
+#pragma unroll
       for (int i = k + 1; i <= J; ++i) acc = cadd(acc, cmul(h[i], sc->Cf[i][k]));
-      sc->Cf[J + 1][k] = make_double2(-acc.x * inv, -acc.y * inv);
+      sc->Cf[J + 1][k] = CT<CR>::make(-acc.x * inv, -acc.y * inv);
     }
-    sc->Cf[J + 1][J] = make_double2(inv, 0);
+    sc->Cf[J + 1][J] = CT<CR>::make(inv, 0);
   }
+}
+
+// Runtime-J dispatch (coarse single-CTA cycle).
+template <typename T>
+__device__ inline void sweep_after_pass_rt(SweepScalarsT<T>* sc, int J, const T* red) {
+  switch (J) {
+    case 1: sweep_after_pass<T, 1>(sc, red); break;
+    case 2: sweep_after_pass<T, 2>(sc, red); break;
+    case 3: sweep_after_pass<T, 3>(sc, red); break;
+    default: sweep_after_pass<T, 4>(sc, red); break;
+  }
+}
+
+// The last CTA of a pass: stage the sweep state in shared memory with one
+// cooperative copy, run the algebra on one thread, copy back.  Every thread of the
+// block must call it.
+template <typename T, int J>
+__device__ inline void block_sweep_after_pass(SweepScalarsT<T>* sc, const T* tot) {
+  __shared__ SweepScalarsT<T> ls;
+  __shared__ T stot[2 * SMAX + 1];
+  const int tid = flat_tid(), nt = block_threads();
+  int* gsrc = reinterpret_cast<int*>(sc);
+  int* sdst = reinterpret_cast<int*>(&ls);
+  const int words = sweep_words<T>();
+  for (int i = tid; i < words; i += nt) sdst[i] = __ldcg(gsrc + i);
+  if (tid == 0)
+    for (int i = 0; i <= 2 * J; ++i) stot[i] = tot[i];
+  __syncthreads();
+  if (tid == 0) sweep_after_pass<T, J>(&ls, stot);
+  __syncthreads();
+  for (int i = tid; i < words; i += nt) gsrc[i] = sdst[i];
 }
 
 }  // namespace helm

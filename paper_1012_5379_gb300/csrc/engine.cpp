@@ -117,7 +117,7 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     L.np = h->dim == 3 ? (size_t)L.P * L.P * L.P : (size_t)L.P * L.P;
     const TileCfg cfg = default_tiles(h->dim, L.P);
     if (l == 0) h->cfg = cfg;
-    L.ntiles = tiles_per_problem(h->dim, L.P, h->cfg);
+    L.ntiles = vtiles(h->dim, L.P);
     L.nflat = (int)std::max<size_t>(1, std::min<size_t>(1024, (L.np + 1023) / 1024));
     TRY(dev_alloc(h.get(), &L.b, L.np * eb));
     TRY(dev_alloc(h.get(), &L.xa, L.np * eb));
@@ -126,10 +126,10 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     for (int j = 0; j < h->s; ++j) TRY(dev_alloc(h.get(), &L.p[j], L.np * eb));
     for (void* v : {L.b, L.xa, L.xb, L.r0}) CUDA_TRY(cudaMemsetAsync(v, 0, L.np * eb, st));
     for (int j = 0; j < h->s; ++j) CUDA_TRY(cudaMemsetAsync(L.p[j], 0, L.np * eb, st));
-    TRY(dev_alloc(h.get(), &L.sc, sizeof(SweepScalars)));
-    CUDA_TRY(cudaMemsetAsync(L.sc, 0, sizeof(SweepScalars), st));
-    // partial-sum slots for the largest tile count any group configuration uses
-    const size_t nparts = std::max<size_t>(std::max(max_tiles(h->dim, L.P), L.nflat), 1);
+    const size_t scb = h->prec == HELM_C128 ? sizeof(SweepScalarsT<double>) : sizeof(SweepScalarsT<float>);
+    TRY(dev_alloc(h.get(), &L.sc, scb));
+    CUDA_TRY(cudaMemsetAsync(L.sc, 0, scb, st));
+    const size_t nparts = std::max<size_t>(std::max(L.ntiles, L.nflat), 1);
     TRY(dev_alloc(h.get(), &L.part, nparts * NPART * sizeof(double)));
     // coefficients of M on this level (rediscretisation with spacing 2^l h)
     std::vector<cplx> a, d, c;
@@ -248,7 +248,8 @@ static LevelDev<C> make_leveldev(const Handle& h, int l) {
   d.cc = (const C*)L.coef + 2 * L.n;
   d.phi = L.phi;
   d.phic = L.phic;
-  d.sc = L.sc;
+  typedef SweepScalarsT<typename RealOf<C>::T> SS;
+  d.sc = (SS*)L.sc;
   d.part = L.part;
   if (l + 1 < (int)h.lev.size()) {
     const HostLevel& Lc = h.lev[l + 1];
@@ -256,7 +257,7 @@ static LevelDev<C> make_leveldev(const Handle& h, int l) {
     d.Pc = Lc.P;
     d.bc = (C*)Lc.b;
     d.xcb = (const C*)Lc.xb;
-    d.scc = Lc.sc;
+    d.scc = (SS*)Lc.sc;
   }
   return d;
 }
@@ -291,7 +292,7 @@ static OuterDev<C> make_outerdev(const Handle& h) {
   o.vscale = h.vscale;
   o.part = h.opart;
   o.st = h.st;
-  o.sc0 = h.lev[0].sc;
+  o.sc0 = (SweepScalarsT<typename RealOf<C>::T>*)h.lev[0].sc;
   return o;
 }
 
@@ -300,10 +301,11 @@ struct Group {
   int dim = 2, nu1 = 1, nu2 = 1, s = 3, Lmax = 0, tc = 0, nprob = 0;
   TileCfg cfg{8};
   std::vector<Handle*> hs;
-  struct Depth { int n = 0, cnt = 0, ntiles = 0, nflat = 0; LevelDev<C>* d = nullptr; };
+  struct Depth { int n = 0, cnt = 0, ntiles = 0, nflat = 0; TileCfg cfg{8}; LevelDev<C>* d = nullptr; };
   std::vector<Depth> depth;      // t < tc
   LevelDev<C>* dcoarse = nullptr;  // [prob][Lmax - tc]
   int nlev_c = 0;
+  size_t coarse_smem = 0;          // dynamic shared memory of the staged coarse kernel (0: global)
   CoarseLU* dlu = nullptr;
   struct Sub {
     int n = 0, cnt = 0, ntiles = 0, chunks = 1, m = 1;
@@ -316,7 +318,18 @@ struct Group {
   LevelDev<C>* lev0 = nullptr;   // level-0 descriptors of all problems (single problem: [0])
   int lev0_nflat = 1;
   void* dmem = nullptr;
-  ~Group() { if (dmem) cudaFree(dmem); }
+  // the V-cycle captured as a CUDA graph (re-captured when profiling starts or stops)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t vexec = nullptr;
+  int vexec_gen = -1;
+  int vkernels = 0;
+  std::vector<GraphRec> vrecs;
+  ~Group() {
+    if (vexec) cudaGraphExecDestroy(vexec);
+    release(vrecs);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (dmem) cudaFree(dmem);
+  }
 };
 
 template <typename C>
@@ -355,6 +368,14 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   }
   g->tc = std::min(std::max(tthr, maxoff), g->Lmax - 1);
   g->nlev_c = g->Lmax - g->tc;
+  {
+    // shared-memory footprint of the coarse levels (same sizes for every problem)
+    const Handle* ref = hs[0];
+    const int off0 = g->Lmax - (int)ref->lev.size();
+    size_t bytes = 0;
+    for (int t = g->tc; t < g->Lmax; ++t) bytes += (size_t)(4 + g->s) * ref->lev[t - off0].np * sizeof(C);
+    g->coarse_smem = (g->nlev_c <= 8 && bytes <= 200 * 1024) ? bytes : 0;
+  }
   // tile config of a group: the first problem's
   for (int p = 0; p < count; ++p)
     if (hs[p]->cfg.rows != g->cfg.rows && off[p] == 0) g->cfg = hs[p]->cfg;
@@ -371,12 +392,9 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
       if (D.cnt > 0 && D.n != L.n) { set_error("batched problems must have n + 1 a power of two"); return HELM_EINVAL; }
       D.n = L.n;
       D.cnt += 1;
-      D.ntiles = tiles_per_problem(g->dim, L.P, g->cfg);
+      D.ntiles = L.ntiles;
       D.nflat = L.nflat;
-      if (D.ntiles > L.ntiles && L.ntiles > 0 && hs[p]->cfg.rows != g->cfg.rows) {
-        set_error("inconsistent tile configuration in batch");
-        return HELM_EINVAL;
-      }
+      D.cfg.rows = zchunk(L.P);
     }
   }
   std::vector<LevelDev<C>> coarse;
@@ -453,26 +471,29 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
     const double ph = g.hs[0]->has_phi ? 4.0 : 0.0;
     if (g.nu1 == 0) {
       Launch L(fine ? "vc.restrict.l0" : "vc.restrict.lc", st, pts * E * (2.0 + cf), 0);
-      launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, g.cfg, true, true, true, st);
+      launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, D.cfg, true, true, true, st);
       continue;
     }
     for (int sw = 0; sw < g.nu1; ++sw) {
       for (int J = 1; J <= g.s; ++J) {
         Launch L(fine ? "vc.arnoldi.l0" : "vc.arnoldi.lc", st, pts * (E * (J + 1) + ph), pts * (8.0 * (2 * dim + 1) + 8.0 * J + 4));
-        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, g.cfg, sw == 0, true, st);
+        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, true, st);
       }
       if (sw < g.nu1 - 1) {
         Launch L(fine ? "vc.update.l0" : "vc.update.lc", st, pts * E * (g.s + 3.0 + (sw == 0 ? 0 : 1)), 0);
         launch_update_flat<C>(dim, UPD_RESIDUAL, D.d, D.cnt, D.nflat, sw == 0, 0, sw == 0, st);
       } else {
         Launch L(fine ? "vc.restrict.l0" : "vc.restrict.lc", st, pts * E * (g.s + 2.0 + cf + (sw == 0 ? 0 : 1)), 0);
-        launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, g.cfg, sw == 0, sw == 0, false, st);
+        launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, sw == 0, false, st);
       }
     }
   }
   {
     Launch L("vc.coarse", st, 0, 0);
-    launch_coarse<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, st);
+    if (g.coarse_smem > 0)
+      launch_coarse_smem<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, g.coarse_smem, st);
+    else
+      launch_coarse<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, st);
   }
   for (int t = g.tc - 1; t >= 0; --t) {
     const auto& D = g.depth[t];
@@ -482,7 +503,7 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
     {
       Launch L(fine ? "vc.prolong.l0" : "vc.prolong.lc", st,
                g.nu2 > 0 ? pts * (E * (4.0 + cf) + ph) : pts * E * (2.0 + cf), 0);
-      launch_prolong<C>(dim, g.nu2 > 0, D.d, D.cnt, g.nu2 > 0 ? D.ntiles : D.nflat, g.cfg, st);
+      launch_prolong<C>(dim, g.nu2 > 0, D.d, D.cnt, g.nu2 > 0 ? D.ntiles : D.nflat, D.cfg, st);
     }
     for (int sw = 0; sw < g.nu2; ++sw) {
       const bool last = (sw == g.nu2 - 1);
@@ -490,12 +511,42 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
         const bool store = J < g.s || !last;
         Launch L(fine ? "vc.arnoldi.l0" : "vc.arnoldi.lc", st, pts * (E * (J + (store ? 1 : 0)) + ph),
                  pts * (8.0 * (2 * dim + 1) + 8.0 * J + 4));
-        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, g.cfg, false, store, st);
+        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, D.cfg, false, store, st);
       }
       Launch L(fine ? "vc.update.l0" : "vc.update.lc", st, pts * E * (last ? g.s + 2.0 : g.s + 4.0), 0);
       launch_update_flat<C>(dim, last ? UPD_XONLY : UPD_RESIDUAL, D.d, D.cnt, D.nflat, false, 1, false, st);
     }
   }
+}
+
+// The V-cycle as one CUDA graph: captured once per group on a private stream (and
+// again whenever profiling starts or stops, so timed launches become event nodes),
+// replayed on the caller's stream.
+template <typename C>
+static int run_vcycle_graph(Group<C>& g, cudaStream_t st) {
+  const int gen = profile_generation();
+  if (!g.vexec || g.vexec_gen != gen) {
+    if (g.vexec) { cudaGraphExecDestroy(g.vexec); g.vexec = nullptr; }
+    release(g.vrecs);
+    g.vkernels = 0;
+    if (!g.cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g.cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    capture_sink_begin(&g.vrecs, &g.vkernels);
+    cudaError_t e = cudaStreamBeginCapture(g.cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      run_vcycle<C>(g, g.cap_stream);
+      e = cudaStreamEndCapture(g.cap_stream, &graph);
+    }
+    capture_sink_end();
+    CUDA_TRY(e);
+    e = cudaGraphInstantiate(&g.vexec, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_TRY(e);
+    g.vexec_gen = gen;
+  }
+  CUDA_TRY(cudaGraphLaunch(g.vexec, st));
+  count_launches(g.vkernels);
+  return HELM_OK;
 }
 
 template <typename C>
@@ -560,8 +611,8 @@ static double sub_points(const typename Group<C>::Sub& o, int dim) {
 }
 
 template <typename C>
-static void run_iteration(const Group<C>& g, cudaStream_t st) {
-  run_vcycle<C>(g, st);
+static int run_iteration(Group<C>& g, cudaStream_t st) {
+  TRY(run_vcycle_graph<C>(g, st));
   const double E = sizeof(C);
   for (const auto& o : g.outer) {
     Launch L("out.apply_h", st, sub_points<C>(o, g.dim) * (16.0 + 2 * E + (g.hs[0]->has_phi ? 4.0 : 0.0)),
@@ -578,6 +629,7 @@ static void run_iteration(const Group<C>& g, cudaStream_t st) {
     Launch L("out.vnew", st, pts1 * (16.0 * (o.sum_j1 + 2 * o.cnt) + E * o.cnt), pts1 * 8.0 * (o.sum_j1 + o.cnt));
     outer_vnew<C>(o.d, o.cnt, o.chunks, o.m, false, st);
   }
+  return HELM_OK;
 }
 
 // Cycle end (acts only on problems whose cycle ended): y = R^{-1} g, x += Z y, true
@@ -630,6 +682,7 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
     return build_group<C>(active.data(), (int)active.size(), st, g);
   };
   TRY(rebuild());
+  Group<C>* graph_pending = nullptr;
   run_cycle_end<C>(*g, st);  // first true residual and v_0 of every problem
   int max_maxit = 0;
   for (int p = 0; p < count; ++p) max_maxit = std::max(max_maxit, hs[p]->maxit);
@@ -637,6 +690,10 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
     for (int p = 0; p < count; ++p)
       CUDA_TRY(cudaMemcpyAsync(pin + p, hs[p]->st, sizeof(OuterState), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (graph_pending) {
+      harvest(graph_pending->vrecs);  // timed V-cycle launches of the replay just completed
+      graph_pending = nullptr;
+    }
     std::vector<Handle*> still;
     for (int p = 0; p < count; ++p) {
       host[p] = pin[p];
@@ -652,9 +709,10 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
       o.sum_j1 = 0;
       for (Handle* m : o.members) o.sum_j1 += m->last_j + 1;
     }
-    run_iteration<C>(*g, st);
+    TRY(run_iteration<C>(*g, st));
     run_cycle_end<C>(*g, st);
     CUDA_TRY(cudaGetLastError());
+    graph_pending = g;
   }
   int rc_all = HELM_OK;
   for (int p = 0; p < count; ++p) {

@@ -25,7 +25,7 @@ struct HostLevel {
   double2* coef64 = nullptr;// the same in FP64
   float* phi = nullptr;     // padded phi or nullptr
   double phic = 0.0;
-  SweepScalars* sc = nullptr;
+  void* sc = nullptr;          // SweepScalarsT<R> of the preconditioner precision
   double* part = nullptr;
 };
 

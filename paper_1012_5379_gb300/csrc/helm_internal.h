@@ -22,21 +22,36 @@ namespace helm {
 constexpr int SMAX = 4;            // max GMRES(s) steps per smoothing sweep
 constexpr int NPART = 2 * SMAX + 4;  // doubles per partial-sum slot of a sweep pass
 
-// Per (problem, level) state of the current GMRES(s) sweep, FP64, device memory.
-// Raw vectors R_0 = r0 (initial residual of the sweep), R_j = p_j = M v_j.  Every
-// Arnoldi vector is kept as coefficients over the raw vectors:
-//   v_j = sum_{k<j} Cf[j][k] R_k   (j = 1..s).
-struct SweepScalars {
-  double beta2;                        // ||R_0||^2
-  int m;                               // Krylov steps of this sweep (0: nothing to do)
-  int s;                               // requested steps
-  double2 G[SMAX + 1][SMAX + 1];       // G[k][j] = <R_k, R_j>, k <= j
-  double2 Cf[SMAX + 1][SMAX + 1];      // Arnoldi vectors over raw vectors
-  double2 Hh[SMAX + 1][SMAX];          // Hessenberg matrix of the sweep
-  double2 xcoef[SMAX + 1];             // x_new = x_old + sum_k xcoef[k] R_k
-  double2 rcoef[SMAX + 1];             // r_new = sum_k rcoef[k] R_k
-  unsigned int counter;                // last-block-done counter
-  int status;                          // nonzero: NaN/Inf seen
+// Real and complex scalar types of a preconditioner precision.
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { typedef float T; };
+template <> struct RealOf<double2> { typedef double T; };
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { typedef float2 T; };
+template <> struct CplxOf<double> { typedef double2 T; };
+
+// Per (problem, level) state of the current GMRES(s) sweep, device memory, in the
+// working precision R of the V-cycle (FP32 for complex64: nothing in that V-cycle
+// touches the slow FP64 pipe).  Raw vectors R_0 = r0 (initial residual of the
+// sweep), R_j = p_j = M v_j.  Every Arnoldi vector is kept as coefficients over the
+// raw vectors:  v_j = sum_{k<j} Cf[j][k] R_k   (j = 1..s).
+template <typename R>
+struct SweepScalarsT {
+  typedef typename CplxOf<R>::T CR;
+  R beta2;                        // ||R_0||^2
+  int m;                          // Krylov steps of this sweep (0: nothing to do)
+  int s;                          // requested steps
+  CR G[SMAX + 1][SMAX + 1];       // G[k][j] = <R_k, R_j>, k <= j
+  CR Cf[SMAX + 1][SMAX + 1];      // Arnoldi vectors over raw vectors
+  CR Hh[SMAX + 1][SMAX];          // Hessenberg matrix of the sweep
+  CR xcoef[SMAX + 1];             // x_new = x_old + sum_k xcoef[k] R_k
+  CR rcoef[SMAX + 1];             // r_new = sum_k rcoef[k] R_k
+  int status;                     // nonzero: NaN/Inf seen
+  int pad0;
+  // everything above is the sweep algebra's state (staged through shared memory);
+  // the reduction counter below is never part of that copy
+  unsigned int counter;           // last-block-done counter
+  int pad1;
 };
 
 // One level of one problem, as seen by the kernels (device memory).
@@ -58,9 +73,9 @@ struct LevelDev {
   const C* cc;            // 1D coefficients of u_{i+1}
   const float* phi;       // phi field in padded layout, or nullptr
   double phic;            // constant phi when phi == nullptr
-  SweepScalars* sc;       // this level's sweep state
-  SweepScalars* scc;      // coarser level's sweep state
-  double* part;           // partial sums: ntiles * NPART doubles
+  SweepScalarsT<typename RealOf<C>::T>* sc;   // this level's sweep state
+  SweepScalarsT<typename RealOf<C>::T>* scc;  // coarser level's sweep state
+  double* part;           // partial sums: ntiles * NPART slots (R or double)
 };
 
 // Dense LU factors of the coarsest operator (FP64), row-major, with pivots.
@@ -116,12 +131,12 @@ struct OuterDev {
   double* vscale;         // m+1: v_i = vscale[i] * V[i] (V stored unnormalised)
   double* part;           // partial sums
   OuterState* st;
-  SweepScalars* sc0;      // level-0 sweep state (set by the kernel that writes b0)
+  SweepScalarsT<typename RealOf<C>::T>* sc0;  // level-0 sweep state (set by the kernel that writes b0)
 };
 
-// Tile configuration of the marching kernels.
+// Tile configuration: rows (2D) or planes (3D) marched per warp / CTA (even).
 struct TileCfg {
-  int rows;   // 2D: rows marched per warp (even); 3D: planes marched per CTA (even)
+  int rows;
 };
 
 constexpr int WARPS2 = 8;     // 2D: warps per CTA (each marches its own rows)
@@ -129,6 +144,15 @@ constexpr int WY3 = 8;        // 3D: owned y rows per CTA (plus 2 halo warps)
 
 HELM_HD inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// V-cycle tile kernels: 2D tiles of 64 x 16 points; 3D blocks of 32 x 8 columns
+// marching zchunk(P) planes.
+HELM_HD inline int zchunk(int P) { return P >= 128 ? 32 : (P >= 32 ? 16 : 8); }
+HELM_HD inline int vtiles(int dim, int P) {
+  return dim == 2 ? ceil_div(P, 64) * ceil_div(P, 16) : ceil_div(P, 32) * ceil_div(P, 8) * ceil_div(P, zchunk(P));
+}
+
+// Marching FP64 stencil of the outer solve: 2D warps march cfg.rows rows, 3D CTAs
+// march cfg.rows planes.
 inline int tiles_per_problem(int dim, int P, TileCfg cfg) {
   if (dim == 2) return ceil_div(P, 32) * ceil_div(P, WARPS2 * cfg.rows);
   return ceil_div(P, 32) * ceil_div(P, WY3) * ceil_div(P, cfg.rows);
@@ -153,6 +177,10 @@ void launch_prolong(int dim, bool with_residual, const LevelDev<C>* levs, int np
 template <typename C>
 void launch_coarse(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
                    int nu1, int nu2, cudaStream_t st);
+// coarse sub-cycle staged in shared memory (smem_bytes: all levels' vectors)
+template <typename C>
+void launch_coarse_smem(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
+                        int nu1, int nu2, size_t smem_bytes, cudaStream_t st);
 // level-0 input from a natural-layout vector of precision in_prec (HELM_C64/HELM_C128)
 template <typename C>
 void launch_load_input(int dim, const LevelDev<C>* levs, int ntiles, const void* src, int in_prec, cudaStream_t st);

@@ -125,7 +125,8 @@ int run_noalloc(const helm_grid* grid, double k, double theta_beta, int nu1, int
   Carve cv;
   const size_t o_lev = cv.take(sizeof(LevelDev<C>) * nlev);
   const size_t o_lu = cv.take(sizeof(CoarseLU));
-  const size_t o_sc = cv.take(sizeof(SweepScalars) * nlev);
+  typedef SweepScalarsT<typename RealOf<C>::T> SS;
+  const size_t o_sc = cv.take(sizeof(SS) * nlev);
   const size_t o_part = cv.take(sizeof(double) * NPART);
   const size_t o_lum = cv.take(sizeof(double2) * m * m);
   const size_t o_piv = cv.take(sizeof(int) * m);
@@ -176,7 +177,7 @@ int run_noalloc(const helm_grid* grid, double k, double theta_beta, int nu1, int
     d.cc = cf + 2 * nl;
     d.phi = nullptr;
     d.phic = k * k;
-    d.sc = (SweepScalars*)(base + o_sc) + l;
+    d.sc = (SS*)(base + o_sc) + l;
     d.part = (double*)(base + o_part);
     {
       cd a[MAX_N], dd[MAX_N], c[MAX_N];

@@ -210,7 +210,7 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
 // its running sums per i in shared memory (fixed order), the block combines warps,
 // and the last block combines blocks and performs the Givens update.
 constexpr int DOT_THREADS = 256;
-constexpr int DOT_PPT = 8;   // points per thread per chunk
+constexpr int DOT_PPT = 16;  // points per thread per chunk
 
 template <typename C>
 __global__ void __launch_bounds__(DOT_THREADS)
@@ -236,12 +236,14 @@ k_dots(const OuterDev<C>* __restrict__ ods, int chunks) {
     }
     for (int i = 0; i <= j; ++i) {
       const double2* v = O.V + (size_t)i * O.vs;
-      double2 acc = make_double2(0, 0);
+      double2 acc = make_double2(0, 0), acc2 = make_double2(0, 0);
 #pragma unroll
-      for (int q = 0; q < DOT_PPT; ++q) {
-        size_t idx = base + (size_t)q * DOT_THREADS + tid;
+      for (int q = 0; q < DOT_PPT; q += 2) {
+        const size_t idx = base + (size_t)q * DOT_THREADS + tid;
         if (idx < npts) acc = cdotacc(__ldcg(v + idx), wv[q], acc);
+        if (idx + DOT_THREADS < npts) acc2 = cdotacc(__ldcg(v + idx + DOT_THREADS), wv[q + 1], acc2);
       }
+      acc = cadd(acc, acc2);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -344,11 +346,17 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int chunks, int start) {
   double accu = 0.0;
   typename CT<C>::R accb = 0;
   for (size_t idx = (size_t)cta * blockDim.x + tid; idx < O.vs; idx += (size_t)chunks * blockDim.x) {
-    double2 wv = __ldcg(O.w + idx);
-    for (int i = 0; i <= j; ++i) {
-      const double2 vi = __ldcg(O.V + (size_t)i * O.vs + idx);
-      wv = csub(wv, cmul(sh[i], vi));
+    // two independent accumulation chains keep the FP64 pipe busy
+    double2 wa = __ldcg(O.w + idx), wb = make_double2(0, 0);
+    const double2* vp = O.V + idx;
+    int i = 0;
+    for (; i + 1 <= j; i += 2) {
+      const double2 v0 = __ldcg(vp + (size_t)i * O.vs), v1 = __ldcg(vp + (size_t)(i + 1) * O.vs);
+      wa = cfms(sh[i], v0, wa);
+      wb = cfms(sh[i + 1], v1, wb);
     }
+    if (i <= j) wa = cfms(sh[i], __ldcg(vp + (size_t)i * O.vs), wa);
+    double2 wv = cadd(wa, wb);
     wv = make_double2(wv.x * inv, wv.y * inv);
     vout[idx] = wv;
     accu += dabs2(wv);
@@ -359,7 +367,7 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int chunks, int start) {
   double red[2] = {accu, (double)accb}, tot[2];
   if (grid_sum_last<2>(red, O.part, cta, chunks, &st->counter, sm, tot)) {
     if (flat_tid() == 0) {
-      sweep_begin(O.sc0, tot[1], O.s);
+      sweep_begin(O.sc0, (typename CT<C>::R)tot[1], O.s);
       if (start) {
         O.vscale[0] = 1.0;
         st->fresh = 0;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 namespace helm {
 
@@ -13,6 +14,22 @@ void profile_begin(const std::string& prefix);
 // Stops profiling, waits for the recorded events and returns a JSON object
 // {"class": {"launches": n, "ms": t, "bytes": b, "flops": f}, ...}.
 std::string profile_end();
+
+// CUDA-graph support: while a capture sink is set on the calling thread, launches
+// are counted into it and timed launches become event-record nodes of the graph;
+// after a replay of that graph has completed, harvest() adds their times.
+struct GraphRec {
+  std::string name;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+void capture_sink_begin(std::vector<GraphRec>* recs, int* kernels);
+void capture_sink_end();
+void harvest(const std::vector<GraphRec>& recs);
+void release(std::vector<GraphRec>& recs);
+void count_launches(int kernels);
+int profile_generation();     // changes whenever profiling starts or stops
+bool profiling();
 
 // Brackets one kernel launch (or a short sequence of launches counted as `kernels`).
 class Launch {
@@ -24,6 +41,7 @@ class Launch {
 
  private:
   int slot_ = -1;
+  bool graph_ = false;
   cudaStream_t st_;
 };
 

@@ -1,0 +1,446 @@
+// Shared-memory tile kernels of the grid-wide V-cycle passes (Sec. 3.1).
+//
+// 2D: a CTA of 32 x 8 threads owns a 64 x 16 tile; each thread owns four points
+//     (x0 + lx + 32a, y0 + ly + 8b).  Threads load the raw vectors at their own points
+//     (keeping them in registers for the dot products) and write the formed vector
+//     into a (16+2) x (64+2) shared tile; the 164 halo points are loaded by the first
+//     164 threads.  The stencil then reads shared memory only.
+// 3D: a CTA of 32 x 8 threads owns a 32 x 8 column block and marches `zc` planes in
+//     z.  Plane tiles (8+2) x (32+2) live in a 4-slot shared ring: the plane loaded in
+//     iteration z sits in slot (z+1)&3, the stencil of plane z reads slots (z-1)&3,
+//     z&3, (z+1)&3, and a slot read in iteration z is next overwritten in iteration
+//     z+2, after iteration z+1's barrier, so one __syncthreads per plane suffices.
+#pragma once
+#include "vcycle.cuh"
+
+namespace helm {
+
+constexpr int T2X = 64, T2Y = 16;
+constexpr int T3X = 32, T3Y = 8;
+constexpr int HALO2 = 2 * (T2X + 2) + 2 * T2Y;  // 164
+constexpr int HALO3 = 2 * (T3X + 2) + 2 * T3Y;  // 84
+
+// h-th halo point of a TX x TY tile in local coordinates (-1..TX, -1..TY):
+// top row, bottom row, left column, right column.
+template <int TX, int TY>
+__device__ __forceinline__ void halo_coord(int h, int& hx, int& hy) {
+  if (h < TX + 2) { hx = h - 1; hy = -1; return; }
+  h -= TX + 2;
+  if (h < TX + 2) { hx = h - 1; hy = TY; return; }
+  h -= TX + 2;
+  if (h < TY) { hx = -1; hy = h; return; }
+  h -= TY;
+  hx = TX;
+  hy = h;
+}
+
+template <typename C>
+__device__ __forceinline__ C stencil5(const Coef3<C>& cx, const Coef3<C>& cy, typename CT<C>::R phi, C v0, C vl,
+                                      C vr, C vs, C vn) {
+  C diag = cadd(cx.d, cy.d);
+  diag.x -= phi;
+  C p = cmul(diag, v0);
+  p = cfma(cx.a, vl, p);
+  p = cfma(cx.c, vr, p);
+  p = cfma(cy.a, vs, p);
+  return cfma(cy.c, vn, p);
+}
+
+// ------------------------------------------------------------------ Arnoldi step J
+template <typename C, int J>
+__global__ void __launch_bounds__(256)
+k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int store_p) {
+  typedef typename CT<C>::R R;
+  __shared__ C vt[T2Y + 2][T2X + 2];
+  __shared__ R sm[32 * (2 * J + 1)];
+  pdl_trigger();
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  auto* sc = L.sc;
+  pdl_wait();
+  if (sc->m < J) return;  // earlier breakdown or empty sweep: uniform for the problem
+  const int n = L.n, P = L.P;
+  const int ntx = ceil_div(P, T2X);
+  const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  const C* Rk[J];
+  C cf[J];
+#pragma unroll
+  for (int k = 0; k < J; ++k) {
+    Rk[k] = (k == 0) ? (r0_is_b ? L.b : L.r0) : L.p[k - 1];
+    cf[k] = sc->Cf[J][k];
+  }
+  C raw[4][J];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+    C v = czero<C>();
+#pragma unroll
+    for (int k = 0; k < J; ++k) {
+      raw[q][k] = ldc(Rk[k], x0 + ox, y0 + oy, 0, n, P);
+      v = cfma(cf[k], raw[q][k], v);
+    }
+    vt[oy + 1][ox + 1] = v;
+  }
+  if (tid < HALO2) {
+    int hx, hy;
+    halo_coord<T2X, T2Y>(tid, hx, hy);
+    C v = czero<C>();
+#pragma unroll
+    for (int k = 0; k < J; ++k) v = cfma(cf[k], ldc(Rk[k], x0 + hx, y0 + hy, 0, n, P), v);
+    vt[hy + 1][hx + 1] = v;
+  }
+  __syncthreads();
+  C acc[J];
+#pragma unroll
+  for (int k = 0; k < J; ++k) acc[k] = czero<C>();
+  R accn = 0;
+  const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+    const int x = x0 + ox, y = y0 + oy;
+    C p = czero<C>();
+    if (x < n && y < n) {
+      const Coef3<C> cy = ldcoef(L, y);
+      p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox], vt[oy + 1][ox + 2],
+                   vt[oy][ox + 1], vt[oy + 2][ox + 1]);
+#pragma unroll
+      for (int k = 0; k < J; ++k) acc[k] = cdotacc(raw[q][k], p, acc[k]);
+      accn += cabs2(p);
+    }
+    if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, 0, P)] = p;
+  }
+  R red[2 * J + 1], tot[2 * J + 1];
+#pragma unroll
+  for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
+  red[2 * J] = accn;
+  if (grid_sum_last<2 * J + 1>(red, L.part, tile, ntiles, &sc->counter, sm, tot))
+    block_sweep_after_pass<R, J>(sc, tot);
+}
+
+template <typename C, int J>
+__global__ void __launch_bounds__(256)
+k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is_b, int store_p) {
+  typedef typename CT<C>::R R;
+  __shared__ C vb[4][T3Y + 2][T3X + 2];
+  __shared__ R sm[32 * (2 * J + 1)];
+  pdl_trigger();
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  auto* sc = L.sc;
+  pdl_wait();
+  if (sc->m < J) return;
+  const int n = L.n, P = L.P;
+  const int ntx = ceil_div(P, T3X), nty = ceil_div(P, T3Y);
+  const int x0 = (tile % ntx) * T3X, y0 = ((tile / ntx) % nty) * T3Y;
+  const int zbeg = (tile / (ntx * nty)) * zc, zend = min(zbeg + zc, P);
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  const int x = x0 + lx, y = y0 + ly;
+  const C* Rk[J];
+  C cf[J];
+#pragma unroll
+  for (int k = 0; k < J; ++k) {
+    Rk[k] = (k == 0) ? (r0_is_b ? L.b : L.r0) : L.p[k - 1];
+    cf[k] = sc->Cf[J][k];
+  }
+  const bool halo = tid < HALO3;
+  int hx = 0, hy = 0;
+  if (halo) halo_coord<T3X, T3Y>(tid, hx, hy);
+  auto load_plane = [&](int z, C* raw) {
+    C v = czero<C>();
+#pragma unroll
+    for (int k = 0; k < J; ++k) {
+      const C r = ldc(Rk[k], x, y, z, n, P);
+      if (raw) raw[k] = r;
+      v = cfma(cf[k], r, v);
+    }
+    vb[z & 3][ly + 1][lx + 1] = v;
+    if (halo) {
+      C w = czero<C>();
+#pragma unroll
+      for (int k = 0; k < J; ++k) w = cfma(cf[k], ldc(Rk[k], x0 + hx, y0 + hy, z, n, P), w);
+      vb[z & 3][hy + 1][hx + 1] = w;
+    }
+  };
+  const Coef3<C> cx = ldcoef(L, x), cy = ldcoef(L, y);
+  C acc[J];
+#pragma unroll
+  for (int k = 0; k < J; ++k) acc[k] = czero<C>();
+  R accn = 0;
+  if (zbeg < P) {
+    C rawc[J], rawn[J];
+    load_plane(zbeg - 1, nullptr);
+    load_plane(zbeg, rawc);
+    for (int z = zbeg; z < zend; ++z) {
+      load_plane(z + 1, rawn);
+      __syncthreads();
+      const int s0 = z & 3;
+      C p = czero<C>();
+      if (inside(x, y, z, n)) {
+        const Coef3<C> cz = ldcoef(L, z);
+        p = stencil5(cx, cy, phi_at(L, x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
+                     vb[s0][ly][lx + 1], vb[s0][ly + 2][lx + 1]);
+        p = cfma(cz.d, vb[s0][ly + 1][lx + 1], p);
+        p = cfma(cz.a, vb[(z - 1) & 3][ly + 1][lx + 1], p);
+        p = cfma(cz.c, vb[(z + 1) & 3][ly + 1][lx + 1], p);
+#pragma unroll
+        for (int k = 0; k < J; ++k) acc[k] = cdotacc(rawc[k], p, acc[k]);
+        accn += cabs2(p);
+      }
+      if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, z, P)] = p;
+#pragma unroll
+      for (int k = 0; k < J; ++k) rawc[k] = rawn[k];
+    }
+  }
+  R red[2 * J + 1], tot[2 * J + 1];
+#pragma unroll
+  for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
+  red[2 * J] = accn;
+  if (grid_sum_last<2 * J + 1>(red, L.part, tile, ntiles, &sc->counter, sm, tot))
+    block_sweep_after_pass<R, J>(sc, tot);
+}
+
+// ------------------------------------------------------------------ end of pre-smoothing
+// x_a = x + dx, r = R_0 - sum y_j p_j and b_c = FW(r), ||b_c||^2 starts the coarser
+// level's first sweep.  Tiles sit at even fine offsets, so a 64 x 16 fine tile maps
+// onto a 32 x 8 coarse tile (one coarse point per thread); r is formed on the tile
+// plus one row/column above (x0+64, y0+16).
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int x_from_zero, int nosmooth) {
+  typedef typename CT<C>::R R;
+  __shared__ C rt[T2Y + 1][T2X + 1];
+  __shared__ R sm[32];
+  pdl_trigger();
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
+  pdl_wait();
+  const int ntx = ceil_div(P, T2X);
+  const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  UpdCoef<C> u = load_upd(L, r0_is_b);
+  if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+    const int x = x0 + ox, y = y0 + oy;
+    C dx, r;
+    upd_point(u, x, y, 0, n, P, dx, r);
+    if (x < P && y < P) {
+      const size_t id = pidx(x, y, 0, P);
+      L.xa[id] = (x < n && y < n) ? cadd(x_from_zero ? czero<C>() : L.xa[id], dx) : czero<C>();
+    }
+    rt[oy][ox] = r;
+  }
+  if (tid < T2X + 1 + T2Y) {
+    const int hx = tid < T2X + 1 ? tid : T2X;
+    const int hy = tid < T2X + 1 ? T2Y : tid - (T2X + 1);
+    C dx, r;
+    upd_point(u, x0 + hx, y0 + hy, 0, n, P, dx, r);
+    rt[hy][hx] = r;
+  }
+  __syncthreads();
+  const int fx = 2 * lx + 1, fy = 2 * ly + 1;
+  C out = czero<C>();
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx)
+      out = cadd(out, cscale(rt[fy + dy][fx + dx], (R)((dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25))));
+  const int Ix = x0 / 2 + lx, Iy = y0 / 2 + ly;
+  R acc = 0;
+  if (Ix < Pc && Iy < Pc) {
+    const bool valid = Ix < nc && Iy < nc;
+    L.bc[pidx(Ix, Iy, 0, Pc)] = valid ? out : czero<C>();
+    if (valid) acc += cabs2(out);
+  }
+  R red[1] = {acc}, tot[1];
+  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
+    if (flat_tid() == 0) sweep_begin(L.scc, tot[0], L.s);
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is_b, int x_from_zero, int nosmooth) {
+  typedef typename CT<C>::R R;
+  __shared__ C rb[4][T3Y + 1][T3X + 1];
+  __shared__ R sm[32];
+  pdl_trigger();
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
+  pdl_wait();
+  const int ntx = ceil_div(P, T3X), nty = ceil_div(P, T3Y);
+  const int x0 = (tile % ntx) * T3X, y0 = ((tile / ntx) % nty) * T3Y;
+  const int zbeg = (tile / (ntx * nty)) * zc, zend = min(zbeg + zc, P);
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  const int x = x0 + lx, y = y0 + ly;
+  UpdCoef<C> u = load_upd(L, r0_is_b);
+  if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
+  const bool halo = tid < T3X + 1 + T3Y;
+  const int hx = tid < T3X + 1 ? tid : T3X;
+  const int hy = tid < T3X + 1 ? T3Y : tid - (T3X + 1);
+  const bool emit = tid < (T3X / 2) * (T3Y / 2);
+  const int cx = tid % (T3X / 2), cy = tid / (T3X / 2);
+  R acc = 0;
+  if (zbeg < P) {
+    for (int z = zbeg; z <= zend; ++z) {
+      C dx, r;
+      upd_point(u, x, y, z, n, P, dx, r);
+      if (z < zend && x < P && y < P) {
+        const size_t id = pidx(x, y, z, P);
+        L.xa[id] = inside(x, y, z, n) ? cadd(x_from_zero ? czero<C>() : L.xa[id], dx) : czero<C>();
+      }
+      rb[z & 3][ly][lx] = r;
+      if (halo) {
+        C d2, r2;
+        upd_point(u, x0 + hx, y0 + hy, z, n, P, d2, r2);
+        rb[z & 3][hy][hx] = r2;
+      }
+      __syncthreads();
+      if ((z & 1) == 0 && z > zbeg && emit) {
+        const int fx = 2 * cx + 1, fy = 2 * cy + 1;
+        C out = czero<C>();
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int ddx = -1; ddx <= 1; ++ddx) {
+              const R wgt = (R)((ddx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25) * (dz == 0 ? 0.5 : 0.25));
+              out = cadd(out, cscale(rb[(z - 1 + dz) & 3][fy + dy][fx + ddx], wgt));
+            }
+        const int Ix = x0 / 2 + cx, Iy = y0 / 2 + cy, Iz = z / 2 - 1;
+        if (Ix < Pc && Iy < Pc && Iz < Pc) {
+          const bool valid = Ix < nc && Iy < nc && Iz < nc;
+          L.bc[pidx(Ix, Iy, Iz, Pc)] = valid ? out : czero<C>();
+          if (valid) acc += cabs2(out);
+        }
+      }
+    }
+  }
+  R red[1] = {acc}, tot[1];
+  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
+    if (flat_tid() == 0) sweep_begin(L.scc, tot[0], L.s);
+  }
+}
+
+// ------------------------------------------------------------------ coarse correction
+// x_b = x_a + P e_c, r0 = b - M x_b, ||r0||^2 starts post-smoothing.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles) {
+  typedef typename CT<C>::R R;
+  __shared__ C vt[T2Y + 2][T2X + 2];
+  __shared__ R sm[32];
+  pdl_trigger();
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  const int n = L.n, P = L.P;
+  pdl_wait();
+  const int ntx = ceil_div(P, T2X);
+  const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  auto form = [&](int xx, int yy) -> C {
+    return cadd(ldc((const C*)L.xa, xx, yy, 0, n, P), interp(L, xx, yy, 0, 2));
+  };
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+    vt[oy + 1][ox + 1] = form(x0 + ox, y0 + oy);
+  }
+  if (tid < HALO2) {
+    int hx, hy;
+    halo_coord<T2X, T2Y>(tid, hx, hy);
+    vt[hy + 1][hx + 1] = form(x0 + hx, y0 + hy);
+  }
+  __syncthreads();
+  R acc = 0;
+  const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+    const int x = x0 + ox, y = y0 + oy;
+    if (x < P && y < P) {
+      C r = czero<C>(), xo = czero<C>();
+      if (x < n && y < n) {
+        const Coef3<C> cy = ldcoef(L, y);
+        const C p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
+                             vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
+        r = csub(__ldg(L.b + pidx(x, y, 0, P)), p);
+        xo = vt[oy + 1][ox + 1];
+        acc += cabs2(r);
+      }
+      L.xb[pidx(x, y, 0, P)] = xo;
+      L.r0[pidx(x, y, 0, P)] = r;
+    }
+  }
+  R red[1] = {acc}, tot[1];
+  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
+    if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
+  typedef typename CT<C>::R R;
+  __shared__ C vb[4][T3Y + 2][T3X + 2];
+  __shared__ R sm[32];
+  pdl_trigger();
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  const int n = L.n, P = L.P;
+  pdl_wait();
+  const int ntx = ceil_div(P, T3X), nty = ceil_div(P, T3Y);
+  const int x0 = (tile % ntx) * T3X, y0 = ((tile / ntx) % nty) * T3Y;
+  const int zbeg = (tile / (ntx * nty)) * zc, zend = min(zbeg + zc, P);
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  const int x = x0 + lx, y = y0 + ly;
+  const bool halo = tid < HALO3;
+  int hx = 0, hy = 0;
+  if (halo) halo_coord<T3X, T3Y>(tid, hx, hy);
+  auto form = [&](int xx, int yy, int zz) -> C {
+    return cadd(ldc((const C*)L.xa, xx, yy, zz, n, P), interp(L, xx, yy, zz, 3));
+  };
+  auto load_plane = [&](int z) {
+    vb[z & 3][ly + 1][lx + 1] = form(x, y, z);
+    if (halo) vb[z & 3][hy + 1][hx + 1] = form(x0 + hx, y0 + hy, z);
+  };
+  const Coef3<C> cx = ldcoef(L, x), cy = ldcoef(L, y);
+  R acc = 0;
+  if (zbeg < P) {
+    load_plane(zbeg - 1);
+    load_plane(zbeg);
+    for (int z = zbeg; z < zend; ++z) {
+      load_plane(z + 1);
+      __syncthreads();
+      const int s0 = z & 3;
+      if (x < P && y < P) {
+        C r = czero<C>(), xo = czero<C>();
+        if (inside(x, y, z, n)) {
+          const Coef3<C> cz = ldcoef(L, z);
+          C p = stencil5(cx, cy, phi_at(L, x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
+                         vb[s0][ly][lx + 1], vb[s0][ly + 2][lx + 1]);
+          p = cfma(cz.d, vb[s0][ly + 1][lx + 1], p);
+          p = cfma(cz.a, vb[(z - 1) & 3][ly + 1][lx + 1], p);
+          p = cfma(cz.c, vb[(z + 1) & 3][ly + 1][lx + 1], p);
+          r = csub(__ldg(L.b + pidx(x, y, z, P)), p);
+          xo = vb[s0][ly + 1][lx + 1];
+          acc += cabs2(r);
+        }
+        L.xb[pidx(x, y, z, P)] = xo;
+        L.r0[pidx(x, y, z, P)] = r;
+      }
+    }
+  }
+  R red[1] = {acc}, tot[1];
+  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
+    if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
+  }
+}
+
+}  // namespace helm

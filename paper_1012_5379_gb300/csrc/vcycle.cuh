@@ -1,12 +1,6 @@
 // V-cycle kernels of the GMRES(s)-smoothed multigrid for M^CSG (Sec. 3.1).
 //
-// Every grid-level kernel is a marching stencil over the padded layout:
-//   2D: a warp owns 32 consecutive x and marches `rows` rows in y; x-neighbours come
-//       from warp shuffles (edge lanes load their outside neighbour), y-neighbours
-//       from a three-deep register queue.
-//   3D: a CTA owns 32 x 8 (x, y) columns plus two halo rows and marches `rows` planes
-//       in z; x-neighbours from shuffles, y-neighbours through a double-buffered
-//       shared-memory plane, z-neighbours from a register queue.
+// The grid-wide passes are shared-memory tile kernels (tiles.cuh).
 // A kernel of Arnoldi step J never stores v_J: it forms v_J on the fly from the raw
 // vectors R_0..R_{J-1} with the sweep's FP64 coefficients (v_J = sum Cf[J][k] R_k),
 // applies M, stores p_J = M v_J and reduces <R_k, p_J> and ||p_J||^2 per problem in a
@@ -72,176 +66,6 @@ __device__ __forceinline__ C interp(const LevelDev<C>& L, int x, int y, int z, i
   return cscale(acc, w);
 }
 
-// ------------------------------------------------------------------ pass J (2D)
-template <typename C, int J>
-__global__ void __launch_bounds__(32 * WARPS2)
-k_arnoldi2(const LevelDev<C>* __restrict__ levs, int ntiles, int rows, int r0_is_b, int store_p) {
-  typedef typename CT<C>::R R;
-  __shared__ double sm[32 * (2 * J + 1)];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
-  const LevelDev<C>& L = levs[prob];
-  SweepScalars* sc = L.sc;
-  if (sc->m < J) return;  // earlier breakdown or empty sweep: uniform for the problem
-  const int n = L.n, P = L.P;
-  const int ntx = ceil_div(P, 32);
-  const int tx = tile % ntx, ty = tile / ntx;
-  const int lane = threadIdx.x, warp = threadIdx.y;
-  const int x = tx * 32 + lane;
-  const int ybeg = (ty * WARPS2 + warp) * rows;
-  const int yend = min(ybeg + rows, P);
-
-  const C* Rk[J];
-  C cf[J];
-#pragma unroll
-  for (int k = 0; k < J; ++k) {
-    Rk[k] = (k == 0) ? (r0_is_b ? L.b : L.r0) : L.p[k - 1];
-    cf[k] = from_d<C>(sc->Cf[J][k]);
-  }
-  const Coef3<C> cx = ldcoef(L, x);
-  auto form = [&](int xx, int yy, C* raw) -> C {
-    C v = czero<C>();
-#pragma unroll
-    for (int k = 0; k < J; ++k) {
-      C r = ldc(Rk[k], xx, yy, 0, n, P);
-      if (raw) raw[k] = r;
-      v = cfma(cf[k], r, v);
-    }
-    return v;
-  };
-
-  C acc[J];
-#pragma unroll
-  for (int k = 0; k < J; ++k) acc[k] = czero<C>();
-  R accn = 0;
-  if (ybeg < P) {
-    C raw0[J], rawn[J];
-    C vm = form(x, ybeg - 1, nullptr);
-    C v0 = form(x, ybeg, raw0);
-    for (int y = ybeg; y < yend; ++y) {
-      C vp = form(x, y + 1, rawn);
-      C vl = shfl_up_c(v0, 1), vr = shfl_down_c(v0, 1);
-      if (lane == 0) vl = form(x - 1, y, nullptr);
-      if (lane == 31) vr = form(x + 1, y, nullptr);
-      C p = czero<C>();
-      if (x < n && y < n) {
-        const Coef3<C> cy = ldcoef(L, y);
-        C diag = cadd(cx.d, cy.d);
-        diag.x -= phi_at(L, x, y, 0);
-        p = cmul(diag, v0);
-        p = cfma(cx.a, vl, p);
-        p = cfma(cx.c, vr, p);
-        p = cfma(cy.a, vm, p);
-        p = cfma(cy.c, vp, p);
-#pragma unroll
-        for (int k = 0; k < J; ++k) acc[k] = cdotacc(raw0[k], p, acc[k]);
-        accn += cabs2(p);
-      }
-      if (store_p && x < P) L.p[J - 1][pidx(x, y, 0, P)] = p;
-      vm = v0;
-      v0 = vp;
-#pragma unroll
-      for (int k = 0; k < J; ++k) raw0[k] = rawn[k];
-    }
-  }
-  double red[2 * J + 1], tot[2 * J + 1];
-#pragma unroll
-  for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
-  red[2 * J] = accn;
-  if (grid_sum_last<2 * J + 1>(red, L.part, tile, ntiles, &sc->counter, sm, tot)) {
-    if (flat_tid() == 0) sweep_after_pass(sc, J, tot, SweepTau<C>::v);
-  }
-}
-
-// ------------------------------------------------------------------ pass J (3D)
-template <typename C, int J>
-__global__ void __launch_bounds__(32 * (WY3 + 2))
-k_arnoldi3(const LevelDev<C>* __restrict__ levs, int ntiles, int rows, int r0_is_b, int store_p) {
-  typedef typename CT<C>::R R;
-  __shared__ double sm[32 * (2 * J + 1)];
-  __shared__ C sv[2][WY3 + 2][32];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
-  const LevelDev<C>& L = levs[prob];
-  SweepScalars* sc = L.sc;
-  if (sc->m < J) return;
-  const int n = L.n, P = L.P;
-  const int ntx = ceil_div(P, 32), nty = ceil_div(P, WY3);
-  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-  const int lane = threadIdx.x, w = threadIdx.y;
-  const bool owned = (w >= 1 && w <= WY3);
-  const int x = tx * 32 + lane;
-  const int y = ty * WY3 - 1 + w;
-  const int zbeg = tz * rows;
-  const int zend = min(zbeg + rows, P);
-
-  const C* Rk[J];
-  C cf[J];
-#pragma unroll
-  for (int k = 0; k < J; ++k) {
-    Rk[k] = (k == 0) ? (r0_is_b ? L.b : L.r0) : L.p[k - 1];
-    cf[k] = from_d<C>(sc->Cf[J][k]);
-  }
-  const Coef3<C> cx = ldcoef(L, x), cy = ldcoef(L, y);
-  auto form = [&](int xx, int yy, int zz, C* raw) -> C {
-    C v = czero<C>();
-#pragma unroll
-    for (int k = 0; k < J; ++k) {
-      C r = ldc(Rk[k], xx, yy, zz, n, P);
-      if (raw) raw[k] = r;
-      v = cfma(cf[k], r, v);
-    }
-    return v;
-  };
-
-  C acc[J];
-#pragma unroll
-  for (int k = 0; k < J; ++k) acc[k] = czero<C>();
-  R accn = 0;
-  if (zbeg < P) {
-    C raw0[J], rawn[J];
-    C vm = form(x, y, zbeg - 1, nullptr);
-    C v0 = form(x, y, zbeg, raw0);
-    for (int z = zbeg; z < zend; ++z) {
-      C vp = form(x, y, z + 1, rawn);
-      sv[z & 1][w][lane] = v0;
-      __syncthreads();
-      if (owned) {
-        C vs = sv[z & 1][w - 1][lane], vn = sv[z & 1][w + 1][lane];
-        C vl = shfl_up_c(v0, 1), vr = shfl_down_c(v0, 1);
-        if (lane == 0) vl = form(x - 1, y, z, nullptr);
-        if (lane == 31) vr = form(x + 1, y, z, nullptr);
-        C p = czero<C>();
-        if (x < n && y < n && z < n) {
-          const Coef3<C> cz = ldcoef(L, z);
-          C diag = cadd(cadd(cx.d, cy.d), cz.d);
-          diag.x -= phi_at(L, x, y, z);
-          p = cmul(diag, v0);
-          p = cfma(cx.a, vl, p);
-          p = cfma(cx.c, vr, p);
-          p = cfma(cy.a, vs, p);
-          p = cfma(cy.c, vn, p);
-          p = cfma(cz.a, vm, p);
-          p = cfma(cz.c, vp, p);
-#pragma unroll
-          for (int k = 0; k < J; ++k) acc[k] = cdotacc(raw0[k], p, acc[k]);
-          accn += cabs2(p);
-        }
-        if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, z, P)] = p;
-      }
-      vm = v0;
-      v0 = vp;
-#pragma unroll
-      for (int k = 0; k < J; ++k) raw0[k] = rawn[k];
-    }
-  }
-  double red[2 * J + 1], tot[2 * J + 1];
-#pragma unroll
-  for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
-  red[2 * J] = accn;
-  if (grid_sum_last<2 * J + 1>(red, L.part, tile, ntiles, &sc->counter, sm, tot)) {
-    if (flat_tid() == 0) sweep_after_pass(sc, J, tot, SweepTau<C>::v);
-  }
-}
-
 // ------------------------------------------------------------------ sweep end
 // Coefficients of the sweep's update, staged in registers.
 template <typename C>
@@ -253,12 +77,12 @@ struct UpdCoef {
 template <typename C>
 __device__ __forceinline__ UpdCoef<C> load_upd(const LevelDev<C>& L, int r0_is_b) {
   UpdCoef<C> u;
-  const SweepScalars* sc = L.sc;
+  const auto* sc = L.sc;
   u.m = sc->m;
 #pragma unroll
   for (int k = 0; k <= SMAX; ++k) {
-    u.xc[k] = from_d<C>(sc->xcoef[k]);
-    u.rc[k] = from_d<C>(sc->rcoef[k]);
+    u.xc[k] = sc->xcoef[k];
+    u.rc[k] = sc->rcoef[k];
     u.Rk[k] = (k == 0) ? (r0_is_b ? L.b : L.r0) : L.p[k - 1];
   }
   return u;
@@ -286,10 +110,12 @@ template <typename C>
 __global__ void __launch_bounds__(256)
 k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mode, int r0_is_b, int xsel,
               int x_from_zero) {
-  __shared__ double sm[32];
+  __shared__ typename CT<C>::R sm[32];
+  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
+  pdl_wait();
   const UpdCoef<C> u = load_upd(L, r0_is_b);
   C* xo = xsel ? L.xb : L.xa;
   const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
@@ -309,7 +135,7 @@ k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mod
     }
   }
   if (!want_r) return;
-  double red[1] = {(double)acc}, tot[1];
+  typename CT<C>::R red[1] = {acc}, tot[1];
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
   }
@@ -320,10 +146,12 @@ k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mod
 template <typename Cin, typename C>
 __global__ void __launch_bounds__(256)
 k_load_input(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, const Cin* __restrict__ src) {
-  __shared__ double sm[32];
+  __shared__ typename CT<C>::R sm[32];
+  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
+  pdl_wait();
   const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
   typename CT<C>::R acc = 0;
   for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < npts; i += (size_t)ntiles * blockDim.x) {
@@ -335,7 +163,7 @@ k_load_input(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, const Ci
     L.b[i] = v;
     acc += cabs2(v);
   }
-  double red[1] = {(double)acc}, tot[1];
+  typename CT<C>::R red[1] = {acc}, tot[1];
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
   }
@@ -345,8 +173,10 @@ k_load_input(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, const Ci
 template <typename C, typename Cout>
 __global__ void __launch_bounds__(256)
 k_store_output(const LevelDev<C>* __restrict__ levs, int dim, Cout* __restrict__ dst) {
+  pdl_trigger();
   const LevelDev<C>& L = levs[0];
   const int n = L.n, P = L.P;
+  pdl_wait();
   const size_t npts = dim == 3 ? (size_t)n * n * n : (size_t)n * n;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % n);
@@ -356,266 +186,16 @@ k_store_output(const LevelDev<C>* __restrict__ levs, int dim, Cout* __restrict__
   }
 }
 
-// End of pre-smoothing, fused with full-weighting restriction (2D): x_a = x + dx,
-// r = R_0 - sum y_j p_j, b_c = FW(r) on the coarser grid, ||b_c||^2 starts the
-// coarse level's first sweep.  A warp covers 32 fine x (16 coarse) and an even run
-// of fine rows plus one halo row above.
-template <typename C>
-__global__ void __launch_bounds__(32 * WARPS2)
-k_restrict2(const LevelDev<C>* __restrict__ levs, int ntiles, int rows, int r0_is_b, int x_from_zero,
-            int nosmooth) {
-  typedef typename CT<C>::R R;
-  __shared__ double sm[32];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
-  const LevelDev<C>& L = levs[prob];
-  const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
-  const int ntx = ceil_div(P, 32);
-  const int tx = tile % ntx, ty = tile / ntx;
-  const int lane = threadIdx.x, warp = threadIdx.y;
-  const int x = tx * 32 + lane;
-  const int ybeg = (ty * WARPS2 + warp) * rows;
-  const int yend = min(ybeg + rows, P);
-  UpdCoef<C> u = load_upd(L, r0_is_b);
-  if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
-  R acc = 0;
-  if (ybeg < P) {
-    C cacc = czero<C>();
-    for (int y = ybeg; y <= yend; ++y) {
-      C dx, r;
-      upd_point(u, x, y, 0, n, P, dx, r);
-      if (y < yend && x < P) {
-        C xv = x_from_zero ? czero<C>() : L.xa[pidx(x, y, 0, P)];
-        L.xa[pidx(x, y, 0, P)] = (x < n && y < n) ? cadd(xv, dx) : czero<C>();
-      }
-      C rl = shfl_up_c(r, 1), rr = shfl_down_c(r, 1);
-      if (lane == 31) {
-        C d2;
-        upd_point(u, x + 1, y, 0, n, P, d2, rr);
-      }
-      // horizontal full weighting at odd x
-      C rh = cadd(cscale(r, (R)0.5), cscale(cadd(rl, rr), (R)0.25));
-      if ((y & 1) == 0) {
-        if (y > ybeg) {
-          cacc = cadd(cacc, cscale(rh, (R)0.25));
-          const int I = (y >> 1) - 1, Ix = x >> 1;
-          if ((x & 1) && Ix < Pc) {
-            const bool valid = (Ix < nc && I < nc);
-            C out = valid ? cacc : czero<C>();
-            L.bc[pidx(Ix, I, 0, Pc)] = out;
-            if (valid) acc += cabs2(out);
-          }
-        }
-        cacc = cscale(rh, (R)0.25);
-      } else {
-        cacc = cadd(cacc, cscale(rh, (R)0.5));
-      }
-    }
-  }
-  double red[1] = {(double)acc}, tot[1];
-  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
-    if (flat_tid() == 0) sweep_begin(L.scc, tot[0], L.s);
-  }
-}
-
-// 3D version: the CTA's warps 1..WY3+1 cover fine rows y0..y0+WY3 (one halo row);
-// horizontal weighting by shuffles, y-weighting through shared memory, z-weighting
-// in registers along the march (planes zbeg..zend, the last one a halo).
-template <typename C>
-__global__ void __launch_bounds__(32 * (WY3 + 2))
-k_restrict3(const LevelDev<C>* __restrict__ levs, int ntiles, int rows, int r0_is_b, int x_from_zero,
-            int nosmooth) {
-  typedef typename CT<C>::R R;
-  __shared__ double sm[32];
-  __shared__ C srh[2][WY3 + 2][32];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
-  const LevelDev<C>& L = levs[prob];
-  const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
-  const int ntx = ceil_div(P, 32), nty = ceil_div(P, WY3);
-  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-  const int lane = threadIdx.x, w = threadIdx.y;
-  const bool owned = (w >= 1 && w <= WY3);
-  const int x = tx * 32 + lane;
-  const int y = ty * WY3 - 1 + w;
-  const int zbeg = tz * rows;
-  const int zend = min(zbeg + rows, P);
-  UpdCoef<C> u = load_upd(L, r0_is_b);
-  if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
-  R acc = 0;
-  if (zbeg < P) {
-    C cacc = czero<C>();
-    for (int z = zbeg; z <= zend; ++z) {
-      C rh = czero<C>();
-      if (w >= 1) {
-        C dx, r;
-        upd_point(u, x, y, z, n, P, dx, r);
-        if (owned && z < zend && x < P && y < P) {
-          const size_t id = pidx(x, y, z, P);
-          C xv = x_from_zero ? czero<C>() : L.xa[id];
-          L.xa[id] = inside(x, y, z, n) ? cadd(xv, dx) : czero<C>();
-        }
-        C rl = shfl_up_c(r, 1), rr = shfl_down_c(r, 1);
-        if (lane == 31) {
-          C d2;
-          upd_point(u, x + 1, y, z, n, P, d2, rr);
-        }
-        rh = cadd(cscale(r, (R)0.5), cscale(cadd(rl, rr), (R)0.25));
-      }
-      srh[z & 1][w][lane] = rh;
-      __syncthreads();
-      // rows y odd (w even, y0 even) own a coarse row
-      if (owned && (y & 1)) {
-        C ry = cadd(cscale(rh, (R)0.5), cscale(cadd(srh[z & 1][w - 1][lane], srh[z & 1][w + 1][lane]), (R)0.25));
-        if ((z & 1) == 0) {
-          if (z > zbeg) {
-            cacc = cadd(cacc, cscale(ry, (R)0.25));
-            const int Iz = (z >> 1) - 1, Iy = y >> 1, Ix = x >> 1;
-            if ((x & 1) && Ix < Pc && Iy < Pc) {
-              const bool valid = (Ix < nc && Iy < nc && Iz < nc);
-              C out = valid ? cacc : czero<C>();
-              L.bc[pidx(Ix, Iy, Iz, Pc)] = out;
-              if (valid) acc += cabs2(out);
-            }
-          }
-          cacc = cscale(ry, (R)0.25);
-        } else {
-          cacc = cadd(cacc, cscale(ry, (R)0.5));
-        }
-      }
-    }
-  }
-  double red[1] = {(double)acc}, tot[1];
-  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
-    if (flat_tid() == 0) sweep_begin(L.scc, tot[0], L.s);
-  }
-}
-
 // ------------------------------------------------------------------ coarse correction
-// x_b = x_a + P e_c and r0 = b - M x_b (2D), ||r0||^2 starts post-smoothing.
-template <typename C>
-__global__ void __launch_bounds__(32 * WARPS2)
-k_prolong2(const LevelDev<C>* __restrict__ levs, int ntiles, int rows) {
-  typedef typename CT<C>::R R;
-  __shared__ double sm[32];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
-  const LevelDev<C>& L = levs[prob];
-  const int n = L.n, P = L.P;
-  const int ntx = ceil_div(P, 32);
-  const int tx = tile % ntx, ty = tile / ntx;
-  const int lane = threadIdx.x, warp = threadIdx.y;
-  const int x = tx * 32 + lane;
-  const int ybeg = (ty * WARPS2 + warp) * rows;
-  const int yend = min(ybeg + rows, P);
-  const Coef3<C> cx = ldcoef(L, x);
-  auto form = [&](int xx, int yy) -> C {
-    return cadd(ldc((const C*)L.xa, xx, yy, 0, n, P), interp(L, xx, yy, 0, 2));
-  };
-  R acc = 0;
-  if (ybeg < P) {
-    C vm = form(x, ybeg - 1), v0 = form(x, ybeg);
-    for (int y = ybeg; y < yend; ++y) {
-      C vp = form(x, y + 1);
-      C vl = shfl_up_c(v0, 1), vr = shfl_down_c(v0, 1);
-      if (lane == 0) vl = form(x - 1, y);
-      if (lane == 31) vr = form(x + 1, y);
-      if (x < P) {
-        C r = czero<C>(), xo = czero<C>();
-        if (x < n && y < n) {
-          const Coef3<C> cy = ldcoef(L, y);
-          C diag = cadd(cx.d, cy.d);
-          diag.x -= phi_at(L, x, y, 0);
-          C p = cmul(diag, v0);
-          p = cfma(cx.a, vl, p);
-          p = cfma(cx.c, vr, p);
-          p = cfma(cy.a, vm, p);
-          p = cfma(cy.c, vp, p);
-          r = csub(__ldg(L.b + pidx(x, y, 0, P)), p);
-          xo = v0;
-          acc += cabs2(r);
-        }
-        L.xb[pidx(x, y, 0, P)] = xo;
-        L.r0[pidx(x, y, 0, P)] = r;
-      }
-      vm = v0;
-      v0 = vp;
-    }
-  }
-  double red[1] = {(double)acc}, tot[1];
-  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
-    if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
-  }
-}
-
-template <typename C>
-__global__ void __launch_bounds__(32 * (WY3 + 2))
-k_prolong3(const LevelDev<C>* __restrict__ levs, int ntiles, int rows) {
-  typedef typename CT<C>::R R;
-  __shared__ double sm[32];
-  __shared__ C sv[2][WY3 + 2][32];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
-  const LevelDev<C>& L = levs[prob];
-  const int n = L.n, P = L.P;
-  const int ntx = ceil_div(P, 32), nty = ceil_div(P, WY3);
-  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-  const int lane = threadIdx.x, w = threadIdx.y;
-  const bool owned = (w >= 1 && w <= WY3);
-  const int x = tx * 32 + lane;
-  const int y = ty * WY3 - 1 + w;
-  const int zbeg = tz * rows;
-  const int zend = min(zbeg + rows, P);
-  const Coef3<C> cx = ldcoef(L, x), cy = ldcoef(L, y);
-  auto form = [&](int xx, int yy, int zz) -> C {
-    return cadd(ldc((const C*)L.xa, xx, yy, zz, n, P), interp(L, xx, yy, zz, 3));
-  };
-  R acc = 0;
-  if (zbeg < P) {
-    C vm = form(x, y, zbeg - 1), v0 = form(x, y, zbeg);
-    for (int z = zbeg; z < zend; ++z) {
-      C vp = form(x, y, z + 1);
-      sv[z & 1][w][lane] = v0;
-      __syncthreads();
-      if (owned) {
-        C vs = sv[z & 1][w - 1][lane], vn = sv[z & 1][w + 1][lane];
-        C vl = shfl_up_c(v0, 1), vr = shfl_down_c(v0, 1);
-        if (lane == 0) vl = form(x - 1, y, z);
-        if (lane == 31) vr = form(x + 1, y, z);
-        if (x < P && y < P) {
-          C r = czero<C>(), xo = czero<C>();
-          if (inside(x, y, z, n)) {
-            const Coef3<C> cz = ldcoef(L, z);
-            C diag = cadd(cadd(cx.d, cy.d), cz.d);
-            diag.x -= phi_at(L, x, y, z);
-            C p = cmul(diag, v0);
-            p = cfma(cx.a, vl, p);
-            p = cfma(cx.c, vr, p);
-            p = cfma(cy.a, vs, p);
-            p = cfma(cy.c, vn, p);
-            p = cfma(cz.a, vm, p);
-            p = cfma(cz.c, vp, p);
-            r = csub(__ldg(L.b + pidx(x, y, z, P)), p);
-            xo = v0;
-            acc += cabs2(r);
-          }
-          L.xb[pidx(x, y, z, P)] = xo;
-          L.r0[pidx(x, y, z, P)] = r;
-        }
-      }
-      vm = v0;
-      v0 = vp;
-    }
-  }
-  double red[1] = {(double)acc}, tot[1];
-  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
-    if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
-  }
-}
-
 // Coarse correction without post-smoothing (nu2 = 0): x_b = x_a + P e_c, pointwise.
 template <typename C>
 __global__ void __launch_bounds__(256)
 k_prolong_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim) {
+  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
+  pdl_wait();
   const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
   for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < npts; i += (size_t)ntiles * blockDim.x) {
     const int x = (int)(i % P), y = (int)((i / P) % P), z = dim == 3 ? (int)(i / ((size_t)P * P)) : 0;
@@ -664,9 +244,9 @@ __device__ __forceinline__ void cblock_coords(size_t i, int P, int dim, int& x, 
 // is left in `tmp` for the caller.
 template <typename C>
 __device__ void cblock_sweep(const LevelDev<C>& L, int dim, int r0_is_b, C* xo, int x_from_zero, C* tmp,
-                             int end_mode, double* sm) {
+                             int end_mode, typename CT<C>::R* sm) {
   typedef typename CT<C>::R R;
-  SweepScalars* sc = L.sc;
+  auto* sc = L.sc;
   const int P = L.P, n = L.n;
   const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
   const int tid = flat_tid(), nth = block_threads();
@@ -679,13 +259,13 @@ __device__ void cblock_sweep(const LevelDev<C>& L, int dim, int r0_is_b, C* xo, 
       C v = czero<C>();
       for (int k = 0; k < J; ++k) {
         const C* Rk = k == 0 ? R0 : L.p[k - 1];
-        v = cfma(from_d<C>(sc->Cf[J][k]), Rk[i], v);
+        v = cfma(sc->Cf[J][k], Rk[i], v);
       }
       tmp[i] = v;
     }
     __syncthreads();
-    double red[2 * SMAX + 1];
-    for (int q = 0; q < 2 * SMAX + 1; ++q) red[q] = 0.0;
+    R red[2 * SMAX + 1];
+    for (int q = 0; q < 2 * SMAX + 1; ++q) red[q] = (R)0;
     C acc[SMAX];
     for (int k = 0; k < SMAX; ++k) acc[k] = czero<C>();
     R accn = 0;
@@ -702,17 +282,13 @@ __device__ void cblock_sweep(const LevelDev<C>& L, int dim, int r0_is_b, C* xo, 
     }
     for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
     red[2 * J] = accn;
-    block_sum<2 * SMAX + 1>(red, sm);
-    if (tid == 0) {
-      double tot[2 * SMAX + 1];
-      for (int q = 0; q < 2 * SMAX + 1; ++q) tot[q] = red[q];
-      sweep_after_pass(sc, J, tot, SweepTau<C>::v);
-    }
+    block_sum<2 * SMAX + 1, R>(red, sm);
+    if (tid == 0) sweep_after_pass_rt<R>(sc, J, red);
   }
   __syncthreads();
   const int m = sc->m;
   C xc[SMAX + 1], rc[SMAX + 1];
-  for (int k = 0; k <= SMAX; ++k) { xc[k] = from_d<C>(sc->xcoef[k]); rc[k] = from_d<C>(sc->rcoef[k]); }
+  for (int k = 0; k <= SMAX; ++k) { xc[k] = sc->xcoef[k]; rc[k] = sc->rcoef[k]; }
   __syncthreads();
   R accr = 0;
   for (size_t i = tid; i < npts; i += nth) {
@@ -727,21 +303,21 @@ __device__ void cblock_sweep(const LevelDev<C>& L, int dim, int r0_is_b, C* xo, 
     if (end_mode == UPD_RESTRICT) tmp[i] = r;
   }
   if (end_mode == UPD_RESIDUAL) {
-    double red[1] = {(double)accr};
-    block_sum<1>(red, sm);
+    R red[1] = {accr};
+    block_sum<1, R>(red, sm);
     if (tid == 0) sweep_begin(sc, red[0], L.s);
   }
   __syncthreads();
 }
 
+// The whole sub-cycle of levels Ls[0..nlev-1] (Ls[nlev-1] the coarsest, solved by
+// LU) in one CTA; the level vectors and sweep scalars may live in global or shared
+// memory (plain loads only).  `sm` needs 32 * (2 SMAX + 1) doubles.
 template <typename C>
-__global__ void __launch_bounds__(1024)
-k_coarse(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride, const CoarseLU* __restrict__ lus,
-         int nu1, int nu2, int dim) {
+__device__ void coarse_cycle(const LevelDev<C>* Ls, int nlev, const CoarseLU& lu, int nu1, int nu2, int dim,
+                             double* smd) {
   typedef typename CT<C>::R R;
-  __shared__ double sm[32 * (2 * SMAX + 1)];
-  const int prob = blockIdx.x;
-  const LevelDev<C>* Ls = levs_all + (size_t)prob * lev_stride;
+  R* sm = reinterpret_cast<R*>(smd);
   const int tid = flat_tid(), nth = block_threads();
   // descent
   for (int l = 0; l < nlev - 1; ++l) {
@@ -776,17 +352,16 @@ k_coarse(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride, con
       }
       L.bc[i] = out;
     }
-    double red[1] = {(double)acc};
-    block_sum<1>(red, sm);
+    R red[1] = {acc};
+    block_sum<1, R>(red, sm);
     if (tid == 0) sweep_begin(L.scc, red[0], L.s);
     __syncthreads();
   }
   // coarsest: dense LU solve in FP64 by warp 0
   {
     const LevelDev<C>& L = Ls[nlev - 1];
-    const CoarseLU& lu = lus[prob];
     const int m = lu.m, P = L.P, n = L.n;
-    double2* yv = reinterpret_cast<double2*>(sm);  // m <= 64 complex values
+    double2* yv = reinterpret_cast<double2*>(smd);  // m <= 144 complex values
     if (tid < 32) {
       for (int i = tid; i < m; i += 32) {
         const int src = lu.piv[i];
@@ -844,13 +419,79 @@ k_coarse(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride, con
         }
         L.r0[i] = r;
       }
-      double red[1] = {(double)acc};
-      block_sum<1>(red, sm);
+      R red[1] = {acc};
+      block_sum<1, R>(red, sm);
       if (tid == 0) sweep_begin(L.sc, red[0], L.s);
       __syncthreads();
       for (int sw = 0; sw < nu2; ++sw)
         cblock_sweep(L, dim, 0, L.xb, 0, L.xa, sw == nu2 - 1 ? UPD_XONLY : UPD_RESIDUAL, sm);
     }
+  }
+}
+
+
+// Coarse sub-cycle with the levels in global memory (any size).
+template <typename C>
+__global__ void __launch_bounds__(1024)
+k_coarse(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride, const CoarseLU* __restrict__ lus,
+         int nu1, int nu2, int dim) {
+  __shared__ double sm[32 * (2 * SMAX + 1)];
+  pdl_trigger();
+  pdl_wait();
+  const int prob = blockIdx.x;
+  coarse_cycle<C>(levs_all + (size_t)prob * lev_stride, nlev, lus[prob], nu1, nu2, dim, sm);
+}
+
+// Coarse sub-cycle with every level's vectors, descriptors and sweep scalars staged
+// in shared memory; only the top coarse level's right-hand side (and its sweep state)
+// comes from global memory and only its result goes back.
+constexpr int MAX_COARSE_LEVELS = 8;
+template <typename C>
+__global__ void __launch_bounds__(512)
+k_coarse_smem(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride, const CoarseLU* __restrict__ lus,
+              int nu1, int nu2, int dim) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sm[32 * (2 * SMAX + 1)];
+  __shared__ LevelDev<C> Ls[MAX_COARSE_LEVELS];
+  __shared__ SweepScalarsT<typename CT<C>::R> Ss[MAX_COARSE_LEVELS];
+  pdl_trigger();
+  const int prob = blockIdx.x;
+  const LevelDev<C>* G = levs_all + (size_t)prob * lev_stride;
+  const int tid = flat_tid(), nth = block_threads();
+  pdl_wait();
+  if (tid == 0) {
+    C* cur = reinterpret_cast<C*>(smraw);
+    for (int l = 0; l < nlev; ++l) {
+      Ls[l] = G[l];
+      const size_t np = dim == 3 ? (size_t)G[l].P * G[l].P * G[l].P : (size_t)G[l].P * G[l].P;
+      Ls[l].b = cur; cur += np;
+      Ls[l].xa = cur; cur += np;
+      Ls[l].xb = cur; cur += np;
+      Ls[l].r0 = cur; cur += np;
+      for (int j = 0; j < G[l].s; ++j) { Ls[l].p[j] = cur; cur += np; }
+      Ls[l].sc = &Ss[l];
+    }
+    for (int l = 0; l + 1 < nlev; ++l) {
+      Ls[l].bc = Ls[l + 1].b;
+      Ls[l].xcb = Ls[l + 1].xb;
+      Ls[l].scc = &Ss[l + 1];
+    }
+  }
+  __syncthreads();
+  {
+    const size_t np0 = dim == 3 ? (size_t)G[0].P * G[0].P * G[0].P : (size_t)G[0].P * G[0].P;
+    for (size_t i = tid; i < np0; i += nth) Ls[0].b[i] = G[0].b[i];
+    const int* src = reinterpret_cast<const int*>(G[0].sc);
+    int* dst = reinterpret_cast<int*>(&Ss[0]);
+    const int words = sweep_words<typename CT<C>::R>();
+    for (int i = tid; i < words; i += nth) dst[i] = src[i];
+  }
+  __syncthreads();
+  coarse_cycle<C>(Ls, nlev, lus[prob], nu1, nu2, dim, sm);
+  __syncthreads();
+  {
+    const size_t np0 = dim == 3 ? (size_t)G[0].P * G[0].P * G[0].P : (size_t)G[0].P * G[0].P;
+    for (size_t i = tid; i < np0; i += nth) G[0].xb[i] = Ls[0].xb[i];
   }
 }
 

@@ -1,19 +1,50 @@
 // Host launchers of the V-cycle kernels, instantiated once per precision in
 // vcycle_c64.cu and vcycle_c128.cu (two translation units compile in parallel).
 #pragma once
-#include "vcycle.cuh"
+#include "tiles.cuh"
 #include <algorithm>
 #include "../../include/helm.h"
 
 namespace helm {
 
+// Launch with programmatic stream serialisation: the kernel may start while its
+// predecessor finishes and synchronises with it through griddepcontrol.wait.
+// Only grids that fit in one wave use it: they are latency-bound, while a
+// multi-wave grid gains nothing from an early start of its successor.
+static inline int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+template <typename... KArgs, typename... Args>
+static inline void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  const bool one_wave = (long long)grid.x * grid.y * grid.z <= 2LL * sm_count();
+  cfg.attrs = one_wave ? attr : nullptr;
+  cfg.numAttrs = one_wave ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename C, int J>
 static void arnoldi_J(int dim, const LevelDev<C>* levs, int grid, int ntiles, TileCfg cfg, bool r0_is_b,
                       bool store_p, cudaStream_t st) {
   if (dim == 2)
-    k_arnoldi2<C, J><<<grid, dim3(32, WARPS2), 0, st>>>(levs, ntiles, cfg.rows, r0_is_b, store_p);
+    pdl_launch(k_arnoldi_t2<C, J>, dim3(grid), dim3(dim3(32, 8)), 0, st, levs, ntiles, r0_is_b, store_p);
   else
-    k_arnoldi3<C, J><<<grid, dim3(32, WY3 + 2), 0, st>>>(levs, ntiles, cfg.rows, r0_is_b, store_p);
+    pdl_launch(k_arnoldi_t3<C, J>, dim3(grid), dim3(dim3(32, 8)), 0, st, levs, ntiles, cfg.rows, r0_is_b, store_p);
 }
 
 template <typename C>
@@ -32,43 +63,59 @@ template <typename C>
 void launch_restrict(int dim, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
                      bool x_from_zero, bool nosmooth, cudaStream_t st) {
   if (dim == 2)
-    k_restrict2<C><<<nprob * ntiles, dim3(32, WARPS2), 0, st>>>(levs, ntiles, cfg.rows, r0_is_b, x_from_zero,
-                                                                nosmooth);
+    pdl_launch(k_restrict_t2<C>, dim3(nprob * ntiles), dim3(dim3(32, 8)), 0, st, levs, ntiles, r0_is_b, x_from_zero, nosmooth);
   else
-    k_restrict3<C><<<nprob * ntiles, dim3(32, WY3 + 2), 0, st>>>(levs, ntiles, cfg.rows, r0_is_b, x_from_zero,
-                                                                 nosmooth);
+    pdl_launch(k_restrict_t3<C>, dim3(nprob * ntiles), dim3(dim3(32, 8)), 0, st, levs, ntiles, cfg.rows, r0_is_b, x_from_zero, nosmooth);
 }
 
 template <typename C>
 void launch_update_flat(int dim, UpdateMode mode, const LevelDev<C>* levs, int nprob, int ntiles, bool r0_is_b,
                         int xsel, bool x_from_zero, cudaStream_t st) {
-  k_update_flat<C><<<nprob * ntiles, 256, 0, st>>>(levs, ntiles, dim, (int)mode, r0_is_b, xsel, x_from_zero);
+  pdl_launch(k_update_flat<C>, dim3(nprob * ntiles), dim3(256), 0, st, levs, ntiles, dim, (int)mode, r0_is_b, xsel, x_from_zero);
 }
 
 template <typename C>
 void launch_prolong(int dim, bool with_residual, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg,
                     cudaStream_t st) {
   if (!with_residual) {
-    k_prolong_flat<C><<<nprob * ntiles, 256, 0, st>>>(levs, ntiles, dim);
+    pdl_launch(k_prolong_flat<C>, dim3(nprob * ntiles), dim3(256), 0, st, levs, ntiles, dim);
   } else if (dim == 2) {
-    k_prolong2<C><<<nprob * ntiles, dim3(32, WARPS2), 0, st>>>(levs, ntiles, cfg.rows);
+    pdl_launch(k_prolong_t2<C>, dim3(nprob * ntiles), dim3(dim3(32, 8)), 0, st, levs, ntiles);
   } else {
-    k_prolong3<C><<<nprob * ntiles, dim3(32, WY3 + 2), 0, st>>>(levs, ntiles, cfg.rows);
+    pdl_launch(k_prolong_t3<C>, dim3(nprob * ntiles), dim3(dim3(32, 8)), 0, st, levs, ntiles, cfg.rows);
   }
 }
 
 template <typename C>
 void launch_coarse(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
                    int nu1, int nu2, cudaStream_t st) {
-  k_coarse<C><<<nprob, 1024, 0, st>>>(levs, nlev, lev_stride, lus, nu1, nu2, dim);
+  pdl_launch(k_coarse<C>, dim3(nprob), dim3(1024), 0, st, levs, nlev, lev_stride, lus, nu1, nu2, dim);
+}
+
+template <typename C>
+void launch_coarse_smem(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
+                        int nu1, int nu2, size_t smem_bytes, cudaStream_t st) {
+  // the static part (descriptors, sweep scalars) counts against the same limit: allow
+  // the largest dynamic part the device offers, once
+  static bool configured = false;
+  if (!configured) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (cudaFuncGetAttributes(&fa, k_coarse_smem<C>) == cudaSuccess && optin > (int)fa.sharedSizeBytes)
+      cudaFuncSetAttribute(k_coarse_smem<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    configured = true;
+  }
+  pdl_launch(k_coarse_smem<C>, dim3(nprob), dim3(512), smem_bytes, st, levs, nlev, lev_stride, lus, nu1, nu2, dim);
 }
 
 template <typename C>
 void launch_load_input(int dim, const LevelDev<C>* levs, int ntiles, const void* src, int in_prec, cudaStream_t st) {
   if (in_prec == HELM_C128)
-    k_load_input<double2, C><<<ntiles, 256, 0, st>>>(levs, ntiles, dim, (const double2*)src);
+    pdl_launch(k_load_input<double2, C>, dim3(ntiles), dim3(256), 0, st, levs, ntiles, dim, (const double2*)src);
   else
-    k_load_input<float2, C><<<ntiles, 256, 0, st>>>(levs, ntiles, dim, (const float2*)src);
+    pdl_launch(k_load_input<float2, C>, dim3(ntiles), dim3(256), 0, st, levs, ntiles, dim, (const float2*)src);
 }
 
 template <typename C>
@@ -76,9 +123,9 @@ void launch_store_output(int dim, int n, const LevelDev<C>* levs, void* dst, int
   const size_t npts = dim == 3 ? (size_t)n * n * n : (size_t)n * n;
   const int grid = (int)std::min<size_t>((npts + 255) / 256, 4096);
   if (out_prec == HELM_C128)
-    k_store_output<C, double2><<<grid, 256, 0, st>>>(levs, dim, (double2*)dst);
+    pdl_launch(k_store_output<C, double2>, dim3(grid), dim3(256), 0, st, levs, dim, (double2*)dst);
   else
-    k_store_output<C, float2><<<grid, 256, 0, st>>>(levs, dim, (float2*)dst);
+    pdl_launch(k_store_output<C, float2>, dim3(grid), dim3(256), 0, st, levs, dim, (float2*)dst);
 }
 
 #define HELM_VCYCLE_INST(C)                                                                                   \
@@ -90,6 +137,8 @@ void launch_store_output(int dim, int n, const LevelDev<C>* levs, void* dst, int
   template void launch_prolong<C>(int, bool, const LevelDev<C>*, int, int, TileCfg, cudaStream_t);            \
   template void launch_coarse<C>(int, const LevelDev<C>*, int, int, const CoarseLU*, int, int, int,           \
                                  cudaStream_t);                                                               \
+  template void launch_coarse_smem<C>(int, const LevelDev<C>*, int, int, const CoarseLU*, int, int, int, size_t, \
+                                      cudaStream_t);                                                          \
   template void launch_load_input<C>(int, const LevelDev<C>*, int, const void*, int, cudaStream_t);           \
   template void launch_store_output<C>(int, int, const LevelDev<C>*, void*, int, cudaStream_t);
 

@@ -32,7 +32,8 @@ _STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ENOCONV
 # names declared in include/helm.h (checked by the CPU test suite)
 EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_operator", "helm_solve",
            "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_last_error",
-           "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc")
+           "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc",
+           "helm_batch_solve_host")
 
 
 class HelmError(RuntimeError):
@@ -84,6 +85,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_batch_solve.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp), dp,
                                      ctypes.POINTER(helm_info), vp]
     lib.helm_batch_solve.restype = ip
+    lib.helm_batch_solve_host.argtypes = lib.helm_batch_solve.argtypes
+    lib.helm_batch_solve_host.restype = ip
     lib.helm_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.helm_workspace_bytes.restype = ip
     lib.helm_levels.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
@@ -246,5 +249,18 @@ def batch_solve(handles: Sequence[Handle], bs, xs, tol: float, stream=None):
     xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
     infos = (helm_info * n)()
     _check(load().helm_batch_solve(hs, n, bp, xp, float(tol), infos, _stream(stream)),
+           allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
+    return [Info.of(infos[i]) for i in range(n)]
+
+
+def batch_solve_host(handles: Sequence[Handle], bs, xs, tol: float, stream=None):
+    """helm_batch_solve_host: host arrays (numpy complex128 or pinned tensors)."""
+    n = len(handles)
+    hp = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+    addr = lambda a: a.ctypes.data if hasattr(a, "ctypes") else _ptr(a)
+    bp = (ctypes.c_void_p * n)(*[addr(b) for b in bs])
+    xp = (ctypes.c_void_p * n)(*[addr(x) for x in xs])
+    infos = (helm_info * n)()
+    _check(load().helm_batch_solve_host(hp, n, bp, xp, float(tol), infos, _stream(stream)),
            allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
     return [Info.of(infos[i]) for i in range(n)]
