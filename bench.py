@@ -361,6 +361,205 @@ def run_precond(args):
           flush=True)
 
 
+def _seq_solves(helm, works, precision, bs, xs):
+    """Solve `works` one at a time on fresh handles of `precision` (each timed with CUDA
+    events after one untimed solve of the same handle); returns per-problem seconds and
+    infos."""
+    import torch
+    times, infos = [], []
+    for w, b, x in zip(works, bs, xs):
+        h = helm.Handle(w.dim, w.n, w.theta_beta, k=w.k, precision=precision, restart=w.restart, maxit=400)
+        x.zero_()
+        h.solve(b, x, w.tol)   # graph capture, first touch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        info = h.solve(b, x, w.tol)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+        infos.append(info)
+        h.close()
+    return times, infos
+
+
+def run_batch(args):
+    """64 independent 2D problems (n in {255, 511, 1023}, kh ~ U[0.1, 0.3], theta_beta
+    0.3, random sources, FGMRES(40) to 1e-6): one step = all 64 solved together with
+    helm_batch_solve (every V-cycle level and outer kernel is one launch for all
+    problems of that size).  Compared with the same problems solved one at a time with
+    the complex128 (FP64) preconditioner and with the complex64 one."""
+    import torch
+
+    from paper_1012_5379_gb300 import helm
+    dev = torch.device("cuda", 0)
+    works = I.batch_2d(args.batch)
+    bs = [torch.from_numpy(w.b).to(dev) for w in works]
+    xs = [torch.zeros_like(b) for b in bs]
+    handles = [helm.Handle(w.dim, w.n, w.theta_beta, k=w.k, precision="c64", restart=w.restart, maxit=400)
+               for w in works]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        for x in xs:
+            x.zero_()
+        infos = helm.batch_solve(handles, bs, xs, TOL)
+        bad = [i for i in infos if i.status != 0]
+        if bad:
+            raise RuntimeError(f"{len(bad)} solves did not converge: {bad[0]}")
+        return infos
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(0)
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = helm.launch_count()
+    ms, all_infos = [], []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        all_infos.append(step())
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = helm.launch_count() - launches0
+    clocks = sampler.stop()
+    t = sum(ms) * 1e-3
+    work = sum(float(w.n) ** 2 * i.iters for infos in all_infos for w, i in zip(works, infos))
+    for h in handles:
+        h.close()
+    del handles
+    torch.cuda.empty_cache()
+    seq = {}
+    for prec in ("c128", "c64"):
+        times, infos = _seq_solves(helm, works, prec, bs, xs)
+        seq[prec] = {"solves_per_s": len(works) / sum(times), "s_total": sum(times),
+                     "iters_total": sum(i.iters for i in infos),
+                     "max_rel_res_true": max(i.rel_res_true for i in infos)}
+    infos = all_infos[-1]
+    sizes = {}
+    for w in works:
+        sizes[w.n] = sizes.get(w.n, 0) + 1
+    line = {"mode": "batch", "metric": "solves/s", "value": len(works) * args.steps / t, "unit": "solves/s",
+            "higher_is_better": True, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "vcycle_mpts_per_s": work / t / 1e6, "gpu_launches": int(launches), "clocks": clocks,
+            "config": {"workload": f"{len(works)} independent 2D problems, sizes {sizes}, kh ~ U[0.1,0.3], "
+                                   "theta_beta 0.3, unit-variance complex normal sources (seed 1003), "
+                                   "FGMRES(40) to 1e-6, complex64 V(1,1)-GMRES(3) / FP64 outer",
+                       "l2": "flushed between steps"},
+            "iters_total": sum(i.iters for i in infos), "max_rel_res_true": max(i.rel_res_true for i in infos),
+            "sequential": seq,
+            "speedup_vs_sequential_c128": (len(works) * args.steps / t) / seq["c128"]["solves_per_s"],
+            "ms_steps": ms}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson stream of solve requests through helm_serve_* (continuous batching under
+    a device-memory budget): solves/s over the stream and p50/p99 latency (submission to
+    completion).  The same stream served one request at a time by the complex128
+    (FP64) solver is simulated from measured per-request solve times of a sample."""
+    import threading
+
+    import torch
+
+    from paper_1012_5379_gb300 import helm
+    stream = I.request_stream(count=args.requests, rate=args.rate)
+    shapes = sorted({(r.work.dim, r.work.n) for r in stream})
+    # sources: two seeded arrays per shape, page-locked, shared by that shape's requests
+    srcs, xbuf = {}, {}
+    for sh in shapes:
+        srcs[sh] = [torch.from_numpy(I.request_source(j, *sh)).pin_memory() for j in range(2)]
+        xbuf[sh] = [torch.empty_like(srcs[sh][0]).pin_memory() for _ in range(2)]
+    budget = int(args.budget_gb * 1e9)
+    srv = helm.Server(budget_bytes=budget, precision="c64", restart=40, maxit=400)
+    # warm-up: one request per shape creates that shape's first slot
+    for sh in shapes:
+        t = srv.submit(sh[0], sh[1], 0.2 * (sh[1] + 1), 0.3, srcs[sh][0], xbuf[sh][0], TOL)
+        srv.wait(t)
+    st0 = srv.stats()
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = helm.launch_count()
+    results = [None] * len(stream)
+    tickets = [None] * len(stream)
+    submit_t = [0.0] * len(stream)
+    ready = threading.Semaphore(0)
+
+    def collector():
+        for i in range(len(stream)):
+            ready.acquire()
+            info, lat, rc = srv.wait(tickets[i], timeout=3600.0)
+            results[i] = (info, lat, rc)
+
+    th = threading.Thread(target=collector)
+    th.start()
+    t0 = time.perf_counter()
+    for i, r in enumerate(stream):
+        dt = t0 + r.arrival - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        sh = (r.work.dim, r.work.n)
+        submit_t[i] = time.perf_counter() - t0
+        tickets[i] = srv.submit(sh[0], sh[1], r.work.k, r.work.theta_beta, srcs[sh][i % 2], xbuf[sh][i % 2],
+                                r.work.tol)
+        ready.release()
+    th.join()
+    launches = helm.launch_count() - launches0
+    clocks = sampler.stop()
+    stats = srv.stats()
+    srv.stop()
+    lat = np.array([x[1] for x in results])
+    done = np.array(submit_t) + lat
+    t_total = float(done.max())
+    ok = sum(1 for x in results if x[2] == 0)
+    work = sum(float(r.work.n) ** r.work.dim * x[0].iters for r, x in zip(stream, results))
+    torch.cuda.empty_cache()
+    # sequential complex128 baseline: per-shape solve time from a sample of the stream's requests
+    seq = {}
+    for prec in ("c128", "c64"):
+        per_shape = {}
+        for sh in shapes:
+            sample = [r for r in stream if (r.work.dim, r.work.n) == sh][:args.seq_sample]
+            bs = [srcs[sh][0].to("cuda") for _ in sample]
+            xs = [torch.zeros_like(b) for b in bs]
+            times, _ = _seq_solves(helm, [r.work for r in sample], prec, bs, xs)
+            per_shape[sh] = float(np.mean(times))
+            del bs, xs
+            torch.cuda.empty_cache()
+        svc = np.array([per_shape[(r.work.dim, r.work.n)] for r in stream])
+        arr = np.array([r.arrival for r in stream])
+        fin = np.empty_like(arr)
+        prev = 0.0
+        for i in range(len(arr)):           # one server, first come first served
+            prev = max(arr[i], prev) + svc[i]
+            fin[i] = prev
+        slat = fin - arr
+        seq[prec] = {"solves_per_s": len(stream) / float(fin.max()), "p50_s": float(np.percentile(slat, 50)),
+                     "p99_s": float(np.percentile(slat, 99)),
+                     "solve_s_per_shape": {f"{d}D {n}": v for (d, n), v in per_shape.items()}}
+    line = {"mode": "serve", "metric": "solves/s", "value": len(stream) / t_total, "unit": "solves/s",
+            "higher_is_better": True, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "requests": len(stream), "ok": ok, "rate_per_s": args.rate,
+            "vcycle_mpts_per_s": work / t_total / 1e6, "gpu_launches": int(launches), "clocks": clocks,
+            "max_rel_res_true": max(x[0].rel_res_true for x in results),
+            "server": {k: stats[k] - st0.get(k, 0) if k in ("completed", "submitted", "handles_created",
+                                                           "handles_reused") else stats[k]
+                       for k in stats},
+            "config": {"workload": f"Poisson arrivals, mean {args.rate}/s, {len(stream)} requests, shapes uniform "
+                                   f"over {shapes}, kh ~ U[0.1,0.3], theta_beta 0.3, FGMRES(40) to 1e-6, "
+                                   "complex64 V(1,1)-GMRES(3) / FP64 outer",
+                       "budget_bytes": budget,
+                       "sources": "two seeded unit-variance complex normal sources per shape (pinned), "
+                                  "request i uses source i mod 2; solutions land in pinned buffers"},
+            "sequential_simulated": seq,
+            "speedup_vs_sequential_c128": (len(stream) / t_total) / seq["c128"]["solves_per_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,15 +571,20 @@ def main():
     ap.add_argument("--sequential-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "precond"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve"], default="solve")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--seq-sample", type=int, default=2)
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=4095)
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
-    if args.mode == "precond":
+    if args.mode != "solve":
         from paper_1012_5379_gb300 import build
         build.build()
-        run_precond(args)
+        {"precond": run_precond, "batch": run_batch, "serve": run_serve}[args.mode](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

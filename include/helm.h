@@ -147,6 +147,66 @@ int helm_batch_solve(helm_handle* const* hs, int count, const double* const* b,
 int helm_batch_solve_host(helm_handle* const* hs, int count, const double* const* b_host,
                           double* const* x_host, double tol, helm_info* infos, void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Serving: continuous batching of solves (the workload of Sec. 5 as a service).
+ * A worker thread owns the device.  Between outer FGMRES iterations it admits queued
+ * requests in arrival order while the device-memory budget allows, iterates every
+ * admitted problem of a dimension together (one launch per V-cycle level and outer
+ * kernel for all of them; 2D and 3D on separate streams, so their kernels overlap),
+ * and retires problems as they converge.  Idle problem slots of the same shape are
+ * reused.  A result is bitwise the same whatever other requests shared its launches.
+ * The paper has no counterpart: this is the deployment interface of the solver.
+ * --------------------------------------------------------------------------------- */
+typedef struct helm_server helm_server;
+
+typedef struct {
+  size_t budget_bytes; /* device memory the server's problem slots may hold    [120 GiB] */
+  int max_active;      /* problems iterated at once, 0 = bounded by the budget [0] */
+  int precond_prec;    /* HELM_C64 or HELM_C128                                [HELM_C64] */
+  int restart;         /* FGMRES restart of every request                       [40] */
+  int maxit;           /* max outer iterations of every request                 [400] */
+  int nu1, nu2, s;     /* V(nu1, nu2) with GMRES(s)                             [1, 1, 3] */
+  double ecs_frac;     /* layer width of every request's grid                   [0.125] */
+  double theta_gamma;  /* layer angle                                           [0.5] */
+} helm_serve_opts;
+
+typedef struct {
+  long long submitted, completed, rejected;
+  int queued, active, peak_active;
+  size_t bytes_in_use, peak_bytes;
+  int handles_created, handles_reused;
+} helm_serve_counters;
+
+/* Start a server on the current device (opts may be NULL: all defaults). */
+int helm_serve_start(const helm_serve_opts* opts, helm_server** out);
+
+/* Queue a solve of H x = b: grid (dim, n) with n + 1 a power of two, constant
+ * wavenumber k, CSG angle theta_beta, tolerance tol.  b_host and x_host are HOST
+ * arrays of n^dim complex128 (interleaved re, im; x fastest) that the server BORROWS:
+ * the caller keeps b unchanged and both alive until the ticket completes; the solution
+ * is written into x_host.  Page-locked buffers (cudaHostAlloc) let their copies
+ * overlap with other requests' work; pageable ones are copied synchronously by the
+ * worker.  Returns a ticket; never blocks on the device.  HELM_EINVAL for invalid
+ * arguments or a stopping server. */
+int helm_serve_submit(helm_server* s, int dim, int n, double k, double theta_beta, const double* b_host,
+                      double* x_host, double tol, long long* ticket);
+
+/* If the request is finished (its solution is in x_host): fill info and latency_s
+ * (submit to completion, seconds; both may be NULL), release the ticket and return
+ * its status (HELM_OK, HELM_ENOCONV, HELM_ENUMERIC, or HELM_ENOMEM when the request
+ * can never fit the budget).  HELM_EAGAIN while pending. */
+int helm_serve_poll(helm_server* s, long long ticket, helm_info* info, double* latency_s);
+
+/* As helm_serve_poll, waiting at most timeout_s seconds (HELM_ETIMEOUT). */
+int helm_serve_wait(helm_server* s, long long ticket, double timeout_s, helm_info* info, double* latency_s);
+
+/* Counters of the server (a consistent snapshot). */
+int helm_serve_stats(helm_server* s, helm_serve_counters* out);
+
+/* Finish every queued and admitted request, then stop the worker and free the
+ * device memory of all problem slots.  Unclaimed results are discarded. */
+int helm_serve_stop(helm_server* s);
+
 /* Bytes of device memory the handle holds. */
 int helm_workspace_bytes(const helm_handle* h, size_t* bytes);
 

@@ -39,6 +39,9 @@ using helm::Handle;
 struct helm_handle {
   Handle* h;
 };
+struct helm_server {
+  helm::Server* s;
+};
 
 extern "C" {
 
@@ -206,6 +209,56 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes) {
 int helm_precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, const helm_opts* opts,
                                const void* r, void* z, int prec, void* stream) {
   HELM_GUARD({ return helm::precond_apply_noalloc(grid, k, theta_beta, opts, r, z, prec, (cudaStream_t)stream); })
+}
+
+int helm_serve_start(const helm_serve_opts* opts, helm_server** out) {
+  HELM_GUARD({
+    if (!out) { helm::set_error("out must not be NULL"); return HELM_EINVAL; }
+    *out = nullptr;
+    helm::Server* s = nullptr;
+    int rc = helm::serve_start(opts, &s);
+    if (rc != HELM_OK) return rc;
+    *out = new helm_server{s};
+    return HELM_OK;
+  })
+}
+
+int helm_serve_submit(helm_server* s, int dim, int n, double k, double theta_beta, const double* b_host,
+                      double* x_host, double tol, long long* ticket) {
+  HELM_GUARD({
+    if (!s) { helm::set_error("NULL server"); return HELM_EINVAL; }
+    return helm::serve_submit(s->s, dim, n, k, theta_beta, b_host, x_host, tol, ticket);
+  })
+}
+
+int helm_serve_poll(helm_server* s, long long ticket, helm_info* info, double* latency_s) {
+  HELM_GUARD({
+    if (!s) { helm::set_error("NULL server"); return HELM_EINVAL; }
+    return helm::serve_poll(s->s, ticket, info, latency_s);
+  })
+}
+
+int helm_serve_wait(helm_server* s, long long ticket, double timeout_s, helm_info* info, double* latency_s) {
+  HELM_GUARD({
+    if (!s) { helm::set_error("NULL server"); return HELM_EINVAL; }
+    return helm::serve_wait(s->s, ticket, timeout_s, info, latency_s);
+  })
+}
+
+int helm_serve_stats(helm_server* s, helm_serve_counters* out) {
+  HELM_GUARD({
+    if (!s) { helm::set_error("NULL server"); return HELM_EINVAL; }
+    return helm::serve_stats(s->s, out);
+  })
+}
+
+int helm_serve_stop(helm_server* s) {
+  HELM_GUARD({
+    if (!s) return HELM_OK;
+    int rc = helm::serve_stop(s->s);
+    delete s;
+    return rc;
+  })
 }
 
 unsigned long long helm_launch_count(void) { return helm::launch_count(); }

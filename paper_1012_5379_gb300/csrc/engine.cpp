@@ -16,17 +16,6 @@
 
 namespace helm {
 
-#define CUDA_TRY(expr)                                                                   \
-  do {                                                                                   \
-    cudaError_t e_ = (expr);                                                             \
-    if (e_ != cudaSuccess) {                                                             \
-      std::ostringstream os_;                                                            \
-      os_ << #expr << ": " << cudaGetErrorString(e_) << " (" << __FILE__ << ":" << __LINE__ << ")"; \
-      set_error(os_.str());                                                              \
-      return e_ == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA;                 \
-    }                                                                                    \
-  } while (0)
-
 static size_t elem_bytes(int prec) { return prec == HELM_C128 ? sizeof(double2) : sizeof(float2); }
 
 
@@ -63,11 +52,52 @@ static int dev_alloc(Handle* h, T** p, size_t bytes) {
   return HELM_OK;
 }
 
-#define TRY(expr)                 \
-  do {                            \
-    int r_ = (expr);              \
-    if (r_ != HELM_OK) return r_; \
-  } while (0)
+// Coefficients of M on level l for angle theta_beta (both precisions), and phi.
+static int upload_level_coefficients(Handle* h, int l, double theta_beta, cudaStream_t st) {
+  HostLevel& L = h->lev[l];
+  std::vector<cplx> a, d, c;
+  stencil_coefficients(grid_spacings(L.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
+  std::vector<double2> c64(3 * L.n);
+  for (int i = 0; i < L.n; ++i) {
+    c64[i] = make_double2(a[i].real(), a[i].imag());
+    c64[L.n + i] = make_double2(d[i].real(), d[i].imag());
+    c64[2 * L.n + i] = make_double2(c[i].real(), c[i].imag());
+  }
+  CUDA_TRY(cudaMemcpyAsync(L.coef64, c64.data(), 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
+  if (h->prec == HELM_C128) {
+    CUDA_TRY(cudaMemcpyAsync(L.coef, c64.data(), 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<float2> c32(3 * L.n);
+    for (int i = 0; i < 3 * L.n; ++i) c32[i] = make_float2((float)c64[i].x, (float)c64[i].y);
+    CUDA_TRY(cudaMemcpyAsync(L.coef, c32.data(), 3 * L.n * sizeof(float2), cudaMemcpyHostToDevice, st));
+  }
+  return HELM_OK;
+}
+
+// Dense FP64 LU (partial pivoting) of the coarsest operator, uploaded.
+static int factor_coarsest(Handle* h, double theta_beta, cudaStream_t st) {
+  const HostLevel& Lc = h->lev.back();
+  const int cm = h->lu_m;
+  std::vector<cplx> a, d, c;
+  stencil_coefficients(grid_spacings(Lc.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
+  std::vector<double> phic(cm, Lc.phic);
+  if (Lc.phi) {
+    std::vector<float> pad(Lc.np);
+    CUDA_TRY(cudaMemcpyAsync(pad.data(), Lc.phi, Lc.np * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int z = 0; z < (h->dim == 3 ? Lc.n : 1); ++z)
+      for (int y = 0; y < Lc.n; ++y)
+        for (int x = 0; x < Lc.n; ++x) phic[(z * Lc.n + y) * Lc.n + x] = pad[((size_t)z * Lc.P + y) * Lc.P + x];
+  }
+  std::vector<cplx> A = dense_operator(h->dim, Lc.n, a, d, c, phic);
+  std::vector<int> perm;
+  if (!lu_factor(A, cm, perm)) { set_error("coarsest operator is singular"); return HELM_ENUMERIC; }
+  std::vector<double2> Ad(A.size());
+  for (size_t i = 0; i < A.size(); ++i) Ad[i] = make_double2(A[i].real(), A[i].imag());
+  CUDA_TRY(cudaMemcpyAsync(h->lu, Ad.data(), Ad.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(h->piv, perm.data(), cm * sizeof(int), cudaMemcpyHostToDevice, st));
+  return HELM_OK;
+}
 
 int setup_handle(const helm_grid* grid, const float* phi, double k, double theta_beta, const helm_opts* opts,
                  cudaStream_t st, Handle** out) {
@@ -132,24 +162,9 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     const size_t nparts = std::max<size_t>(std::max(L.ntiles, L.nflat), 1);
     TRY(dev_alloc(h.get(), &L.part, nparts * NPART * sizeof(double)));
     // coefficients of M on this level (rediscretisation with spacing 2^l h)
-    std::vector<cplx> a, d, c;
-    stencil_coefficients(grid_spacings(L.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
-    std::vector<double2> c64(3 * L.n);
-    for (int i = 0; i < L.n; ++i) {
-      c64[i] = make_double2(a[i].real(), a[i].imag());
-      c64[L.n + i] = make_double2(d[i].real(), d[i].imag());
-      c64[2 * L.n + i] = make_double2(c[i].real(), c[i].imag());
-    }
     TRY(dev_alloc(h.get(), &L.coef64, 3 * L.n * sizeof(double2)));
-    CUDA_TRY(cudaMemcpyAsync(L.coef64, c64.data(), 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
     TRY(dev_alloc(h.get(), &L.coef, 3 * L.n * eb));
-    if (h->prec == HELM_C128) {
-      CUDA_TRY(cudaMemcpyAsync(L.coef, c64.data(), 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
-    } else {
-      std::vector<float2> c32(3 * L.n);
-      for (int i = 0; i < 3 * L.n; ++i) c32[i] = make_float2((float)c64[i].x, (float)c64[i].y);
-      CUDA_TRY(cudaMemcpyAsync(L.coef, c32.data(), 3 * L.n * sizeof(float2), cudaMemcpyHostToDevice, st));
-    }
+    TRY(upload_level_coefficients(h.get(), l, theta_beta, st));
     // phi sampled at this level's nodes (node x of level l is fine node (x+1) 2^l - 1)
     if (phi) {
       TRY(dev_alloc(h.get(), &L.phi, L.np * sizeof(float)));
@@ -160,32 +175,11 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     }
   }
   // ------------------------------------------------ coarsest LU (FP64)
-  {
-    const HostLevel& Lc = h->lev.back();
-    std::vector<cplx> a, d, c;
-    stencil_coefficients(grid_spacings(Lc.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
-    std::vector<double> phic(cm, Lc.phic);
-    if (phi) {
-      std::vector<float> pad(Lc.np);
-      CUDA_TRY(cudaMemcpyAsync(pad.data(), Lc.phi, Lc.np * sizeof(float), cudaMemcpyDeviceToHost, st));
-      CUDA_TRY(cudaStreamSynchronize(st));
-      for (int z = 0; z < (h->dim == 3 ? Lc.n : 1); ++z)
-        for (int y = 0; y < Lc.n; ++y)
-          for (int x = 0; x < Lc.n; ++x)
-            phic[(z * Lc.n + y) * Lc.n + x] = pad[((size_t)z * Lc.P + y) * Lc.P + x];
-    }
-    std::vector<cplx> A = dense_operator(h->dim, Lc.n, a, d, c, phic);
-    std::vector<int> perm;
-    if (!lu_factor(A, cm, perm)) { set_error("coarsest operator is singular"); return HELM_ENUMERIC; }
-    std::vector<double2> Ad(A.size());
-    for (size_t i = 0; i < A.size(); ++i) Ad[i] = make_double2(A[i].real(), A[i].imag());
-    h->lu_m = cm;
-    TRY(dev_alloc(h.get(), &h->lu, Ad.size() * sizeof(double2)));
-    TRY(dev_alloc(h.get(), &h->piv, cm * sizeof(int)));
-    CUDA_TRY(cudaMemcpyAsync(h->lu, Ad.data(), Ad.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(h->piv, perm.data(), cm * sizeof(int), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-  }
+  h->lu_m = cm;
+  TRY(dev_alloc(h.get(), &h->lu, (size_t)cm * cm * sizeof(double2)));
+  TRY(dev_alloc(h.get(), &h->piv, cm * sizeof(int)));
+  TRY(factor_coarsest(h.get(), theta_beta, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
   // ------------------------------------------------ H and the outer storage
   {
     const HostLevel& L0 = h->lev[0];
@@ -318,6 +312,7 @@ struct Group {
   LevelDev<C>* lev0 = nullptr;   // level-0 descriptors of all problems (single problem: [0])
   int lev0_nflat = 1;
   void* dmem = nullptr;
+  bool owns = true;              // dmem and cap_stream belong to the group (not to an arena)
   // the V-cycle captured as a CUDA graph (re-captured when profiling starts or stops)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t vexec = nullptr;
@@ -327,13 +322,27 @@ struct Group {
   ~Group() {
     if (vexec) cudaGraphExecDestroy(vexec);
     release(vrecs);
+    if (owns && cap_stream) cudaStreamDestroy(cap_stream);
+    if (owns && dmem) cudaFree(dmem);
+  }
+};
+
+// Device memory for the descriptor arrays of successive groups, grown only, and the
+// stream their V-cycles are captured on: a set whose membership changes often
+// rebuilds its group without cudaFree (which would wait for every stream of the
+// device) and without creating streams.
+struct GroupArena {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaStream_t cap_stream = nullptr;
+  ~GroupArena() {
+    if (p) cudaFree(p);
     if (cap_stream) cudaStreamDestroy(cap_stream);
-    if (dmem) cudaFree(dmem);
   }
 };
 
 template <typename C>
-static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* g) {
+static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* g, GroupArena* arena = nullptr) {
   g->hs.assign(hs, hs + count);
   g->nprob = count;
   const Handle& h0 = *hs[0];
@@ -438,7 +447,22 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   bytes += coarse.size() * sizeof(LevelDev<C>) + lus.size() * sizeof(CoarseLU) + lev0.size() * sizeof(LevelDev<C>);
   for (auto& v : subs) bytes += v.size() * sizeof(OuterDev<C>);
   bytes += 64 * (g->tc + subs.size() + 4);
-  CUDA_TRY(cudaMalloc(&g->dmem, bytes));
+  if (arena) {
+    // the caller guarantees that no launch of the previous group is still in flight
+    if (arena->cap < bytes) {
+      if (arena->p) CUDA_TRY(cudaFree(arena->p));
+      arena->p = nullptr;
+      arena->cap = 0;
+      CUDA_TRY(cudaMalloc(&arena->p, 2 * bytes));
+      arena->cap = 2 * bytes;
+    }
+    if (!arena->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&arena->cap_stream, cudaStreamNonBlocking));
+    g->owns = false;
+    g->dmem = arena->p;
+    g->cap_stream = arena->cap_stream;
+  } else {
+    CUDA_TRY(cudaMalloc(&g->dmem, bytes));
+  }
   char* cur = (char*)g->dmem;
   auto put = [&](const void* src, size_t nb) -> void* {
     void* dst = cur;
@@ -643,68 +667,93 @@ static void run_cycle_end(const Group<C>& g, cudaStream_t st) {
   for (const auto& o : g.outer) outer_vnew<C>(o.d, o.cnt, o.chunks, o.m, true, st);
 }
 
-template <typename C>
-static int solve_t(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
-                   helm_info* infos, cudaStream_t st) {
-  // inputs and state
-  for (int p = 0; p < count; ++p) {
-    Handle* h = hs[p];
-    {
-      Launch L("io.convert", st, 0, 0, 2);
-      convert_dense_to_padded_c128(h->dim, h->n, (const double2*)b[p], h->bpad, st);
-      convert_dense_to_padded_c128(h->dim, h->n, (const double2*)x[p], h->xpad, st);
-    }
-    OuterState s0;
-    std::memset(&s0, 0, sizeof(s0));
-    s0.m = h->m;
-    s0.maxit = h->maxit;
-    s0.tol = tol;
-    s0.bnorm = -1.0;
-    s0.need_residual = 1;
-    CUDA_TRY(cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+// ------------------------------------------------------------------ active sets
+// Problems iterated together.  A problem joins with begin_problem (its state asks
+// for the true residual first) and leaves when its state says done; the group and
+// its V-cycle graph are rebuilt when membership changes.
+static int begin_problem(Handle* h, const double2* b_dense, const double2* x_dense, double tol, cudaStream_t st) {
+  {
+    Launch L("io.convert", st, 0, 0, x_dense ? 2 : 1);
+    convert_dense_to_padded_c128(h->dim, h->n, b_dense, h->bpad, st);
+    if (x_dense) convert_dense_to_padded_c128(h->dim, h->n, x_dense, h->xpad, st);
+  }
+  if (!x_dense) CUDA_TRY(cudaMemsetAsync(h->xpad, 0, h->vs * sizeof(double2), st));
+  OuterState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.m = h->m;
+  s0.maxit = h->maxit;
+  s0.tol = tol;
+  s0.bnorm = -1.0;
+  s0.need_residual = 1;
+  CUDA_TRY(cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+  h->last_j = 0;
+  CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
+static int finish_problem(Handle* h, const OuterState& s, double2* x_dense, cudaStream_t st, helm_info* info) {
+  if (s.bnorm == 0.0) {
+    // b = 0: the solution is x = 0 whatever the initial guess
+    const size_t npts = h->dim == 3 ? (size_t)h->n * h->n * h->n : (size_t)h->n * h->n;
+    CUDA_TRY(cudaMemsetAsync(x_dense, 0, npts * sizeof(double2), st));
+  } else {
+    Launch L("io.convert", st, 0, 0);
+    convert_padded_to_dense_c128(h->dim, h->n, h->xpad, x_dense, st);
+  }
+  const int status = s.done == 1 ? HELM_OK : (s.done == 3 ? HELM_ENUMERIC : HELM_ENOCONV);
+  if (info) {
+    info->iters = s.iters;
+    info->restarts = s.restarts;
+    info->rel_res_est = s.rel_est;
+    info->rel_res_true = s.rel_true;
+    info->status = status;
   }
   CUDA_TRY(cudaGetLastError());
-  std::vector<Handle*> active(hs, hs + count);
-  std::vector<OuterState> host(count);
-  OuterState* pin = nullptr;
-  CUDA_TRY(cudaMallocHost(&pin, sizeof(OuterState) * count));
-  std::unique_ptr<OuterState, decltype(&cudaFreeHost)> pin_guard(pin, &cudaFreeHost);
+  return status;
+}
+
+template <typename C>
+struct ActiveSet {
+  std::vector<Handle*> members;
   std::unique_ptr<Group<C>> own;
   Group<C>* g = nullptr;
-  auto rebuild = [&]() -> int {
-    if (count == 1) {
+  GroupArena* arena = nullptr;  // set: groups are built in it, never from a handle's cache
+  bool dirty = true;       // membership changed since the group was built
+  bool fresh = false;      // members joined: run their first cycle end before iterating
+  Group<C>* graph_pending = nullptr;
+  OuterState* pin = nullptr;
+  size_t pin_cap = 0;
+  size_t n_read = 0;       // members whose state the last iterate() enqueued for reading
+  ~ActiveSet() { if (pin) cudaFreeHost(pin); }
+
+  void add(Handle* h) {
+    members.push_back(h);
+    dirty = true;
+    fresh = true;
+  }
+  int rebuild(cudaStream_t st) {
+    own.reset();
+    g = nullptr;
+    dirty = false;
+    if (members.size() == 1 && !arena) {
       int rc;
-      g = cached_group<C>(active[0], st, &rc);
+      g = cached_group<C>(members[0], st, &rc);
       return rc;
     }
     own.reset(new Group<C>());
     g = own.get();
-    return build_group<C>(active.data(), (int)active.size(), st, g);
-  };
-  TRY(rebuild());
-  Group<C>* graph_pending = nullptr;
-  run_cycle_end<C>(*g, st);  // first true residual and v_0 of every problem
-  int max_maxit = 0;
-  for (int p = 0; p < count; ++p) max_maxit = std::max(max_maxit, hs[p]->maxit);
-  for (int guard = 0; guard <= 2 * max_maxit + 4; ++guard) {
-    for (int p = 0; p < count; ++p)
-      CUDA_TRY(cudaMemcpyAsync(pin + p, hs[p]->st, sizeof(OuterState), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    if (graph_pending) {
-      harvest(graph_pending->vrecs);  // timed V-cycle launches of the replay just completed
-      graph_pending = nullptr;
+    return build_group<C>(members.data(), (int)members.size(), st, g, arena);
+  }
+  // Enqueue one outer iteration of every member (plus the first cycle end of new
+  // members) and the copy of every member's state to pinned host memory.
+  int iterate(cudaStream_t st) {
+    n_read = 0;
+    if (members.empty()) return HELM_OK;
+    if (dirty) TRY(rebuild(st));
+    if (fresh) {
+      run_cycle_end<C>(*g, st);
+      fresh = false;
     }
-    std::vector<Handle*> still;
-    for (int p = 0; p < count; ++p) {
-      host[p] = pin[p];
-      if (!host[p].done && std::find(active.begin(), active.end(), hs[p]) != active.end()) still.push_back(hs[p]);
-    }
-    if (still.empty()) break;
-    if (still.size() != active.size()) {
-      active = still;
-      TRY(rebuild());
-    }
-    for (int p = 0; p < count; ++p) hs[p]->last_j = host[p].j;
     for (auto& o : g->outer) {
       o.sum_j1 = 0;
       for (Handle* m : o.members) o.sum_j1 += m->last_j + 1;
@@ -713,31 +762,114 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
     run_cycle_end<C>(*g, st);
     CUDA_TRY(cudaGetLastError());
     graph_pending = g;
+    if (pin_cap < members.size()) {
+      if (pin) CUDA_TRY(cudaFreeHost(pin));
+      pin = nullptr;
+      pin_cap = std::max<size_t>(2 * members.size(), 16);
+      CUDA_TRY(cudaMallocHost(&pin, sizeof(OuterState) * pin_cap));
+    }
+    for (size_t p = 0; p < members.size(); ++p)
+      CUDA_TRY(cudaMemcpyAsync(pin + p, members[p]->st, sizeof(OuterState), cudaMemcpyDeviceToHost, st));
+    n_read = members.size();
+    return HELM_OK;
+  }
+  // Wait for the last iterate() (synchronises st); finished members move to `done`.
+  // Members added since that iterate() stay.
+  int collect(cudaStream_t st, std::vector<std::pair<Handle*, OuterState>>* done) {
+    if (n_read == 0) return HELM_OK;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (graph_pending) {
+      harvest(graph_pending->vrecs);  // timed V-cycle launches of the replay just completed
+      graph_pending = nullptr;
+    }
+    std::vector<Handle*> still;
+    for (size_t p = 0; p < members.size(); ++p) {
+      if (p >= n_read) { still.push_back(members[p]); continue; }
+      members[p]->last_j = pin[p].j;
+      if (pin[p].done) done->push_back({members[p], pin[p]});
+      else still.push_back(members[p]);
+    }
+    n_read = 0;
+    if (still.size() != members.size()) {
+      members = still;
+      dirty = true;
+    }
+    return HELM_OK;
+  }
+};
+
+template <typename C>
+static int solve_t(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
+                   helm_info* infos, cudaStream_t st) {
+  ActiveSet<C> set;
+  for (int p = 0; p < count; ++p) {
+    TRY(begin_problem(hs[p], (const double2*)b[p], (const double2*)x[p], tol, st));
+    set.add(hs[p]);
+  }
+  std::vector<std::pair<Handle*, OuterState>> done;
+  int max_maxit = 0;
+  for (int p = 0; p < count; ++p) max_maxit = std::max(max_maxit, hs[p]->maxit);
+  // the first iterate() runs every problem's initial residual before its first V-cycle
+  for (int guard = 0; guard <= 2 * max_maxit + 4 && !set.members.empty(); ++guard) {
+    TRY(set.iterate(st));
+    TRY(set.collect(st, &done));
+  }
+  for (Handle* h : set.members) {  // only on a failed guard: report what they have
+    OuterState s;
+    CUDA_TRY(cudaMemcpy(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost));
+    done.push_back({h, s});
   }
   int rc_all = HELM_OK;
   for (int p = 0; p < count; ++p) {
-    Handle* h = hs[p];
-    const OuterState& s = host[p];
-    if (s.bnorm == 0.0) {
-      // b = 0: the solution is x = 0 whatever the initial guess
-      const size_t npts = h->dim == 3 ? (size_t)h->n * h->n * h->n : (size_t)h->n * h->n;
-      CUDA_TRY(cudaMemsetAsync(x[p], 0, npts * sizeof(double2), st));
-    } else {
-      Launch L("io.convert", st, 0, 0);
-      convert_padded_to_dense_c128(h->dim, h->n, h->xpad, (double2*)x[p], st);
+    for (auto& d : done) {
+      if (d.first != hs[p]) continue;
+      const int status = finish_problem(hs[p], d.second, (double2*)x[p], st, infos ? infos + p : nullptr);
+      if (status != HELM_OK && rc_all == HELM_OK) rc_all = status;
     }
-    int status = s.done == 1 ? HELM_OK : (s.done == 3 ? HELM_ENUMERIC : HELM_ENOCONV);
-    if (infos) {
-      infos[p].iters = s.iters;
-      infos[p].restarts = s.restarts;
-      infos[p].rel_res_est = s.rel_est;
-      infos[p].rel_res_true = s.rel_true;
-      infos[p].status = status;
-    }
-    if (status != HELM_OK && rc_all == HELM_OK) rc_all = status;
   }
   CUDA_TRY(cudaStreamSynchronize(st));
   return rc_all;
+}
+
+// ------------------------------------------------------------------ runners (serving)
+struct BatchRunner {
+  int prec;
+  GroupArena arena;
+  ActiveSet<float2> s64;
+  ActiveSet<double2> s128;
+};
+BatchRunner* runner_create(int prec) {
+  BatchRunner* r = new BatchRunner();
+  r->prec = prec;
+  r->s64.arena = &r->arena;
+  r->s128.arena = &r->arena;
+  return r;
+}
+void runner_destroy_groups(BatchRunner* r) {
+  r->s64.own.reset();
+  r->s128.own.reset();
+}
+void runner_destroy(BatchRunner* r) {
+  runner_destroy_groups(r);  // groups before the arena they live in
+  delete r;
+}
+int runner_add(BatchRunner* r, Handle* h, const double2* b_dense, double tol, cudaStream_t st) {
+  TRY(begin_problem(h, b_dense, nullptr, tol, st));
+  if (r->prec == HELM_C128) r->s128.add(h);
+  else r->s64.add(h);
+  return HELM_OK;
+}
+int runner_iterate(BatchRunner* r, cudaStream_t st) {
+  return r->prec == HELM_C128 ? r->s128.iterate(st) : r->s64.iterate(st);
+}
+int runner_collect(BatchRunner* r, cudaStream_t st, std::vector<std::pair<Handle*, OuterState>>* done) {
+  return r->prec == HELM_C128 ? r->s128.collect(st, done) : r->s64.collect(st, done);
+}
+int runner_size(const BatchRunner* r) {
+  return (int)(r->prec == HELM_C128 ? r->s128.members.size() : r->s64.members.size());
+}
+int runner_finish(Handle* h, const OuterState& s, double2* x_dense, cudaStream_t st, helm_info* info) {
+  return finish_problem(h, s, x_dense, st, info);
 }
 
 int solve_group(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
@@ -749,6 +881,43 @@ int solve_group(Handle* const* hs, int count, const double* const* b, double* co
   const int prec = hs[0]->prec;
   return prec == HELM_C128 ? solve_t<double2>(hs, count, b, x, tol, infos, st)
                            : solve_t<float2>(hs, count, b, x, tol, infos, st);
+}
+
+static void destroy_group_cache(Handle* h);
+
+// Point an existing handle at a new constant wavenumber and CSG angle (same grid,
+// precision and options): the hierarchy buffers are reused, coefficients, phi and the
+// coarsest LU are recomputed.
+int retarget_handle(Handle* h, double k, double theta_beta, cudaStream_t st) {
+  if (!(theta_beta >= 0 && theta_beta < M_PI / 2) || !std::isfinite(k)) {
+    set_error("theta_beta must be in [0, pi/2) and k finite");
+    return HELM_EINVAL;
+  }
+  if (h->has_phi) { set_error("a handle built with a phi field cannot be retargeted"); return HELM_EINVAL; }
+  h->k = k;
+  h->theta_beta = theta_beta;
+  for (int l = 0; l < (int)h->lev.size(); ++l) {
+    h->lev[l].phic = k * k;
+    TRY(upload_level_coefficients(h, l, theta_beta, st));
+  }
+  TRY(factor_coarsest(h, theta_beta, st));
+  destroy_group_cache(h);  // its descriptors carry the old phi
+  return HELM_OK;
+}
+
+// Device bytes helm_setup allocates for these parameters (admission control).
+size_t estimate_handle_bytes(int dim, int n, int prec, int s, int restart, int maxit, int coarsest) {
+  const std::vector<int> sizes = level_sizes(n, coarsest > 0 ? coarsest : 3);
+  const size_t eb = prec == HELM_C128 ? sizeof(double2) : sizeof(float2);
+  size_t bytes = 0;
+  for (int nl : sizes) {
+    const size_t P = nl + 1, np = dim == 3 ? P * P * P : P * P;
+    bytes += (4 + (size_t)s) * np * eb + 3 * nl * (eb + sizeof(double2)) + 4096;
+  }
+  const size_t P0 = n + 1, vs = dim == 3 ? P0 * P0 * P0 : P0 * P0;
+  const size_t m = restart > 0 ? std::min(restart, maxit) : maxit;
+  bytes += 3 * vs * sizeof(double2) + (m + 1) * vs * sizeof(double2) + m * vs * eb + (m + 1) * (m + 8) * 16;
+  return bytes;
 }
 
 static void destroy_group_cache(Handle* h) {

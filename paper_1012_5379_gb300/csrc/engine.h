@@ -1,6 +1,8 @@
 // Host engine: problem handles, problem groups and the solve drivers.
 #pragma once
+#include <sstream>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/helm.h"
@@ -10,6 +12,25 @@ namespace helm {
 
 // Thread-local last error text (capi.cpp).
 void set_error(const std::string& msg);
+
+// Return the failing CUDA call's status as HELM_ENOMEM / HELM_ECUDA with its text.
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      std::ostringstream os_;                                                            \
+      os_ << #expr << ": " << cudaGetErrorString(e_) << " (" << __FILE__ << ":" << __LINE__ << ")"; \
+      set_error(os_.str());                                                              \
+      return e_ == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA;                 \
+    }                                                                                    \
+  } while (0)
+
+// Return a failing helm status.
+#define TRY(expr)                 \
+  do {                            \
+    int r_ = (expr);              \
+    if (r_ != HELM_OK) return r_; \
+  } while (0)
 
 struct HostLevel {
   int n = 0, P = 0;
@@ -71,6 +92,25 @@ int precond_apply(Handle* h, const void* r, void* z, int prec, cudaStream_t st);
 int apply_operator(Handle* h, int which, const void* v, void* w, int prec, cudaStream_t st);
 int precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, const helm_opts* opts,
                           const void* r, void* z, int prec, cudaStream_t st);
+// Problems iterated together, joining and leaving between outer iterations.
+struct BatchRunner;
+BatchRunner* runner_create(int prec);
+void runner_destroy(BatchRunner* r);
+int runner_add(BatchRunner* r, Handle* h, const double2* b_dense, double tol, cudaStream_t st);
+int runner_iterate(BatchRunner* r, cudaStream_t st);
+int runner_collect(BatchRunner* r, cudaStream_t st, std::vector<std::pair<Handle*, OuterState>>* done);
+int runner_size(const BatchRunner* r);
+int runner_finish(Handle* h, const OuterState& s, double2* x_dense, cudaStream_t st, helm_info* info);
+struct Server;
+int serve_start(const helm_serve_opts* opts, Server** out);
+int serve_submit(Server* s, int dim, int n, double k, double theta_beta, const double* b_host, double* x_host,
+                 double tol, long long* ticket);
+int serve_poll(Server* s, long long ticket, helm_info* info, double* latency);
+int serve_wait(Server* s, long long ticket, double timeout_s, helm_info* info, double* latency);
+int serve_stats(Server* s, helm_serve_counters* out);
+int serve_stop(Server* s);
+int retarget_handle(Handle* h, double k, double theta_beta, cudaStream_t st);
+size_t estimate_handle_bytes(int dim, int n, int prec, int s, int restart, int maxit, int coarsest);
 int solve_group(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
                 helm_info* infos, cudaStream_t st);
 

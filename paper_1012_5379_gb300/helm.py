@@ -33,7 +33,21 @@ _STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ENOCONV
 EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_operator", "helm_solve",
            "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_last_error",
            "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc",
-           "helm_batch_solve_host")
+           "helm_batch_solve_host", "helm_serve_start", "helm_serve_submit", "helm_serve_poll", "helm_serve_wait",
+           "helm_serve_stats", "helm_serve_stop")
+
+
+class helm_serve_opts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("precond_prec", ctypes.c_int),
+                ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("s", ctypes.c_int), ("ecs_frac", ctypes.c_double), ("theta_gamma", ctypes.c_double)]
+
+
+class helm_serve_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
+                ("queued", ctypes.c_int), ("active", ctypes.c_int), ("peak_active", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("handles_created", ctypes.c_int), ("handles_reused", ctypes.c_int)]
 
 
 class HelmError(RuntimeError):
@@ -96,6 +110,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_precond_apply_noalloc.argtypes = [ctypes.POINTER(helm_grid), dp, dp, ctypes.POINTER(helm_opts), vp, vp,
                                                ip, vp]
     lib.helm_precond_apply_noalloc.restype = ip
+    lib.helm_serve_start.argtypes = [ctypes.POINTER(helm_serve_opts), ctypes.POINTER(vp)]
+    lib.helm_serve_start.restype = ip
+    lib.helm_serve_submit.argtypes = [vp, ip, ip, dp, dp, vp, vp, dp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.helm_serve_submit.restype = ip
+    lib.helm_serve_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(helm_info), ctypes.POINTER(dp)]
+    lib.helm_serve_poll.restype = ip
+    lib.helm_serve_wait.argtypes = [vp, ctypes.c_longlong, dp, ctypes.POINTER(helm_info), ctypes.POINTER(dp)]
+    lib.helm_serve_wait.restype = ip
+    lib.helm_serve_stats.argtypes = [vp, ctypes.POINTER(helm_serve_counters)]
+    lib.helm_serve_stats.restype = ip
+    lib.helm_serve_stop.argtypes = [vp]
+    lib.helm_serve_stop.restype = ip
     lib.helm_launch_count.argtypes = []
     lib.helm_launch_count.restype = ctypes.c_ulonglong
     lib.helm_profile_begin.argtypes = [ctypes.c_char_p]
@@ -264,3 +290,65 @@ def batch_solve_host(handles: Sequence[Handle], bs, xs, tol: float, stream=None)
     _check(load().helm_batch_solve_host(hp, n, bp, xp, float(tol), infos, _stream(stream)),
            allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
     return [Info.of(infos[i]) for i in range(n)]
+
+
+def _host_ptr(a) -> int:
+    return a.ctypes.data if hasattr(a, "ctypes") else a.data_ptr()
+
+
+class Server:
+    """Continuous-batching solve server (helm_serve_*).  submit() borrows the source
+    and solution arrays (numpy complex128, or pinned torch tensors for overlapped
+    copies) until the ticket completes; this object keeps references to them."""
+
+    def __init__(self, budget_bytes: int = 120 << 30, max_active: int = 0, precision: str = "c64",
+                 restart: int = 40, maxit: int = 400, theta_gamma: float = 0.5, ecs_frac: float = 0.125):
+        o = helm_serve_opts(budget_bytes, max_active, HELM_C128 if precision == "c128" else HELM_C64, restart,
+                            maxit, 1, 1, 3, ecs_frac, theta_gamma)
+        s = ctypes.c_void_p()
+        _check(load().helm_serve_start(ctypes.byref(o), ctypes.byref(s)))
+        self._s = s
+        self._borrowed = {}
+
+    def submit(self, dim: int, n: int, k: float, theta_beta: float, b_host, x_host, tol: float) -> int:
+        t = ctypes.c_longlong()
+        _check(load().helm_serve_submit(self._s, dim, n, float(k), float(theta_beta), _host_ptr(b_host),
+                                        _host_ptr(x_host), float(tol), ctypes.byref(t)))
+        self._borrowed[t.value] = (b_host, x_host)
+        return t.value
+
+    def poll(self, ticket: int):
+        """(Info, latency seconds, status) once finished, else None."""
+        ci, lat = helm_info(), ctypes.c_double()
+        rc = load().helm_serve_poll(self._s, ticket, ctypes.byref(ci), ctypes.byref(lat))
+        if rc == HELM_EAGAIN:
+            return None
+        self._borrowed.pop(ticket, None)
+        _check(rc, allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC, HELM_ENOMEM))
+        return Info.of(ci), lat.value, rc
+
+    def wait(self, ticket: int, timeout: float = 600.0):
+        ci, lat = helm_info(), ctypes.c_double()
+        rc = load().helm_serve_wait(self._s, ticket, float(timeout), ctypes.byref(ci), ctypes.byref(lat))
+        if rc != HELM_ETIMEOUT:
+            self._borrowed.pop(ticket, None)
+        _check(rc, allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC, HELM_ENOMEM))
+        return Info.of(ci), lat.value, rc
+
+    def stats(self) -> dict:
+        st = helm_serve_counters()
+        _check(load().helm_serve_stats(self._s, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in helm_serve_counters._fields_}
+
+    def stop(self):
+        """Finish every request, stop the worker, free the device memory."""
+        if self._s is not None and self._s.value:
+            s, self._s = self._s, ctypes.c_void_p()
+            _check(load().helm_serve_stop(s))
+        self._borrowed.clear()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
