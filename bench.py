@@ -361,6 +361,25 @@ def run_precond(args):
           flush=True)
 
 
+def run_single(args):
+    """One complex64-preconditioned solve (--dim, --n, --maxit, --restart; kh = 0.156,
+    theta_beta 0.3, random source), for profiler captures of the outer kernels on a
+    bounded FGMRES basis.  Stopping at maxit is not an error here."""
+    import torch
+
+    from paper_1012_5379_gb300 import helm
+    dev = torch.device("cuda", 0)
+    n, dim = args.n, args.dim
+    h = helm.Handle(dim, n, 0.3, k=0.156 * (n + 1), precision="c64", restart=args.restart, maxit=args.maxit)
+    b = torch.from_numpy(I.random_source(dim, n, 1001)).to(dev)
+    x = torch.zeros_like(b)
+    t0 = time.perf_counter()
+    info = h.solve(b, x, TOL)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "single", "dim": dim, "n": n, "iters": info.iters, "status": info.status,
+                      "rel_res_true": info.rel_res_true, "s": time.perf_counter() - t0}), flush=True)
+
+
 def _seq_solves(helm, works, precision, bs, xs):
     """Solve `works` one at a time on fresh handles of `precision` (each timed with CUDA
     events after one untimed solve of the same handle); returns per-problem seconds and
@@ -571,7 +590,8 @@ def main():
     ap.add_argument("--sequential-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single"], default="solve")
+    ap.add_argument("--restart", type=int, default=0)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -584,7 +604,7 @@ def main():
     if args.mode != "solve":
         from paper_1012_5379_gb300 import build
         build.build()
-        {"precond": run_precond, "batch": run_batch, "serve": run_serve}[args.mode](args)
+        {"precond": run_precond, "batch": run_batch, "serve": run_serve, "single": run_single}[args.mode](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

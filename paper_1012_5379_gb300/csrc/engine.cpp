@@ -195,7 +195,7 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     CUDA_TRY(cudaMemcpyAsync(h->hcoef, hc.data(), hc.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
     h->vs = L0.np;
     h->ntiles0 = L0.ntiles;
-    h->chunks = (int)std::max<size_t>(1, std::min<size_t>(256, (h->vs + 2047) / 2048));
+    h->chunks = outer_chunks(h->vs);
     const int m = h->m;
     TRY(dev_alloc(h.get(), &h->bpad, h->vs * sizeof(double2)));
     TRY(dev_alloc(h.get(), &h->xpad, h->vs * sizeof(double2)));
@@ -211,8 +211,9 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     TRY(dev_alloc(h.get(), &h->vscale, (size_t)(m + 1) * sizeof(double)));
     const size_t op = std::max<size_t>(std::max<size_t>((size_t)max_tiles(h->dim, L0.P) * NPART,
                                                         (size_t)h->chunks * NPART),
-                                       (size_t)h->chunks * 2 * (m + 1));
+                                       outer_part_doubles(h->chunks, m));
     TRY(dev_alloc(h.get(), &h->opart, op * sizeof(double)));
+    CUDA_TRY(cudaMemsetAsync(h->opart, 0, op * sizeof(double), st));  // multi-dot group counters
     TRY(dev_alloc(h.get(), &h->st, sizeof(OuterState)));
     CUDA_TRY(cudaMemsetAsync(h->w, 0, h->vs * sizeof(double2), st));
     CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(OuterState), st));
@@ -917,6 +918,7 @@ size_t estimate_handle_bytes(int dim, int n, int prec, int s, int restart, int m
   const size_t P0 = n + 1, vs = dim == 3 ? P0 * P0 * P0 : P0 * P0;
   const size_t m = restart > 0 ? std::min(restart, maxit) : maxit;
   bytes += 3 * vs * sizeof(double2) + (m + 1) * vs * sizeof(double2) + m * vs * eb + (m + 1) * (m + 8) * 16;
+  bytes += outer_part_doubles(outer_chunks(vs), (int)m) * sizeof(double);
   return bytes;
 }
 

@@ -192,6 +192,8 @@ template <typename C>
 void outer_residual(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCfg cfg, cudaStream_t st);
 template <typename C>
 void outer_apply_h(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCfg cfg, cudaStream_t st);
+int outer_chunks(size_t vs);
+size_t outer_part_doubles(int chunks, int m);
 template <typename C>
 void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t st);
 template <typename C>

@@ -12,6 +12,8 @@
 // sqrt(||w||^2 - sum |h|^2), whose cancellation made the basis lose orthogonality
 // once the preconditioned operator is close to the identity.
 // At a cycle end: y = R^{-1} g, x += Z y, true residual b - H x recomputed in FP64.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "vcycle.cuh"
 
@@ -206,82 +208,166 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
 }
 
 // ------------------------------------------------------------------ multi-dot
-// h_i = <v_i, w>, i = 0..j, over a grid of `chunks` CTAs per problem; each warp keeps
-// its running sums per i in shared memory (fixed order), the block combines warps,
-// and the last block combines blocks and performs the Givens update.
+// h_i = <v_i, w>, i = 0..j.  The points of a problem are split into `chunks` fixed
+// units (contiguous ranges of equal size, +-1); persistent CTAs take units in turn, so the partial sums, and hence the result, depend neither on the
+// grid nor on which other problems share the launch.  A unit sweeps its points once
+// per block of DOT_VB vectors with the DOT_VB complex sums in registers, so the FP64
+// pipe runs 4 DFMA per point and vector; the warp combines its 2 DOT_VB partial sums
+// with a transposed butterfly (about one add per value instead of five), the CTA
+// combines warps in fixed order.  Units are combined in two levels, so that no
+// single SM adds up every unit: the last unit of each group of DOT_GROUP units sums
+// the group, the last group sums the groups.
 constexpr int DOT_THREADS = 256;
-constexpr int DOT_PPT = 16;  // points per thread per chunk
+constexpr int DOT_VB = 8;      // vectors per register block
+constexpr int DOT_GROUP = 16;  // units per first-level group
+
+HELM_HD inline int dot_groups(int chunks) { return (chunks + DOT_GROUP - 1) / DOT_GROUP; }
+
+// First point of unit u of `chunks` equal contiguous units over n points.
+__device__ __forceinline__ size_t unit_begin(size_t n, int u, int chunks) {
+  return (n * (size_t)u) / (size_t)chunks;
+}
+
+// Sum 16 per-lane values over the warp; lane L returns the total of value L >> 1
+// (fixed order: butterflies at offsets 16, 8, 4, 2, 1, halving the values kept).
+__device__ __forceinline__ double warp_transpose_sum16(double (&v)[16], int lane) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const bool hi = lane & 16;
+    const double send = hi ? v[k] : v[k + 8];
+    const double keep = hi ? v[k + 8] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool hi = lane & 8;
+    const double send = hi ? v[k] : v[k + 4];
+    const double keep = hi ? v[k + 4] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool hi = lane & 4;
+    const double send = hi ? v[k] : v[k + 2];
+    const double keep = hi ? v[k + 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const double send = hi ? v[0] : v[1];
+    const double keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
 
 template <typename C>
 __global__ void __launch_bounds__(DOT_THREADS)
-k_dots(const OuterDev<C>* __restrict__ ods, int chunks) {
-  extern __shared__ double2 swarp[];  // [8][m+1]
+k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
+  extern __shared__ double sred[];  // [warp][2 (m + 1)] per-warp sums of the unit
   __shared__ int s_last;
-  const int prob = blockIdx.x / chunks, cta = blockIdx.x - prob * chunks;
-  const OuterDev<C>& O = ods[prob];
-  OuterState* st = O.st;
-  if (st->done || st->cycle_end) return;
-  const int j = st->j, M1 = st->m + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < 8 * M1; i += DOT_THREADS) swarp[i] = make_double2(0, 0);
-  __syncthreads();
-  const size_t npts = O.vs;
-  const size_t per_chunk = (size_t)DOT_THREADS * DOT_PPT;
-  for (size_t base = (size_t)cta * per_chunk; base < npts; base += (size_t)chunks * per_chunk) {
-    double2 wv[DOT_PPT];
+  const int ngroups = dot_groups(chunks);
+  for (int g = blockIdx.x; g < nprob * chunks; g += gridDim.x) {
+    const int prob = g / chunks, unit = g - prob * chunks;
+    const OuterDev<C>& O = ods[prob];
+    OuterState* st = O.st;
+    if (st->done || st->cycle_end) continue;  // uniform over the CTA
+    const int j = st->j, M1 = st->m + 1;
+    const size_t npts = O.vs;
+    const size_t ubeg = unit_begin(npts, unit, chunks), uend = unit_begin(npts, unit + 1, chunks);
+    double* upart = O.part;                                   // [chunks][M1][2]
+    double* gpart = O.part + (size_t)chunks * M1 * 2;         // [ngroups][M1][2]
+    unsigned* gcnt = reinterpret_cast<unsigned*>(gpart + (size_t)ngroups * M1 * 2);  // [ngroups]
+    double* wsum = sred + (size_t)warp * 2 * M1;
+    __syncthreads();  // the previous unit's readers of sred are done
+    for (int vb = 0; vb <= j; vb += DOT_VB) {
+      const int nv = min(DOT_VB, j + 1 - vb);
+      const double2* vbase = O.V + (size_t)vb * npts;
+      double acc[2 * DOT_VB];
 #pragma unroll
-    for (int q = 0; q < DOT_PPT; ++q) {
-      size_t idx = base + (size_t)q * DOT_THREADS + tid;
-      wv[q] = idx < npts ? __ldcg(O.w + idx) : make_double2(0, 0);
-    }
-    for (int i = 0; i <= j; ++i) {
-      const double2* v = O.V + (size_t)i * O.vs;
-      double2 acc = make_double2(0, 0), acc2 = make_double2(0, 0);
+      for (int k = 0; k < 2 * DOT_VB; ++k) acc[k] = 0.0;
+#pragma unroll 2
+      for (size_t idx = ubeg + tid; idx < uend; idx += DOT_THREADS) {
+        const double2 w = __ldcg(O.w + idx);
 #pragma unroll
-      for (int q = 0; q < DOT_PPT; q += 2) {
-        const size_t idx = base + (size_t)q * DOT_THREADS + tid;
-        if (idx < npts) acc = cdotacc(__ldcg(v + idx), wv[q], acc);
-        if (idx + DOT_THREADS < npts) acc2 = cdotacc(__ldcg(v + idx + DOT_THREADS), wv[q + 1], acc2);
+        for (int t = 0; t < DOT_VB; ++t) {
+          if (t < nv) {
+            const double2 v = __ldcs(vbase + (size_t)t * npts + idx);
+            acc[2 * t] = fma(v.x, w.x, acc[2 * t]);
+            acc[2 * t] = fma(v.y, w.y, acc[2 * t]);
+            acc[2 * t + 1] = fma(v.x, w.y, acc[2 * t + 1]);
+            acc[2 * t + 1] = fma(-v.y, w.x, acc[2 * t + 1]);
+          }
+        }
       }
-      acc = cadd(acc, acc2);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if (lane == 0) swarp[warp * M1 + i] = cadd(swarp[warp * M1 + i], acc);
+      const double r = warp_transpose_sum16(acc, lane);
+      if ((lane & 1) == 0 && (lane >> 1) < 2 * nv) wsum[2 * vb + (lane >> 1)] = r;
     }
+    __syncthreads();
+    for (int k = tid; k < 2 * (j + 1); k += DOT_THREADS) {
+      double sum = 0.0;
+#pragma unroll
+      for (int ww = 0; ww < DOT_THREADS / 32; ++ww) sum += sred[(size_t)ww * 2 * M1 + k];
+      upart[(size_t)unit * M1 * 2 + k] = sum;
+    }
+    // first level: the last unit of the group sums the group's units
+    const int grp = unit / DOT_GROUP, u0 = grp * DOT_GROUP, gsize = min(DOT_GROUP, chunks - u0);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(gcnt + grp, 1u) == (unsigned)gsize - 1u);
+    __syncthreads();
+    if (!s_last) continue;
+    __threadfence();
+    for (int k = tid; k < 2 * (j + 1); k += DOT_THREADS) {
+      double sum = 0.0;
+      for (int u = u0; u < u0 + gsize; ++u) sum += __ldcg(upart + (size_t)u * M1 * 2 + k);
+      gpart[(size_t)grp * M1 * 2 + k] = sum;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      gcnt[grp] = 0u;
+      s_last = (atomicAdd(&st->counter, 1u) == (unsigned)ngroups - 1u);
+    }
+    __syncthreads();
+    if (!s_last) continue;
+    // second level: the last group sums the groups and scales into the Hessenberg column
+    __threadfence();
+    for (int i = tid; i <= j; i += DOT_THREADS) {
+      double2 sum = make_double2(0, 0);
+      for (int c = 0; c < ngroups; ++c)
+        sum = cadd(sum, make_double2(__ldcg(gpart + ((size_t)c * M1 + i) * 2),
+                                     __ldcg(gpart + ((size_t)c * M1 + i) * 2 + 1)));
+      const double sc = O.vscale[i];
+      const double2 h = make_double2(sum.x * sc, sum.y * sc);
+      O.hcol[i] = h;
+      O.Hm[(size_t)j * M1 + i] = h;
+    }
+    if (tid == 0) st->counter = 0u;
+    __syncthreads();
   }
-  __syncthreads();
-  // combine warps (fixed order) and publish this block's partials
-  for (int i = tid; i <= j; i += DOT_THREADS) {
-    double2 s = make_double2(0, 0);
-    for (int ww = 0; ww < 8; ++ww) s = cadd(s, swarp[ww * M1 + i]);
-    O.part[((size_t)cta * M1 + i) * 2] = s.x;
-    O.part[((size_t)cta * M1 + i) * 2 + 1] = s.y;
+}
+
+// Units of the multi-dot and new-vector passes for a problem of vs points: two per
+// SM (so the persistent grids, one or two CTAs per SM, get equal shares), at most one
+// per 256 points.
+int outer_chunks(size_t vs) {
+  static int units = 0;
+  if (units == 0) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    units = 2 * std::max(1, sms);
   }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&st->counter, 1u) == (unsigned)chunks - 1u);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int i = tid; i <= j; i += DOT_THREADS) {
-    double2 s = make_double2(0, 0);
-    for (int c = 0; c < chunks; ++c)
-      s = cadd(s, make_double2(__ldcg(O.part + ((size_t)c * M1 + i) * 2), __ldcg(O.part + ((size_t)c * M1 + i) * 2 + 1)));
-    O.hcol[i] = s;
-  }
-  __syncthreads();
-  if (tid != 0) return;
-  st->counter = 0u;
-  double2* Hc = O.Hm + (size_t)j * M1;
-  for (int i = 0; i <= j; ++i) {
-    const double sc = O.vscale[i];
-    const double2 h = make_double2(O.hcol[i].x * sc, O.hcol[i].y * sc);
-    O.hcol[i] = h;
-    Hc[i] = h;
-  }
+  return (int)std::max<size_t>(1, std::min<size_t>((size_t)units, (vs + DOT_THREADS - 1) / DOT_THREADS));
+}
+
+// Doubles of the outer partial-sum buffer the passes need for `chunks` units and
+// restart length m (unit and group partials of the multi-dot, its group counters).
+size_t outer_part_doubles(int chunks, int m) {
+  const int ng = dot_groups(chunks);
+  return (size_t)(chunks + ng) * (m + 1) * 2 + (size_t)ng + 1;
 }
 
 // ------------------------------------------------------------------ new Arnoldi vector
@@ -326,62 +412,66 @@ __device__ void givens_step(const OuterDev<C>& O, OuterState* st, int j, double 
 // (precision C) and start level 0's first sweep from its norm.
 template <typename C>
 __global__ void __launch_bounds__(256)
-k_vnew(const OuterDev<C>* __restrict__ ods, int chunks, int start) {
+k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
   extern __shared__ double2 sh[];  // m+1
   __shared__ double sm[64];
-  const int prob = blockIdx.x / chunks, cta = blockIdx.x - prob * chunks;
-  const OuterDev<C>& O = ods[prob];
-  OuterState* st = O.st;
-  if (st->done || (!start && st->cycle_end) || (start && !st->fresh)) return;
-  const int j = start ? -1 : st->j;
   const int tid = threadIdx.x;
-  for (int i = tid; i <= j; i += blockDim.x) {
-    const double sc = O.vscale[i];
-    sh[i] = make_double2(O.hcol[i].x * sc, O.hcol[i].y * sc);
-  }
-  __syncthreads();
-  const double inv = start ? 1.0 / st->beta : 1.0;
-  const int jn = j + 1;
-  double2* vout = O.V + (size_t)jn * O.vs;
-  double accu = 0.0;
-  typename CT<C>::R accb = 0;
-  for (size_t idx = (size_t)cta * blockDim.x + tid; idx < O.vs; idx += (size_t)chunks * blockDim.x) {
-    // two independent accumulation chains keep the FP64 pipe busy
-    double2 wa = __ldcg(O.w + idx), wb = make_double2(0, 0);
-    const double2* vp = O.V + idx;
-    int i = 0;
-    for (; i + 1 <= j; i += 2) {
-      const double2 v0 = __ldcg(vp + (size_t)i * O.vs), v1 = __ldcg(vp + (size_t)(i + 1) * O.vs);
-      wa = cfms(sh[i], v0, wa);
-      wb = cfms(sh[i + 1], v1, wb);
+  for (int g = blockIdx.x; g < nprob * chunks; g += gridDim.x) {
+    const int prob = g / chunks, unit = g - prob * chunks;
+    const OuterDev<C>& O = ods[prob];
+    OuterState* st = O.st;
+    if (st->done || (!start && st->cycle_end) || (start && !st->fresh)) continue;  // uniform
+    const int j = start ? -1 : st->j;
+    __syncthreads();  // the previous unit's readers of sh are done
+    for (int i = tid; i <= j; i += blockDim.x) {
+      const double sc = O.vscale[i];
+      sh[i] = make_double2(O.hcol[i].x * sc, O.hcol[i].y * sc);
     }
-    if (i <= j) wa = cfms(sh[i], __ldcg(vp + (size_t)i * O.vs), wa);
-    double2 wv = cadd(wa, wb);
-    wv = make_double2(wv.x * inv, wv.y * inv);
-    vout[idx] = wv;
-    accu += dabs2(wv);
-    C c = from_d<C>(wv);
-    O.b0[idx] = c;
-    accb += cabs2(c);
-  }
-  double red[2] = {accu, (double)accb}, tot[2];
-  if (grid_sum_last<2>(red, O.part, cta, chunks, &st->counter, sm, tot)) {
-    if (flat_tid() == 0) {
-      sweep_begin(O.sc0, (typename CT<C>::R)tot[1], O.s);
-      if (start) {
-        O.vscale[0] = 1.0;
-        st->fresh = 0;
-        st->j = 0;
-      } else {
-        const double hn = sqrt(tot[0]);
-        O.vscale[jn] = hn > 0.0 ? 1.0 / hn : 0.0;
-        givens_step(O, st, j, hn);
-        st->iters += 1;
-        st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
-        const bool breakdown = !(hn > 1e-14 * st->beta);
-        if (!isfinite(st->rel_est)) { st->done = 3; st->status = -4; st->cycle_end = 1; }
-        else if (st->rel_est <= st->tol || st->iters >= st->maxit || j + 1 >= st->m || breakdown) st->cycle_end = 1;
-        else st->j = jn;
+    __syncthreads();
+    const double inv = start ? 1.0 / st->beta : 1.0;
+    const int jn = j + 1;
+    double2* vout = O.V + (size_t)jn * O.vs;
+    double accu = 0.0;
+    typename CT<C>::R accb = 0;
+    const size_t end = unit_begin(O.vs, unit + 1, chunks);
+    for (size_t idx = unit_begin(O.vs, unit, chunks) + tid; idx < end; idx += blockDim.x) {
+      // two independent accumulation chains keep the FP64 pipe busy
+      double2 wa = __ldcg(O.w + idx), wb = make_double2(0, 0);
+      const double2* vp = O.V + idx;
+      int i = 0;
+      for (; i + 1 <= j; i += 2) {
+        const double2 v0 = __ldcs(vp + (size_t)i * O.vs), v1 = __ldcs(vp + (size_t)(i + 1) * O.vs);
+        wa = cfms(sh[i], v0, wa);
+        wb = cfms(sh[i + 1], v1, wb);
+      }
+      if (i <= j) wa = cfms(sh[i], __ldcs(vp + (size_t)i * O.vs), wa);
+      double2 wv = cadd(wa, wb);
+      wv = make_double2(wv.x * inv, wv.y * inv);
+      vout[idx] = wv;
+      accu += dabs2(wv);
+      C c = from_d<C>(wv);
+      O.b0[idx] = c;
+      accb += cabs2(c);
+    }
+    double red[2] = {accu, (double)accb}, tot[2];
+    if (grid_sum_last<2>(red, O.part, unit, chunks, &st->counter, sm, tot)) {
+      if (tid == 0) {
+        sweep_begin(O.sc0, (typename CT<C>::R)tot[1], O.s);
+        if (start) {
+          O.vscale[0] = 1.0;
+          st->fresh = 0;
+          st->j = 0;
+        } else {
+          const double hn = sqrt(tot[0]);
+          O.vscale[jn] = hn > 0.0 ? 1.0 / hn : 0.0;
+          givens_step(O, st, j, hn);
+          st->iters += 1;
+          st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
+          const bool breakdown = !(hn > 1e-14 * st->beta);
+          if (!isfinite(st->rel_est)) { st->done = 3; st->status = -4; st->cycle_end = 1; }
+          else if (st->rel_est <= st->tol || st->iters >= st->maxit || j + 1 >= st->m || breakdown) st->cycle_end = 1;
+          else st->j = jn;
+        }
       }
     }
   }
@@ -441,19 +531,52 @@ void outer_apply_h(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCf
   if (dim == 2) k_hstencil2<C, 1><<<nprob * ntiles, dim3(32, WARPS2), 0, s>>>(od, ntiles, cfg.rows);
   else k_hstencil3<C, 1><<<nprob * ntiles, dim3(32, WY3 + 2), 0, s>>>(od, ntiles, cfg.rows);
 }
+// Resident CTAs of a kernel over the whole GPU (the persistent grid of the outer
+// passes), cached per thread for the last shared-memory size asked.
+template <typename K>
+static int resident_grid(K kernel, int threads, size_t smem) {
+  thread_local K last_kernel = nullptr;
+  thread_local size_t last_smem = 0;
+  thread_local int last = 0;
+  if (kernel == last_kernel && smem == last_smem && last > 0) return last;
+  int dev = 0, sms = 1, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  last_kernel = kernel;
+  last_smem = smem;
+  last = per_sm * std::max(sms, 1);
+  return last;
+}
+
 template <typename C>
 void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t s) {
-  const size_t smem = (size_t)8 * (m + 1) * sizeof(double2);
+  const size_t smem = (size_t)(DOT_THREADS / 32) * 2 * (m + 1) * sizeof(double);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaFuncSetAttribute(k_dots<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = smem;
   }
-  k_dots<C><<<nprob * chunks, DOT_THREADS, smem, s>>>(od, chunks);
+  const int resident = resident_grid(k_dots<C>, DOT_THREADS, smem);
+  k_dots<C><<<std::min(nprob * chunks, resident), DOT_THREADS, smem, s>>>(od, nprob, chunks);
 }
 template <typename C>
 void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start, cudaStream_t s) {
-  k_vnew<C><<<nprob * chunks, 256, (size_t)(m + 1) * sizeof(double2), s>>>(od, chunks, start ? 1 : 0);
+  // Shared memory is padded so that at most two CTAs fit on an SM: the persistent
+  // grid of two CTAs per SM then places exactly two on every SM, and the FP64 work
+  // (the bound of this pass) is spread evenly.
+  static size_t pad = 0;
+  if (pad == 0) {
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    pad = (size_t)per_sm / 3 + 1024;
+    cudaFuncSetAttribute(k_vnew<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(pad, 160 * 1024));
+  }
+  const size_t smem = std::max<size_t>((size_t)(m + 1) * sizeof(double2), pad);
+  const int resident = resident_grid(k_vnew<C>, 256, smem);
+  k_vnew<C><<<std::min(nprob * chunks, resident), 256, smem, s>>>(od, nprob, chunks, start ? 1 : 0);
 }
 template <typename C>
 void outer_backsolve(const OuterDev<C>* od, int nprob, cudaStream_t s) {
