@@ -33,6 +33,8 @@ static TileCfg default_tiles(int dim, int P) {
   return c;
 }
 
+// Largest level size run by the coarse sub-cycle kernel (one CTA per problem with the
+// levels staged in shared memory) instead of grid-wide launches.
 static int coarse_threshold(int dim) { return dim == 2 ? 31 : 7; }
 
 // Tiles of the finest tile configuration (2 rows / planes per march).
@@ -376,15 +378,18 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
     for (int t = 0; t < g->Lmax; ++t)
       if (big->lev[t].n <= coarse_threshold(g->dim)) { tthr = t; break; }
   }
-  g->tc = std::min(std::max(tthr, maxoff), g->Lmax - 1);
+  // the split depends on the level sizes only, never on the other problems: a problem
+  // whose finest level is already coarse runs its whole cycle in the coarse kernel
+  g->tc = std::min(tthr, g->Lmax - 1);
   g->nlev_c = g->Lmax - g->tc;
+  (void)maxoff;
   {
-    // shared-memory footprint of the coarse levels (same sizes for every problem)
-    const Handle* ref = hs[0];
-    const int off0 = g->Lmax - (int)ref->lev.size();
+    // shared-memory footprint of the coarse levels (a function of the level sizes only)
+    const Handle* big = nullptr;
+    for (int p = 0; p < count; ++p) if (off[p] == 0) big = hs[p];
     size_t bytes = 0;
-    for (int t = g->tc; t < g->Lmax; ++t) bytes += (size_t)(4 + g->s) * ref->lev[t - off0].np * sizeof(C);
-    g->coarse_smem = (g->nlev_c <= 8 && bytes <= 200 * 1024) ? bytes : 0;
+    for (int t = g->tc; t < g->Lmax; ++t) bytes += (size_t)(4 + g->s) * big->lev[t].np * sizeof(C);
+    g->coarse_smem = (g->nlev_c <= MAX_COARSE_LEVELS_HOST && bytes <= 200 * 1024) ? bytes : 0;
   }
   // tile config of a group: the first problem's
   for (int p = 0; p < count; ++p)
@@ -410,8 +415,15 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   std::vector<LevelDev<C>> coarse;
   std::vector<CoarseLU> lus;
   for (int p = 0; p < count; ++p) {
-    for (int t = g->tc; t < g->Lmax; ++t) coarse.push_back(make_leveldev<C>(*hs[p], t - off[p]));
+    // the problem's coarse levels (depths t0 .. Lmax-1) first, then padding up to the stride
+    const int t0 = std::max(g->tc, off[p]);
+    const int coarsest = (int)hs[p]->lev.size() - 1;
+    for (int k = 0; k < g->nlev_c; ++k) {
+      const int t = t0 + k;
+      coarse.push_back(make_leveldev<C>(*hs[p], t < g->Lmax ? t - off[p] : coarsest));
+    }
     CoarseLU c;
+    c.nlev = g->Lmax - t0;
     c.m = hs[p]->lu_m;
     c.lu = hs[p]->lu;
     c.piv = hs[p]->piv;
@@ -518,7 +530,7 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
     if (g.coarse_smem > 0)
       launch_coarse_smem<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, g.coarse_smem, st);
     else
-      launch_coarse<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, st);
+      launch_coarse_cluster<C>(dim, g.dcoarse, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, st);
   }
   for (int t = g.tc - 1; t >= 0; --t) {
     const auto& D = g.depth[t];

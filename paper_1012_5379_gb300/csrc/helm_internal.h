@@ -79,8 +79,11 @@ struct LevelDev {
 };
 
 // Dense LU factors of the coarsest operator (FP64), row-major, with pivots.
+constexpr int MAX_COARSE_LEVELS_HOST = 8;  // levels the staged coarse kernels hold
+
 struct CoarseLU {
   int m;                  // unknowns (n^d)
+  int nlev;               // levels of the problem's coarse sub-cycle
   const double2* lu;      // m*m
   const int* piv;         // m
 };
@@ -178,6 +181,9 @@ template <typename C>
 void launch_coarse(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
                    int nu1, int nu2, cudaStream_t st);
 // coarse sub-cycle staged in shared memory (smem_bytes: all levels' vectors)
+template <typename C>
+void launch_coarse_cluster(int dim, const LevelDev<C>* levs, int lev_stride, const CoarseLU* lus, int nprob,
+                           int nu1, int nu2, cudaStream_t st);
 template <typename C>
 void launch_coarse_smem(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
                         int nu1, int nu2, size_t smem_bytes, cudaStream_t st);

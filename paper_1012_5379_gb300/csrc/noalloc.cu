@@ -242,6 +242,7 @@ int run_noalloc(const helm_grid* grid, double k, double theta_beta, int nu1, int
     NA_CUDA(cudaMemcpyAsync(base + o_piv, perm, sizeof(int) * m, cudaMemcpyHostToDevice, st));
     CoarseLU lu;
     lu.m = m;
+    lu.nlev = nlev;
     lu.lu = (const double2*)(base + o_lum);
     lu.piv = (const int*)(base + o_piv);
     NA_CUDA(cudaMemcpyAsync(base + o_lu, &lu, sizeof(lu), cudaMemcpyHostToDevice, st));

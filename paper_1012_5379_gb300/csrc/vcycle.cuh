@@ -206,10 +206,90 @@ k_prolong_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim) {
 }
 
 // ------------------------------------------------------------------ coarse levels
-// One CTA per problem runs the whole sub-cycle of the coarse levels (sizes where a
-// grid-wide launch is all latency): every pass is a block-wide loop with
-// __syncthreads and fixed-order block reductions; the coarsest level is a dense FP64
-// LU solve by one warp.
+// The sub-cycle of the coarse levels (sizes where a grid-wide launch is all latency)
+// runs on a "team" per problem: one CTA, or a thread-block cluster whose CTAs act as
+// one block.  Every pass is a team-wide loop over the level's points; sync() orders
+// all of the team's global-memory accesses; sum() totals per-thread values in a fixed
+// order and leaves the totals with thread 0 of every CTA, which then runs the small
+// sweep algebra on its CTA's own copy of the sweep scalars (bitwise the same in every
+// CTA, so no further exchange is needed).  The coarsest level is a dense FP64 LU solve
+// by one warp.
+struct CtaTeam {
+  __device__ __forceinline__ int rank() const { return 0; }
+  __device__ __forceinline__ unsigned gtid() const { return (unsigned)flat_tid(); }
+  __device__ __forceinline__ unsigned gnth() const { return (unsigned)block_threads(); }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  template <int NV, typename T>
+  __device__ __forceinline__ void sum(T (&v)[NV], T* sm) { block_sum<NV, T>(v, sm); }
+};
+
+constexpr int CLUSTER_MAX = 16;
+constexpr int TEAM_NV = 2 * SMAX + 1;  // most values one team sum carries
+constexpr int CB_U = 4;                // points per thread per step of the team loops
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned n;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+  return n;
+}
+// Every thread of every CTA of the cluster; release/acquire at cluster scope.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Load a word of CTA `rank`'s shared memory at the address of `p` in this CTA's.
+__device__ __forceinline__ float ld_dsmem(const float* p, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+  float v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_dsmem(const double* p, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// `slots` is this CTA's [2][CLUSTER_MAX][TEAM_NV] doubles of shared memory.  The two
+// halves alternate between sums: a CTA can only rewrite a half after every CTA has
+// passed the barrier that follows the reads of the previous sum in it.
+struct ClusterTeam {
+  unsigned r, n;
+  double* slots;
+  int buf;
+  __device__ __forceinline__ explicit ClusterTeam(double* s) : r(cluster_rank()), n(cluster_size()), slots(s), buf(0) {}
+  __device__ __forceinline__ int rank() const { return (int)r; }
+  __device__ __forceinline__ unsigned gtid() const { return r * (unsigned)block_threads() + (unsigned)flat_tid(); }
+  __device__ __forceinline__ unsigned gnth() const { return n * (unsigned)block_threads(); }
+  __device__ __forceinline__ void sync() const { cluster_sync(); }
+  template <int NV, typename T>
+  __device__ __forceinline__ void sum(T (&v)[NV], T* sm) {
+    block_sum<NV, T>(v, sm);
+    T* half = reinterpret_cast<T*>(slots + (size_t)buf * CLUSTER_MAX * TEAM_NV);
+    if (flat_tid() == 0)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) half[r * NV + i] = v[i];
+    cluster_sync();
+    if (flat_tid() < 32) {  // lane q reads rank q's sums, a fixed butterfly adds them
+      const unsigned q = (unsigned)flat_tid();
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] = q < n ? ld_dsmem(half + q * NV + i, q) : (T)0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    buf ^= 1;
+  }
+};
+
 template <typename C>
 __device__ void cblock_stencil_apply(const LevelDev<C>& L, const C* v, int x, int y, int z, int dim, C& out) {
   const int n = L.n, P = L.P;
@@ -231,200 +311,271 @@ __device__ void cblock_stencil_apply(const LevelDev<C>& L, const C* v, int x, in
   out = cfma(diag, v0, p);
 }
 
-template <typename C>
-__device__ __forceinline__ void cblock_coords(size_t i, int P, int dim, int& x, int& y, int& z) {
-  x = (int)(i % P);
-  y = (int)((i / P) % P);
-  z = dim == 3 ? (int)(i / ((size_t)P * P)) : 0;
+// Coordinates of padded index i (coarse levels have fewer than 2^32 points).
+__device__ __forceinline__ void cblock_coords(unsigned i, unsigned P, int dim, int& x, int& y, int& z) {
+  const unsigned q = i / P;
+  x = (int)(i - q * P);
+  if (dim == 3) {
+    const unsigned zz = q / P;
+    y = (int)(q - zz * P);
+    z = (int)zz;
+  } else {
+    y = (int)q;
+    z = 0;
+  }
+}
+__device__ __forceinline__ unsigned cblock_npts(int P, int dim) {
+  return dim == 3 ? (unsigned)P * P * P : (unsigned)P * P;
 }
 
-// One GMRES(s) sweep on level L in a single CTA.  R_0 is b (r0_is_b) or r0; x is
-// updated in place in xo (or written from zero).  `tmp` holds v_J.  At the end, in
-// residual mode r0 <- r_new and the next sweep starts; in restrict mode the residual
-// is left in `tmp` for the caller.
-template <typename C>
-__device__ void cblock_sweep(const LevelDev<C>& L, int dim, int r0_is_b, C* xo, int x_from_zero, C* tmp,
+// One GMRES(s) sweep on level L by the team.  R_0 is b (r0_is_b) or r0; x is updated
+// in place in xo (or written from zero).  `tmp` holds v_J.  At the end, in residual
+// mode r0 <- r_new and the next sweep starts; in restrict mode the residual is left in
+// `tmp` for the caller.
+template <typename C, typename Team>
+__device__ void cblock_sweep(Team& team, const LevelDev<C>& L, int dim, int r0_is_b, C* xo, int x_from_zero, C* tmp,
                              int end_mode, typename CT<C>::R* sm) {
   typedef typename CT<C>::R R;
   auto* sc = L.sc;
   const int P = L.P, n = L.n;
-  const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
-  const int tid = flat_tid(), nth = block_threads();
+  const unsigned npts = cblock_npts(P, dim);
+  const unsigned gt = team.gtid(), gn = team.gnth();
   const C* R0 = r0_is_b ? L.b : L.r0;
   for (int J = 1; J <= SMAX; ++J) {
-    __syncthreads();
-    if (sc->m < J) break;
-    // v_J = sum_k Cf[J][k] R_k
-    for (size_t i = tid; i < npts; i += nth) {
-      C v = czero<C>();
-      for (int k = 0; k < J; ++k) {
-        const C* Rk = k == 0 ? R0 : L.p[k - 1];
-        v = cfma(sc->Cf[J][k], Rk[i], v);
+    __syncthreads();  // this CTA's sweep scalars are final
+    if (sc->m < J) break;  // the same in every CTA of the team
+    // v_J = sum_k Cf[J][k] R_k (each point by the thread that owns it in every pass;
+    // CB_U points at a time, all loads before the stores)
+    C cf[SMAX];
+    for (int k = 0; k < J; ++k) cf[k] = sc->Cf[J][k];
+    for (unsigned i0 = gt; i0 < npts; i0 += CB_U * gn) {
+      C v[CB_U];
+#pragma unroll
+      for (int u = 0; u < CB_U; ++u) {
+        const unsigned i = i0 + u * gn;
+        v[u] = czero<C>();
+        if (i < npts)
+          for (int k = 0; k < J; ++k) v[u] = cfma(cf[k], (k == 0 ? R0 : L.p[k - 1])[i], v[u]);
       }
-      tmp[i] = v;
+#pragma unroll
+      for (int u = 0; u < CB_U; ++u)
+        if (i0 + u * gn < npts) tmp[i0 + u * gn] = v[u];
     }
-    __syncthreads();
+    team.sync();
     R red[2 * SMAX + 1];
     for (int q = 0; q < 2 * SMAX + 1; ++q) red[q] = (R)0;
     C acc[SMAX];
     for (int k = 0; k < SMAX; ++k) acc[k] = czero<C>();
     R accn = 0;
-    for (size_t i = tid; i < npts; i += nth) {
-      int x, y, z;
-      cblock_coords<C>(i, P, dim, x, y, z);
-      C p = czero<C>();
-      if (inside(x, y, z, n)) {
-        cblock_stencil_apply(L, tmp, x, y, z, dim, p);
-        for (int k = 0; k < J; ++k) acc[k] = cdotacc((k == 0 ? R0 : L.p[k - 1])[i], p, acc[k]);
-        accn += cabs2(p);
+    for (unsigned i0 = gt; i0 < npts; i0 += CB_U * gn) {
+      C p[CB_U];
+#pragma unroll
+      for (int u = 0; u < CB_U; ++u) {
+        const unsigned i = i0 + u * gn;
+        p[u] = czero<C>();
+        if (i < npts) {
+          int x, y, z;
+          cblock_coords(i, (unsigned)P, dim, x, y, z);
+          if (inside(x, y, z, n)) {
+            cblock_stencil_apply(L, tmp, x, y, z, dim, p[u]);
+            for (int k = 0; k < J; ++k) acc[k] = cdotacc((k == 0 ? R0 : L.p[k - 1])[i], p[u], acc[k]);
+            accn += cabs2(p[u]);
+          }
+        }
       }
-      L.p[J - 1][i] = p;
+#pragma unroll
+      for (int u = 0; u < CB_U; ++u)
+        if (i0 + u * gn < npts) L.p[J - 1][i0 + u * gn] = p[u];
     }
     for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
     red[2 * J] = accn;
-    block_sum<2 * SMAX + 1, R>(red, sm);
-    if (tid == 0) sweep_after_pass_rt<R>(sc, J, red);
+    team.sum(red, sm);  // also separates this pass's reads of tmp from the next pass's writes
+    if (flat_tid() == 0) sweep_after_pass_rt<R>(sc, J, red);
   }
   __syncthreads();
   const int m = sc->m;
   C xc[SMAX + 1], rc[SMAX + 1];
   for (int k = 0; k <= SMAX; ++k) { xc[k] = sc->xcoef[k]; rc[k] = sc->rcoef[k]; }
-  __syncthreads();
   R accr = 0;
-  for (size_t i = tid; i < npts; i += nth) {
-    C dx = czero<C>(), r = czero<C>();
-    for (int k = 0; k <= m; ++k) {
-      C v = (k == 0 ? R0 : L.p[k - 1])[i];
-      if (k < m) dx = cfma(xc[k], v, dx);
-      r = cfma(rc[k], v, r);
+  for (unsigned i0 = gt; i0 < npts; i0 += CB_U * gn) {
+    C xn[CB_U], r[CB_U];
+#pragma unroll
+    for (int u = 0; u < CB_U; ++u) {
+      const unsigned i = i0 + u * gn;
+      C dx = czero<C>();
+      r[u] = czero<C>();
+      xn[u] = czero<C>();
+      if (i < npts) {
+        for (int k = 0; k <= m; ++k) {
+          C v = (k == 0 ? R0 : L.p[k - 1])[i];
+          if (k < m) dx = cfma(xc[k], v, dx);
+          r[u] = cfma(rc[k], v, r[u]);
+        }
+        xn[u] = cadd(x_from_zero ? czero<C>() : xo[i], dx);
+      }
     }
-    xo[i] = cadd(x_from_zero ? czero<C>() : xo[i], dx);
-    if (end_mode == UPD_RESIDUAL) { L.r0[i] = r; accr += cabs2(r); }
-    if (end_mode == UPD_RESTRICT) tmp[i] = r;
+#pragma unroll
+    for (int u = 0; u < CB_U; ++u) {
+      const unsigned i = i0 + u * gn;
+      if (i >= npts) continue;
+      xo[i] = xn[u];
+      if (end_mode == UPD_RESIDUAL) { L.r0[i] = r[u]; accr += cabs2(r[u]); }
+      if (end_mode == UPD_RESTRICT) tmp[i] = r[u];
+    }
   }
   if (end_mode == UPD_RESIDUAL) {
     R red[1] = {accr};
-    block_sum<1, R>(red, sm);
-    if (tid == 0) sweep_begin(sc, red[0], L.s);
+    team.sum(red, sm);
+    if (flat_tid() == 0) sweep_begin(sc, red[0], L.s);
   }
-  __syncthreads();
+  team.sync();
 }
 
 // The whole sub-cycle of levels Ls[0..nlev-1] (Ls[nlev-1] the coarsest, solved by
-// LU) in one CTA; the level vectors and sweep scalars may live in global or shared
-// memory (plain loads only).  `sm` needs 32 * (2 SMAX + 1) doubles.
-template <typename C>
-__device__ void coarse_cycle(const LevelDev<C>* Ls, int nlev, const CoarseLU& lu, int nu1, int nu2, int dim,
-                             double* smd) {
+// LU) on one team; the level vectors may live in global or shared memory (plain
+// loads only), the sweep scalars are the CTA's own.  `sm` needs 32 * (2 SMAX + 1)
+// doubles.
+template <typename C, typename Team>
+__device__ void coarse_cycle(Team& team, const LevelDev<C>* Ls, int nlev, const CoarseLU& lu, int nu1, int nu2,
+                             int dim, double* smd) {
   typedef typename CT<C>::R R;
   R* sm = reinterpret_cast<R*>(smd);
+  const unsigned gt = team.gtid(), gn = team.gnth();
   const int tid = flat_tid(), nth = block_threads();
   // descent
   for (int l = 0; l < nlev - 1; ++l) {
     const LevelDev<C>& L = Ls[l];
     const int P = L.P;
-    const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
+    const unsigned npts = cblock_npts(P, dim);
     if (nu1 == 0) {
-      for (size_t i = tid; i < npts; i += nth) { L.xa[i] = czero<C>(); L.xb[i] = L.b[i]; }
+      for (unsigned i = gt; i < npts; i += gn) { L.xa[i] = czero<C>(); L.xb[i] = L.b[i]; }
     } else {
       for (int sw = 0; sw < nu1; ++sw)
-        cblock_sweep(L, dim, sw == 0, L.xa, sw == 0, L.xb, sw == nu1 - 1 ? UPD_RESTRICT : UPD_RESIDUAL, sm);
+        cblock_sweep(team, L, dim, sw == 0, L.xa, sw == 0, L.xb, sw == nu1 - 1 ? UPD_RESTRICT : UPD_RESIDUAL, sm);
     }
-    __syncthreads();
+    team.sync();
     // b_c = FW(r) with r in xb
     const int Pc = L.Pc, nc = L.nc;
-    const size_t ncpts = dim == 3 ? (size_t)Pc * Pc * Pc : (size_t)Pc * Pc;
+    const unsigned ncpts = cblock_npts(Pc, dim);
     R acc = 0;
-    for (size_t i = tid; i < ncpts; i += nth) {
-      int X, Y, Z;
-      cblock_coords<C>(i, Pc, dim, X, Y, Z);
-      C out = czero<C>();
-      if (inside(X, Y, Z, nc)) {
-        const int fx = 2 * X + 1, fy = 2 * Y + 1, fz = dim == 3 ? 2 * Z + 1 : 0;
-        const int dz0 = dim == 3 ? -1 : 0, dz1 = dim == 3 ? 1 : 0;
-        for (int dz = dz0; dz <= dz1; ++dz)
-          for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-              R wgt = (R)((dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25) * (dim == 3 ? (dz == 0 ? 0.5 : 0.25) : 1.0));
-              out = cadd(out, cscale(ldc<C, false>((const C*)L.xb, fx + dx, fy + dy, fz + dz, L.n, P), wgt));
-            }
-        acc += cabs2(out);
+    for (unsigned i0 = gt; i0 < ncpts; i0 += CB_U * gn) {
+      C out[CB_U];
+#pragma unroll
+      for (int u = 0; u < CB_U; ++u) {
+        const unsigned i = i0 + u * gn;
+        out[u] = czero<C>();
+        if (i >= ncpts) continue;
+        int X, Y, Z;
+        cblock_coords(i, (unsigned)Pc, dim, X, Y, Z);
+        if (inside(X, Y, Z, nc)) {
+          const int fx = 2 * X + 1, fy = 2 * Y + 1, fz = dim == 3 ? 2 * Z + 1 : 0;
+          const int dz0 = dim == 3 ? -1 : 0, dz1 = dim == 3 ? 1 : 0;
+          for (int dz = dz0; dz <= dz1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+              for (int dx = -1; dx <= 1; ++dx) {
+                R wgt = (R)((dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25) * (dim == 3 ? (dz == 0 ? 0.5 : 0.25) : 1.0));
+                out[u] = cadd(out[u], cscale(ldc<C, false>((const C*)L.xb, fx + dx, fy + dy, fz + dz, L.n, P), wgt));
+              }
+          acc += cabs2(out[u]);
+        }
       }
-      L.bc[i] = out;
+#pragma unroll
+      for (int u = 0; u < CB_U; ++u)
+        if (i0 + u * gn < ncpts) L.bc[i0 + u * gn] = out[u];
     }
     R red[1] = {acc};
-    block_sum<1, R>(red, sm);
+    team.sum(red, sm);
     if (tid == 0) sweep_begin(L.scc, red[0], L.s);
-    __syncthreads();
+    team.sync();
   }
-  // coarsest: dense LU solve in FP64 by warp 0
+  // coarsest: dense LU solve in FP64 by warp 0 of the first CTA, which also writes x
   {
     const LevelDev<C>& L = Ls[nlev - 1];
     const int m = lu.m, P = L.P, n = L.n;
     double2* yv = reinterpret_cast<double2*>(smd);  // m <= 144 complex values
-    if (tid < 32) {
-      for (int i = tid; i < m; i += 32) {
-        const int src = lu.piv[i];
-        int sx = src % n, sy = (src / n) % n, sz = dim == 3 ? src / (n * n) : 0;
-        yv[i] = to_d(L.b[pidx(sx, sy, sz, P)]);
+    if (team.rank() == 0) {
+      if (tid < 32) {
+        for (int i = tid; i < m; i += 32) {
+          const int src = lu.piv[i];
+          int sx = src % n, sy = (src / n) % n, sz = dim == 3 ? src / (n * n) : 0;
+          yv[i] = to_d(L.b[pidx(sx, sy, sz, P)]);
+        }
+        __syncwarp();
+        for (int k = 0; k < m; ++k) {  // forward, unit lower
+          const double2 yk = yv[k];
+          __syncwarp();
+          for (int i = k + 1 + tid; i < m; i += 32) yv[i] = csub(yv[i], cmul(lu.lu[(size_t)i * m + k], yk));
+          __syncwarp();
+        }
+        for (int k = m - 1; k >= 0; --k) {  // backward
+          if (tid == 0) yv[k] = ddiv(yv[k], lu.lu[(size_t)k * m + k]);
+          __syncwarp();
+          const double2 yk = yv[k];
+          for (int i = tid; i < k; i += 32) yv[i] = csub(yv[i], cmul(lu.lu[(size_t)i * m + k], yk));
+          __syncwarp();
+        }
       }
-      __syncwarp();
-      for (int k = 0; k < m; ++k) {  // forward, unit lower
-        const double2 yk = yv[k];
-        __syncwarp();
-        for (int i = k + 1 + tid; i < m; i += 32) yv[i] = csub(yv[i], cmul(lu.lu[(size_t)i * m + k], yk));
-        __syncwarp();
-      }
-      for (int k = m - 1; k >= 0; --k) {  // backward
-        if (tid == 0) yv[k] = ddiv(yv[k], lu.lu[(size_t)k * m + k]);
-        __syncwarp();
-        const double2 yk = yv[k];
-        for (int i = tid; i < k; i += 32) yv[i] = csub(yv[i], cmul(lu.lu[(size_t)i * m + k], yk));
-        __syncwarp();
+      __syncthreads();
+      const unsigned npts = cblock_npts(P, dim);
+      for (unsigned i = tid; i < npts; i += nth) {
+        int x, y, z;
+        cblock_coords(i, (unsigned)P, dim, x, y, z);
+        C v = czero<C>();
+        if (inside(x, y, z, n)) v = from_d<C>(yv[(z * n + y) * n + x]);
+        L.xb[i] = v;
       }
     }
-    __syncthreads();
-    const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
-    for (size_t i = tid; i < npts; i += nth) {
-      int x, y, z;
-      cblock_coords<C>(i, P, dim, x, y, z);
-      C v = czero<C>();
-      if (inside(x, y, z, n)) v = from_d<C>(yv[(z * n + y) * n + x]);
-      L.xb[i] = v;
-    }
-    __syncthreads();
+    team.sync();
   }
   // ascent
   for (int l = nlev - 2; l >= 0; --l) {
     const LevelDev<C>& L = Ls[l];
     const int P = L.P, n = L.n;
-    const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
-    for (size_t i = tid; i < npts; i += nth) {
-      int x, y, z;
-      cblock_coords<C>(i, P, dim, x, y, z);
-      L.xb[i] = inside(x, y, z, n) ? cadd(L.xa[i], interp<C, false>(L, x, y, z, dim)) : czero<C>();
+    const unsigned npts = cblock_npts(P, dim);
+    for (unsigned i0 = gt; i0 < npts; i0 += CB_U * gn) {
+      C xv[CB_U];
+#pragma unroll
+      for (int u = 0; u < CB_U; ++u) {
+        const unsigned i = i0 + u * gn;
+        xv[u] = czero<C>();
+        if (i >= npts) continue;
+        int x, y, z;
+        cblock_coords(i, (unsigned)P, dim, x, y, z);
+        if (inside(x, y, z, n)) xv[u] = cadd(L.xa[i], interp<C, false>(L, x, y, z, dim));
+      }
+#pragma unroll
+      for (int u = 0; u < CB_U; ++u)
+        if (i0 + u * gn < npts) L.xb[i0 + u * gn] = xv[u];
     }
-    __syncthreads();
+    team.sync();
     if (nu2 > 0) {
       R acc = 0;
-      for (size_t i = tid; i < npts; i += nth) {
-        int x, y, z;
-        cblock_coords<C>(i, P, dim, x, y, z);
-        C r = czero<C>();
-        if (inside(x, y, z, n)) {
-          C p;
-          cblock_stencil_apply(L, (const C*)L.xb, x, y, z, dim, p);
-          r = csub(L.b[i], p);
-          acc += cabs2(r);
+      for (unsigned i0 = gt; i0 < npts; i0 += CB_U * gn) {
+        C r[CB_U];
+#pragma unroll
+        for (int u = 0; u < CB_U; ++u) {
+          const unsigned i = i0 + u * gn;
+          r[u] = czero<C>();
+          if (i >= npts) continue;
+          int x, y, z;
+          cblock_coords(i, (unsigned)P, dim, x, y, z);
+          if (inside(x, y, z, n)) {
+            C p;
+            cblock_stencil_apply(L, (const C*)L.xb, x, y, z, dim, p);
+            r[u] = csub(L.b[i], p);
+            acc += cabs2(r[u]);
+          }
         }
-        L.r0[i] = r;
+#pragma unroll
+        for (int u = 0; u < CB_U; ++u)
+          if (i0 + u * gn < npts) L.r0[i0 + u * gn] = r[u];
       }
       R red[1] = {acc};
-      block_sum<1, R>(red, sm);
+      team.sum(red, sm);
       if (tid == 0) sweep_begin(L.sc, red[0], L.s);
-      __syncthreads();
+      team.sync();
       for (int sw = 0; sw < nu2; ++sw)
-        cblock_sweep(L, dim, 0, L.xb, 0, L.xa, sw == nu2 - 1 ? UPD_XONLY : UPD_RESIDUAL, sm);
+        cblock_sweep(team, L, dim, 0, L.xb, 0, L.xa, sw == nu2 - 1 ? UPD_XONLY : UPD_RESIDUAL, sm);
     }
   }
 }
@@ -432,20 +583,21 @@ __device__ void coarse_cycle(const LevelDev<C>* Ls, int nlev, const CoarseLU& lu
 
 // Coarse sub-cycle with the levels in global memory (any size).
 template <typename C>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(512)
 k_coarse(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride, const CoarseLU* __restrict__ lus,
          int nu1, int nu2, int dim) {
   __shared__ double sm[32 * (2 * SMAX + 1)];
   pdl_trigger();
   pdl_wait();
   const int prob = blockIdx.x;
-  coarse_cycle<C>(levs_all + (size_t)prob * lev_stride, nlev, lus[prob], nu1, nu2, dim, sm);
+  CtaTeam team;
+  coarse_cycle<C>(team, levs_all + (size_t)prob * lev_stride, nlev, lus[prob], nu1, nu2, dim, sm);
 }
 
 // Coarse sub-cycle with every level's vectors, descriptors and sweep scalars staged
 // in shared memory; only the top coarse level's right-hand side (and its sweep state)
 // comes from global memory and only its result goes back.
-constexpr int MAX_COARSE_LEVELS = 8;
+constexpr int MAX_COARSE_LEVELS = MAX_COARSE_LEVELS_HOST;
 template <typename C>
 __global__ void __launch_bounds__(512)
 k_coarse_smem(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride, const CoarseLU* __restrict__ lus,
@@ -459,6 +611,7 @@ k_coarse_smem(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride
   const LevelDev<C>* G = levs_all + (size_t)prob * lev_stride;
   const int tid = flat_tid(), nth = block_threads();
   pdl_wait();
+  nlev = lus[prob].nlev;  // this problem's coarse levels (<= the stride)
   if (tid == 0) {
     C* cur = reinterpret_cast<C*>(smraw);
     for (int l = 0; l < nlev; ++l) {
@@ -487,12 +640,51 @@ k_coarse_smem(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride
     for (int i = tid; i < words; i += nth) dst[i] = src[i];
   }
   __syncthreads();
-  coarse_cycle<C>(Ls, nlev, lus[prob], nu1, nu2, dim, sm);
+  CtaTeam team;
+  coarse_cycle<C>(team, Ls, nlev, lus[prob], nu1, nu2, dim, sm);
   __syncthreads();
   {
     const size_t np0 = dim == 3 ? (size_t)G[0].P * G[0].P * G[0].P : (size_t)G[0].P * G[0].P;
     for (size_t i = tid; i < np0; i += nth) G[0].xb[i] = Ls[0].xb[i];
   }
+}
+
+// Coarse sub-cycle on one thread-block cluster per problem (clusters are consecutive
+// blocks along x): the level vectors stay in global memory, every CTA holds its own
+// copy of the descriptors and sweep scalars.  Problem p runs lus[p].nlev levels.
+constexpr int CLUSTER_THREADS = 512;
+template <typename C>
+__global__ void __launch_bounds__(CLUSTER_THREADS)
+k_coarse_cluster(const LevelDev<C>* __restrict__ levs_all, int lev_stride, const CoarseLU* __restrict__ lus,
+                 int nu1, int nu2, int dim) {
+  __shared__ double sm[32 * (2 * SMAX + 1)];
+  __shared__ double slots[2 * CLUSTER_MAX * TEAM_NV];
+  __shared__ LevelDev<C> Ls[MAX_COARSE_LEVELS];
+  __shared__ SweepScalarsT<typename CT<C>::R> Ss[MAX_COARSE_LEVELS];
+  pdl_trigger();
+  ClusterTeam team(slots);
+  const int prob = blockIdx.x / (int)team.n;
+  const CoarseLU lu = lus[prob];
+  const int nlev = lu.nlev;
+  const LevelDev<C>* G = levs_all + (size_t)prob * lev_stride;
+  const int tid = flat_tid(), nth = block_threads();
+  pdl_wait();
+  if (tid == 0) {
+    for (int l = 0; l < nlev; ++l) {
+      Ls[l] = G[l];
+      Ls[l].sc = &Ss[l];
+    }
+    for (int l = 0; l + 1 < nlev; ++l) Ls[l].scc = &Ss[l + 1];
+  }
+  {
+    const int* src = reinterpret_cast<const int*>(G[0].sc);
+    int* dst = reinterpret_cast<int*>(&Ss[0]);
+    const int words = sweep_words<typename CT<C>::R>();
+    for (int i = tid; i < words; i += nth) dst[i] = __ldcg(src + i);
+  }
+  __syncthreads();
+  coarse_cycle<C>(team, Ls, nlev, lu, nu1, nu2, dim, sm);
+  team.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 }  // namespace helm

@@ -89,7 +89,7 @@ void launch_prolong(int dim, bool with_residual, const LevelDev<C>* levs, int np
 template <typename C>
 void launch_coarse(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
                    int nu1, int nu2, cudaStream_t st) {
-  pdl_launch(k_coarse<C>, dim3(nprob), dim3(1024), 0, st, levs, nlev, lev_stride, lus, nu1, nu2, dim);
+  pdl_launch(k_coarse<C>, dim3(nprob), dim3(512), 0, st, levs, nlev, lev_stride, lus, nu1, nu2, dim);
 }
 
 template <typename C>
@@ -108,6 +108,53 @@ void launch_coarse_smem(int dim, const LevelDev<C>* levs, int nlev, int lev_stri
     configured = true;
   }
   pdl_launch(k_coarse_smem<C>, dim3(nprob), dim3(512), smem_bytes, st, levs, nlev, lev_stride, lus, nu1, nu2, dim);
+}
+
+// Cluster size of the coarse sub-cycle: the largest power of two up to CLUSTER_MAX
+// that the device can make resident (a constant of the device, so a problem's result
+// does not depend on the other problems of its launch).
+template <typename C>
+static int coarse_cluster_size() {
+  static int csize = 0;
+  if (csize == 0) {
+    cudaFuncSetAttribute(k_coarse_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int c = CLUSTER_MAX; c >= 1 && csize == 0; c >>= 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(c);
+      cfg.blockDim = dim3(CLUSTER_THREADS);
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = c;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      cfg.attrs = &at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_cluster<C>, &cfg) == cudaSuccess && nclusters > 0)
+        csize = c;
+    }
+    cudaGetLastError();
+    if (csize == 0) csize = 1;
+  }
+  return csize;
+}
+
+template <typename C>
+void launch_coarse_cluster(int dim, const LevelDev<C>* levs, int lev_stride, const CoarseLU* lus, int nprob,
+                           int nu1, int nu2, cudaStream_t st) {
+  const int c = coarse_cluster_size<C>();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nprob * c);
+  cfg.blockDim = dim3(CLUSTER_THREADS);
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = c;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_coarse_cluster<C>, levs, lev_stride, lus, nu1, nu2, dim);
 }
 
 template <typename C>
@@ -139,6 +186,8 @@ void launch_store_output(int dim, int n, const LevelDev<C>* levs, void* dst, int
                                  cudaStream_t);                                                               \
   template void launch_coarse_smem<C>(int, const LevelDev<C>*, int, int, const CoarseLU*, int, int, int, size_t, \
                                       cudaStream_t);                                                          \
+  template void launch_coarse_cluster<C>(int, const LevelDev<C>*, int, const CoarseLU*, int, int, int,       \
+                                         cudaStream_t);                                                       \
   template void launch_load_input<C>(int, const LevelDev<C>*, int, const void*, int, cudaStream_t);           \
   template void launch_store_output<C>(int, int, const LevelDev<C>*, void*, int, cudaStream_t);
 
