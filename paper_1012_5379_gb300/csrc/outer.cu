@@ -262,7 +262,7 @@ __device__ __forceinline__ double warp_transpose_sum16(double (&v)[16], int lane
 }
 
 template <typename C>
-__global__ void __launch_bounds__(DOT_THREADS)
+__global__ void __launch_bounds__(DOT_THREADS, 2)
 k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
   extern __shared__ double sred[];  // [warp][2 (m + 1)] per-warp sums of the unit
   __shared__ int s_last;
