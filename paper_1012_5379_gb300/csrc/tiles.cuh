@@ -53,7 +53,6 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int 
   typedef typename CT<C>::R R;
   __shared__ C vt[T2Y + 2][T2X + 2];
   __shared__ R sm[32 * (2 * J + 1)];
-  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   auto* sc = L.sc;
@@ -115,6 +114,7 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int 
 #pragma unroll
   for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
   red[2 * J] = accn;
+  pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<2 * J + 1>(red, L.part, tile, ntiles, &sc->counter, sm, tot))
     block_sweep_after_pass<R, J>(sc, tot);
 }
@@ -125,7 +125,6 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
   typedef typename CT<C>::R R;
   __shared__ C vb[4][T3Y + 2][T3X + 2];
   __shared__ R sm[32 * (2 * J + 1)];
-  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   auto* sc = L.sc;
@@ -197,6 +196,7 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
 #pragma unroll
   for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
   red[2 * J] = accn;
+  pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<2 * J + 1>(red, L.part, tile, ntiles, &sc->counter, sm, tot))
     block_sweep_after_pass<R, J>(sc, tot);
 }
@@ -212,7 +212,6 @@ k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int
   typedef typename CT<C>::R R;
   __shared__ C rt[T2Y + 1][T2X + 1];
   __shared__ R sm[32];
-  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
@@ -257,6 +256,7 @@ k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int
     if (valid) acc += cabs2(out);
   }
   R red[1] = {acc}, tot[1];
+  pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.scc, tot[0], L.s);
   }
@@ -268,7 +268,6 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
   typedef typename CT<C>::R R;
   __shared__ C rb[4][T3Y + 1][T3X + 1];
   __shared__ R sm[32];
-  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
@@ -323,6 +322,7 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
     }
   }
   R red[1] = {acc}, tot[1];
+  pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.scc, tot[0], L.s);
   }
@@ -336,7 +336,6 @@ k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles) {
   typedef typename CT<C>::R R;
   __shared__ C vt[T2Y + 2][T2X + 2];
   __shared__ R sm[32];
-  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
@@ -379,6 +378,7 @@ k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles) {
     }
   }
   R red[1] = {acc}, tot[1];
+  pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
   }
@@ -390,7 +390,6 @@ k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
   typedef typename CT<C>::R R;
   __shared__ C vb[4][T3Y + 2][T3X + 2];
   __shared__ R sm[32];
-  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
@@ -438,6 +437,7 @@ k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
     }
   }
   R red[1] = {acc}, tot[1];
+  pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
   }

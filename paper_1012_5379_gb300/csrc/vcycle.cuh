@@ -111,7 +111,6 @@ __global__ void __launch_bounds__(256)
 k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mode, int r0_is_b, int xsel,
               int x_from_zero) {
   __shared__ typename CT<C>::R sm[32];
-  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
@@ -136,6 +135,7 @@ k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mod
   }
   if (!want_r) return;
   typename CT<C>::R red[1] = {acc}, tot[1];
+  pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
   }
@@ -147,7 +147,6 @@ template <typename Cin, typename C>
 __global__ void __launch_bounds__(256)
 k_load_input(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, const Cin* __restrict__ src) {
   __shared__ typename CT<C>::R sm[32];
-  pdl_trigger();
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
@@ -164,6 +163,7 @@ k_load_input(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, const Ci
     acc += cabs2(v);
   }
   typename CT<C>::R red[1] = {acc}, tot[1];
+  pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
   }

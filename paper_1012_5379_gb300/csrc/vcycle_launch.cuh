@@ -8,9 +8,11 @@
 namespace helm {
 
 // Launch with programmatic stream serialisation: the kernel may start while its
-// predecessor finishes and synchronises with it through griddepcontrol.wait.
-// Only grids that fit in one wave use it: they are latency-bound, while a
-// multi-wave grid gains nothing from an early start of its successor.
+// predecessor finishes and synchronises with it through griddepcontrol.wait.  The
+// passes that end in a grid reduction signal their dependents only after their main
+// work, so waiting dependents never hold SM slots the predecessor's later waves need;
+// the launch latency and the dependent's prologue then overlap the predecessor's
+// reduction tail.
 static inline int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -32,9 +34,8 @@ static inline void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  const bool one_wave = (long long)grid.x * grid.y * grid.z <= 2LL * sm_count();
-  cfg.attrs = one_wave ? attr : nullptr;
-  cfg.numAttrs = one_wave ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
