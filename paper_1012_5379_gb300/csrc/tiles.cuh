@@ -48,19 +48,19 @@ __device__ __forceinline__ C stencil5(const Coef3<C>& cx, const Coef3<C>& cy, ty
 
 // ------------------------------------------------------------------ Arnoldi step J
 template <typename C, int J>
-__global__ void __launch_bounds__(256)
-k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int store_p) {
+__global__ void __launch_bounds__(256, J <= 2 ? 4 : 3)
+k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_is_b, int store_p) {
   typedef typename CT<C>::R R;
   __shared__ C vt[T2Y + 2][T2X + 2];
   __shared__ R sm[32 * (2 * J + 1)];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const int nunits = ceil_div(ntiles, tpc);
+  const int prob = blockIdx.x / nunits, unit = blockIdx.x - prob * nunits;
   const LevelDev<C>& L = levs[prob];
   auto* sc = L.sc;
   pdl_wait();
   if (sc->m < J) return;  // earlier breakdown or empty sweep: uniform for the problem
   const int n = L.n, P = L.P;
   const int ntx = ceil_div(P, T2X);
-  const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
   const C* Rk[J];
   C cf[J];
@@ -69,53 +69,59 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int 
     Rk[k] = (k == 0) ? (r0_is_b ? L.b : L.r0) : L.p[k - 1];
     cf[k] = sc->Cf[J][k];
   }
-  C raw[4][J];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
-    C v = czero<C>();
-#pragma unroll
-    for (int k = 0; k < J; ++k) {
-      raw[q][k] = ldc(Rk[k], x0 + ox, y0 + oy, 0, n, P);
-      v = cfma(cf[k], raw[q][k], v);
-    }
-    vt[oy + 1][ox + 1] = v;
-  }
-  if (tid < HALO2) {
-    int hx, hy;
-    halo_coord<T2X, T2Y>(tid, hx, hy);
-    C v = czero<C>();
-#pragma unroll
-    for (int k = 0; k < J; ++k) v = cfma(cf[k], ldc(Rk[k], x0 + hx, y0 + hy, 0, n, P), v);
-    vt[hy + 1][hx + 1] = v;
-  }
-  __syncthreads();
   C acc[J];
 #pragma unroll
   for (int k = 0; k < J; ++k) acc[k] = czero<C>();
   R accn = 0;
-  const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+  const int t_end = min(ntiles, (unit + 1) * tpc);
+#pragma unroll 1
+  for (int tile = unit * tpc; tile < t_end; ++tile) {
+    const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
+    C raw[4][J];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
-    const int x = x0 + ox, y = y0 + oy;
-    C p = czero<C>();
-    if (x < n && y < n) {
-      const Coef3<C> cy = ldcoef(L, y);
-      p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox], vt[oy + 1][ox + 2],
-                   vt[oy][ox + 1], vt[oy + 2][ox + 1]);
+    for (int q = 0; q < 4; ++q) {
+      const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+      C v = czero<C>();
 #pragma unroll
-      for (int k = 0; k < J; ++k) acc[k] = cdotacc(raw[q][k], p, acc[k]);
-      accn += cabs2(p);
+      for (int k = 0; k < J; ++k) {
+        raw[q][k] = ldc(Rk[k], x0 + ox, y0 + oy, 0, n, P);
+        v = cfma(cf[k], raw[q][k], v);
+      }
+      vt[oy + 1][ox + 1] = v;
     }
-    if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, 0, P)] = p;
+    if (tid < HALO2) {
+      int hx, hy;
+      halo_coord<T2X, T2Y>(tid, hx, hy);
+      C v = czero<C>();
+#pragma unroll
+      for (int k = 0; k < J; ++k) v = cfma(cf[k], ldc(Rk[k], x0 + hx, y0 + hy, 0, n, P), v);
+      vt[hy + 1][hx + 1] = v;
+    }
+    __syncthreads();
+    const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+      const int x = x0 + ox, y = y0 + oy;
+      C p = czero<C>();
+      if (x < n && y < n) {
+        const Coef3<C> cy = ldcoef(L, y);
+        p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
+                     vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
+#pragma unroll
+        for (int k = 0; k < J; ++k) acc[k] = cdotacc(raw[q][k], p, acc[k]);
+        accn += cabs2(p);
+      }
+      if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, 0, P)] = p;
+    }
+    __syncthreads();  // the next tile rewrites vt
   }
   R red[2 * J + 1], tot[2 * J + 1];
 #pragma unroll
   for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
   red[2 * J] = accn;
   pdl_trigger();  // the main work is done: let the next pass launch
-  if (grid_sum_last<2 * J + 1>(red, L.part, tile, ntiles, &sc->counter, sm, tot))
+  if (grid_sum_last<2 * J + 1>(red, L.part, unit, nunits, &sc->counter, sm, tot))
     block_sweep_after_pass<R, J>(sc, tot);
 }
 
@@ -208,56 +214,63 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
 // plus one row/column above (x0+64, y0+16).
 template <typename C>
 __global__ void __launch_bounds__(256)
-k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int r0_is_b, int x_from_zero, int nosmooth) {
+k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_is_b, int x_from_zero,
+              int nosmooth) {
   typedef typename CT<C>::R R;
   __shared__ C rt[T2Y + 1][T2X + 1];
   __shared__ R sm[32];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const int nunits = ceil_div(ntiles, tpc);
+  const int prob = blockIdx.x / nunits, unit = blockIdx.x - prob * nunits;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
   pdl_wait();
   const int ntx = ceil_div(P, T2X);
-  const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
   UpdCoef<C> u = load_upd(L, r0_is_b);
   if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
-    const int x = x0 + ox, y = y0 + oy;
-    C dx, r;
-    upd_point(u, x, y, 0, n, P, dx, r);
-    if (x < P && y < P) {
-      const size_t id = pidx(x, y, 0, P);
-      L.xa[id] = (x < n && y < n) ? cadd(x_from_zero ? czero<C>() : L.xa[id], dx) : czero<C>();
-    }
-    rt[oy][ox] = r;
-  }
-  if (tid < T2X + 1 + T2Y) {
-    const int hx = tid < T2X + 1 ? tid : T2X;
-    const int hy = tid < T2X + 1 ? T2Y : tid - (T2X + 1);
-    C dx, r;
-    upd_point(u, x0 + hx, y0 + hy, 0, n, P, dx, r);
-    rt[hy][hx] = r;
-  }
-  __syncthreads();
-  const int fx = 2 * lx + 1, fy = 2 * ly + 1;
-  C out = czero<C>();
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx)
-      out = cadd(out, cscale(rt[fy + dy][fx + dx], (R)((dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25))));
-  const int Ix = x0 / 2 + lx, Iy = y0 / 2 + ly;
   R acc = 0;
-  if (Ix < Pc && Iy < Pc) {
-    const bool valid = Ix < nc && Iy < nc;
-    L.bc[pidx(Ix, Iy, 0, Pc)] = valid ? out : czero<C>();
-    if (valid) acc += cabs2(out);
+  const int t_end = min(ntiles, (unit + 1) * tpc);
+#pragma unroll 1
+  for (int tile = unit * tpc; tile < t_end; ++tile) {
+    const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+      const int x = x0 + ox, y = y0 + oy;
+      C dx, r;
+      upd_point(u, x, y, 0, n, P, dx, r);
+      if (x < P && y < P) {
+        const size_t id = pidx(x, y, 0, P);
+        L.xa[id] = (x < n && y < n) ? cadd(x_from_zero ? czero<C>() : L.xa[id], dx) : czero<C>();
+      }
+      rt[oy][ox] = r;
+    }
+    if (tid < T2X + 1 + T2Y) {
+      const int hx = tid < T2X + 1 ? tid : T2X;
+      const int hy = tid < T2X + 1 ? T2Y : tid - (T2X + 1);
+      C dx, r;
+      upd_point(u, x0 + hx, y0 + hy, 0, n, P, dx, r);
+      rt[hy][hx] = r;
+    }
+    __syncthreads();
+    const int fx = 2 * lx + 1, fy = 2 * ly + 1;
+    C out = czero<C>();
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx)
+        out = cadd(out, cscale(rt[fy + dy][fx + dx], (R)((dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25))));
+    const int Ix = x0 / 2 + lx, Iy = y0 / 2 + ly;
+    if (Ix < Pc && Iy < Pc) {
+      const bool valid = Ix < nc && Iy < nc;
+      L.bc[pidx(Ix, Iy, 0, Pc)] = valid ? out : czero<C>();
+      if (valid) acc += cabs2(out);
+    }
+    __syncthreads();  // the next tile rewrites rt
   }
   R red[1] = {acc}, tot[1];
   pdl_trigger();  // the main work is done: let the next pass launch
-  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
+  if (grid_sum_last<1>(red, L.part, unit, nunits, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.scc, tot[0], L.s);
   }
 }
@@ -332,54 +345,60 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
 // x_b = x_a + P e_c, r0 = b - M x_b, ||r0||^2 starts post-smoothing.
 template <typename C>
 __global__ void __launch_bounds__(256)
-k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles) {
+k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc) {
   typedef typename CT<C>::R R;
   __shared__ C vt[T2Y + 2][T2X + 2];
   __shared__ R sm[32];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const int nunits = ceil_div(ntiles, tpc);
+  const int prob = blockIdx.x / nunits, unit = blockIdx.x - prob * nunits;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
   pdl_wait();
   const int ntx = ceil_div(P, T2X);
-  const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
   auto form = [&](int xx, int yy) -> C {
     return cadd(ldc((const C*)L.xa, xx, yy, 0, n, P), interp(L, xx, yy, 0, 2));
   };
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
-    vt[oy + 1][ox + 1] = form(x0 + ox, y0 + oy);
-  }
-  if (tid < HALO2) {
-    int hx, hy;
-    halo_coord<T2X, T2Y>(tid, hx, hy);
-    vt[hy + 1][hx + 1] = form(x0 + hx, y0 + hy);
-  }
-  __syncthreads();
   R acc = 0;
-  const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+  const int t_end = min(ntiles, (unit + 1) * tpc);
+#pragma unroll 1
+  for (int tile = unit * tpc; tile < t_end; ++tile) {
+    const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
-    const int x = x0 + ox, y = y0 + oy;
-    if (x < P && y < P) {
-      C r = czero<C>(), xo = czero<C>();
-      if (x < n && y < n) {
-        const Coef3<C> cy = ldcoef(L, y);
-        const C p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
-                             vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
-        r = csub(__ldg(L.b + pidx(x, y, 0, P)), p);
-        xo = vt[oy + 1][ox + 1];
-        acc += cabs2(r);
-      }
-      L.xb[pidx(x, y, 0, P)] = xo;
-      L.r0[pidx(x, y, 0, P)] = r;
+    for (int q = 0; q < 4; ++q) {
+      const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+      vt[oy + 1][ox + 1] = form(x0 + ox, y0 + oy);
     }
+    if (tid < HALO2) {
+      int hx, hy;
+      halo_coord<T2X, T2Y>(tid, hx, hy);
+      vt[hy + 1][hx + 1] = form(x0 + hx, y0 + hy);
+    }
+    __syncthreads();
+    const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+      const int x = x0 + ox, y = y0 + oy;
+      if (x < P && y < P) {
+        C r = czero<C>(), xo = czero<C>();
+        if (x < n && y < n) {
+          const Coef3<C> cy = ldcoef(L, y);
+          const C p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
+                               vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
+          r = csub(__ldg(L.b + pidx(x, y, 0, P)), p);
+          xo = vt[oy + 1][ox + 1];
+          acc += cabs2(r);
+        }
+        L.xb[pidx(x, y, 0, P)] = xo;
+        L.r0[pidx(x, y, 0, P)] = r;
+      }
+    }
+    __syncthreads();  // the next tile rewrites vt
   }
   R red[1] = {acc}, tot[1];
   pdl_trigger();  // the main work is done: let the next pass launch
-  if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
+  if (grid_sum_last<1>(red, L.part, unit, nunits, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
   }
 }

@@ -105,7 +105,10 @@ __device__ __forceinline__ void upd_point(const UpdCoef<C>& u, int x, int y, int
 }
 
 // Pointwise end of a sweep: x += dx (in place on xa or xb, or from zero) and, in
-// residual mode, r0 <- r (in place) with ||r||^2 starting the next sweep.
+// residual mode, r0 <- r (in place) with ||r||^2 starting the next sweep.  Every
+// vector is zero at the padding positions, so this is a plain stream over the padded
+// index (UF_U points per thread at a time, all loads before the stores).
+constexpr int UF_U = 4;
 template <typename C>
 __global__ void __launch_bounds__(256)
 k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mode, int r0_is_b, int xsel,
@@ -113,24 +116,42 @@ k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mod
   __shared__ typename CT<C>::R sm[32];
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
-  const int n = L.n, P = L.P;
+  const int P = L.P;
   pdl_wait();
   const UpdCoef<C> u = load_upd(L, r0_is_b);
   C* xo = xsel ? L.xb : L.xa;
   const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
   const bool want_r = (mode == UPD_RESIDUAL);
+  const size_t stride = (size_t)ntiles * blockDim.x;
   typename CT<C>::R acc = 0;
-  for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < npts; i += (size_t)ntiles * blockDim.x) {
-    const int x = (int)(i % P);
-    const int y = (int)((i / P) % P);
-    const int z = dim == 3 ? (int)(i / ((size_t)P * P)) : 0;
-    C dx, r;
-    upd_point<C, false>(u, x, y, z, n, P, dx, r, want_r);
-    C xv = x_from_zero ? czero<C>() : xo[i];
-    xo[i] = cadd(xv, dx);
-    if (want_r) {
-      L.r0[i] = r;
-      acc += cabs2(r);
+  for (size_t i0 = (size_t)tile * blockDim.x + threadIdx.x; i0 < npts; i0 += UF_U * stride) {
+    C xn[UF_U], rn[UF_U];
+#pragma unroll
+    for (int q = 0; q < UF_U; ++q) {
+      const size_t i = i0 + q * stride;
+      C dx = czero<C>(), r = czero<C>();
+      if (i < npts) {
+#pragma unroll
+        for (int k = 0; k <= SMAX; ++k) {
+          if (k < u.m || (want_r && k == u.m)) {
+            const C v = u.Rk[k][i];
+            if (k < u.m) dx = cfma(u.xc[k], v, dx);
+            r = cfma(u.rc[k], v, r);
+          }
+        }
+        xn[q] = cadd(x_from_zero ? czero<C>() : xo[i], dx);
+      }
+      rn[q] = r;
+    }
+#pragma unroll
+    for (int q = 0; q < UF_U; ++q) {
+      const size_t i = i0 + q * stride;
+      if (i >= npts) continue;
+      xo[i] = xn[q];
+      if (want_r) {
+        L.r0[i] = rn[q];
+        acc += cabs2(rn[q]);
+      }
     }
   }
   if (!want_r) return;

@@ -39,11 +39,39 @@ static inline void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// Tiles per CTA of a 2D pass for one problem of `ntiles` tiles: each CTA pays a fixed
+// cost (its reduction, the atomic, the ramp; about half a tile's time on GB300) plus
+// the cost of its tiles, so t tiles per CTA take ceil(ntiles / (t slots)) rounds of
+// (1/2 + t) tile times; the smallest such t up to 8 wins.  A function of the level size and of the kernel's
+// residency on the device only (it fixes the order of the pass's partial sums).
+template <typename K>
+static int tiles_per_cta(K kernel, int ntiles) {
+  static thread_local K last_kernel = nullptr;
+  static thread_local int slots = 0;
+  if (kernel != last_kernel) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    slots = per_sm * sm_count();
+    last_kernel = kernel;
+  }
+  int best = 1;
+  long long best_cost = -1;
+  for (int t = 1; t <= 8; t *= 2) {
+    const long long rounds = (ntiles + (long long)t * slots - 1) / ((long long)t * slots);
+    const long long cost = rounds * (1 + 2 * t);
+    if (best_cost < 0 || cost < best_cost) { best = t; best_cost = cost; }
+  }
+  return best;
+}
+
 template <typename C, int J>
 static void arnoldi_J(int dim, const LevelDev<C>* levs, int grid, int ntiles, TileCfg cfg, bool r0_is_b,
                       bool store_p, cudaStream_t st) {
-  if (dim == 2)
-    pdl_launch(k_arnoldi_t2<C, J>, dim3(grid), dim3(dim3(32, 8)), 0, st, levs, ntiles, r0_is_b, store_p);
+  if (dim == 2) {
+    const int t = tiles_per_cta(k_arnoldi_t2<C, J>, ntiles);
+    pdl_launch(k_arnoldi_t2<C, J>, dim3(grid / ntiles * ceil_div(ntiles, t)), dim3(dim3(32, 8)), 0, st, levs, ntiles, t,
+               r0_is_b, store_p);
+  }
   else
     pdl_launch(k_arnoldi_t3<C, J>, dim3(grid), dim3(dim3(32, 8)), 0, st, levs, ntiles, cfg.rows, r0_is_b, store_p);
 }
@@ -64,7 +92,9 @@ template <typename C>
 void launch_restrict(int dim, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
                      bool x_from_zero, bool nosmooth, cudaStream_t st) {
   if (dim == 2)
-    pdl_launch(k_restrict_t2<C>, dim3(nprob * ntiles), dim3(dim3(32, 8)), 0, st, levs, ntiles, r0_is_b, x_from_zero, nosmooth);
+    pdl_launch(k_restrict_t2<C>, dim3(nprob * ceil_div(ntiles, tiles_per_cta(k_restrict_t2<C>, ntiles))),
+               dim3(dim3(32, 8)), 0, st, levs, ntiles, tiles_per_cta(k_restrict_t2<C>, ntiles), r0_is_b, x_from_zero,
+               nosmooth);
   else
     pdl_launch(k_restrict_t3<C>, dim3(nprob * ntiles), dim3(dim3(32, 8)), 0, st, levs, ntiles, cfg.rows, r0_is_b, x_from_zero, nosmooth);
 }
@@ -81,7 +111,8 @@ void launch_prolong(int dim, bool with_residual, const LevelDev<C>* levs, int np
   if (!with_residual) {
     pdl_launch(k_prolong_flat<C>, dim3(nprob * ntiles), dim3(256), 0, st, levs, ntiles, dim);
   } else if (dim == 2) {
-    pdl_launch(k_prolong_t2<C>, dim3(nprob * ntiles), dim3(dim3(32, 8)), 0, st, levs, ntiles);
+    pdl_launch(k_prolong_t2<C>, dim3(nprob * ceil_div(ntiles, tiles_per_cta(k_prolong_t2<C>, ntiles))),
+               dim3(dim3(32, 8)), 0, st, levs, ntiles, tiles_per_cta(k_prolong_t2<C>, ntiles));
   } else {
     pdl_launch(k_prolong_t3<C>, dim3(nprob * ntiles), dim3(dim3(32, 8)), 0, st, levs, ntiles, cfg.rows);
   }
