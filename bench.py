@@ -388,6 +388,42 @@ def run_single(args):
                       "rel_res_true": info.rel_res_true, "s": time.perf_counter() - t0}), flush=True)
 
 
+def run_cube(args):
+    """The 3D workload: 255^3 unit cube, heterogeneous k(x) = 80 (1 + 0.3 g(x)) with
+    8 seeded Gaussian bumps, point source, theta_beta 0.4, FGMRES(40) to 1e-6.  One
+    solve with the complex64 and one with the complex128 preconditioner (each timed
+    with CUDA events after an untimed solve)."""
+    import torch
+
+    from paper_1012_5379_gb300 import helm
+    dev = torch.device("cuda", 0)
+    w = I.cube_3d(args.n if args.n in (63, 127, 255) else 255)
+    b = torch.from_numpy(w.b).to(dev)
+    phi = torch.from_numpy(w.phi).to(dev)
+    out = {"mode": "cube", "config": {"workload": f"3D {w.n}^3 unit cube, k(x)=80(1+0.3 g(x)), 8 seeded bumps "
+                                                  "(seed 1002, sigma 0.1), point source, theta_beta 0.4, ECS 1/8 at "
+                                                  "0.5 rad, V(1,1) GMRES(3), FGMRES(40) to 1e-6"}}
+    for prec in ("c64", "c128"):
+        h = helm.Handle(3, w.n, w.theta_beta, phi=phi, precision=prec, restart=w.restart, maxit=400)
+        x = torch.zeros_like(b)
+        h.solve(b, x, w.tol)
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        info = h.solve(b, x, w.tol)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        out[prec] = {"iters": info.iters, "restarts": info.restarts, "rel_res_true": info.rel_res_true,
+                     "status": info.status, "s": sec, "vcycle_mpts_per_s": float(w.n) ** 3 * info.iters / sec / 1e6,
+                     "device_bytes": h.workspace_bytes()}
+        h.close()
+        del h
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def _seq_solves(helm, works, precision, bs, xs):
     """Solve `works` one at a time on fresh handles of `precision` (each timed with CUDA
     events after one untimed solve of the same handle); returns per-problem seconds and
@@ -598,7 +634,7 @@ def main():
     ap.add_argument("--sequential-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single", "cube"], default="solve")
     ap.add_argument("--restart", type=int, default=0)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--requests", type=int, default=2000)
@@ -612,7 +648,8 @@ def main():
     if args.mode != "solve":
         from paper_1012_5379_gb300 import build
         build.build()
-        {"precond": run_precond, "batch": run_batch, "serve": run_serve, "single": run_single}[args.mode](args)
+        {"precond": run_precond, "batch": run_batch, "serve": run_serve, "single": run_single,
+         "cube": run_cube}[args.mode](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -811,27 +811,78 @@ struct ActiveSet {
   }
 };
 
+// A second stream per host thread for batched solves.
+static cudaStream_t side_stream() {
+  thread_local cudaStream_t s2 = nullptr;
+  if (!s2) cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+  return s2;
+}
+
+// Batched solve.  With two or more problems the batch is split into two halves that
+// iterate on two streams: one half's latency-bound V-cycle levels run beside the
+// other half's FP64-bound outer passes.  Each problem's arithmetic does not depend
+// on the grouping, so results are the same as in one group or alone.
 template <typename C>
 static int solve_t(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
                    helm_info* infos, cudaStream_t st) {
-  ActiveSet<C> set;
+  const int nsets = count >= 2 ? 2 : 1;
+  cudaStream_t sts[2] = {st, nsets == 2 ? side_stream() : st};
+  if (nsets == 2 && !sts[1]) { set_error("cudaStreamCreate failed"); return HELM_ECUDA; }
+  ActiveSet<C> sets[2];
   for (int p = 0; p < count; ++p) {
     TRY(begin_problem(hs[p], (const double2*)b[p], (const double2*)x[p], tol, st));
-    set.add(hs[p]);
+    sets[p % nsets].add(hs[p]);
+  }
+  cudaEvent_t ev = nullptr;
+  if (nsets == 2) {  // the side stream starts after the inputs are in place
+    CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(ev, st));
+    CUDA_TRY(cudaStreamWaitEvent(sts[1], ev, 0));
   }
   std::vector<std::pair<Handle*, OuterState>> done;
   int max_maxit = 0;
   for (int p = 0; p < count; ++p) max_maxit = std::max(max_maxit, hs[p]->maxit);
-  // the first iterate() runs every problem's initial residual before its first V-cycle
-  for (int guard = 0; guard <= 2 * max_maxit + 4 && !set.members.empty(); ++guard) {
-    TRY(set.iterate(st));
-    TRY(set.collect(st, &done));
+  // The first iterate() runs every problem's initial residual before its first
+  // V-cycle.  Each half is relaunched as soon as its own iteration has finished, so
+  // the two drift into different phases.
+  int rc = HELM_OK;
+  bool inflight[2] = {false, false};
+  int rounds[2] = {0, 0};
+  const int guard = 2 * max_maxit + 4;
+  while (rc == HELM_OK) {
+    bool busy = false;
+    for (int k = 0; k < nsets && rc == HELM_OK; ++k) {
+      if (inflight[k]) {
+        const cudaError_t q = nsets == 1 ? cudaSuccess : cudaStreamQuery(sts[k]);
+        if (q == cudaErrorNotReady) { busy = true; continue; }
+        if (q != cudaSuccess) { set_error(cudaGetErrorString(q)); rc = HELM_ECUDA; break; }
+        rc = sets[k].collect(sts[k], &done);
+        inflight[k] = false;
+      }
+      if (rc == HELM_OK && !sets[k].members.empty() && rounds[k] <= guard) {
+        rc = sets[k].iterate(sts[k]);
+        inflight[k] = true;
+        rounds[k] += 1;
+        busy = true;
+      }
+    }
+    if (!busy) break;
   }
-  for (Handle* h : set.members) {  // only on a failed guard: report what they have
-    OuterState s;
-    CUDA_TRY(cudaMemcpy(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost));
-    done.push_back({h, s});
+  if (nsets == 2) {  // the main stream continues after the side stream's work
+    if (rc == HELM_OK) {
+      cudaError_t e = cudaEventRecord(ev, sts[1]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+      if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = HELM_ECUDA; }
+    }
+    cudaEventDestroy(ev);
   }
+  TRY(rc);
+  for (int k = 0; k < nsets; ++k)
+    for (Handle* h : sets[k].members) {  // only on a failed guard: report what they have
+      OuterState s;
+      CUDA_TRY(cudaMemcpy(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost));
+      done.push_back({h, s});
+    }
   int rc_all = HELM_OK;
   for (int p = 0; p < count; ++p) {
     for (auto& d : done) {

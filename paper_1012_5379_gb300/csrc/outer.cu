@@ -429,6 +429,12 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
     }
     __syncthreads();
     const double inv = start ? 1.0 / st->beta : 1.0;
+    // The next V-cycle's input is u / ||w|| (start: r / beta): the preconditioned
+    // operator maps it back to O(1) norms, so its magnitude does not drift over a
+    // cycle (an unscaled u shrinks geometrically and would underflow complex64).
+    // FGMRES is exact for any scaling of z_j: w = H z_j and the Hessenberg column
+    // inherit it, and x = Z y cancels it.
+    const double bsc = start ? 1.0 : (st->wnorm2 > 0.0 ? 1.0 / sqrt(st->wnorm2) : 1.0);
     const int jn = j + 1;
     double2* vout = O.V + (size_t)jn * O.vs;
     double accu = 0.0;
@@ -449,7 +455,7 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
       wv = make_double2(wv.x * inv, wv.y * inv);
       vout[idx] = wv;
       accu += dabs2(wv);
-      C c = from_d<C>(wv);
+      C c = from_d<C>(make_double2(wv.x * bsc, wv.y * bsc));
       O.b0[idx] = c;
       accb += cabs2(c);
     }
@@ -467,7 +473,8 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
           givens_step(O, st, j, hn);
           st->iters += 1;
           st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
-          const bool breakdown = !(hn > 1e-14 * st->beta);
+          // lucky breakdown: the new direction vanishes against H z_j
+        const bool breakdown = !(hn > 1e-14 * sqrt(st->wnorm2));
           if (!isfinite(st->rel_est)) { st->done = 3; st->status = -4; st->cycle_end = 1; }
           else if (st->rel_est <= st->tol || st->iters >= st->maxit || j + 1 >= st->m || breakdown) st->cycle_end = 1;
           else st->j = jn;
