@@ -150,7 +150,9 @@ int helm_batch_solve_host(helm_handle* const* hs, int count, const double* const
 /* ---------------------------------------------------------------------------------
  * Serving: continuous batching of solves (the workload of Sec. 5 as a service).
  * A worker thread owns the device.  Between outer FGMRES iterations it admits queued
- * requests in arrival order while the device-memory budget allows, iterates every
+ * requests while the device-memory budget allows (in arrival order, except that a
+ * request an idle slot or the free budget can serve may pass a waiting head a bounded
+ * number of times), iterates every
  * admitted problem of a dimension together (one launch per V-cycle level and outer
  * kernel for all of them; 2D and 3D on separate streams, so their kernels overlap),
  * and retires problems as they converge.  Idle problem slots of the same shape are

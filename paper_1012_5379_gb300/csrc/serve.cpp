@@ -5,7 +5,8 @@
 // are iterated by two runners on two streams that advance independently: whenever a
 // runner's stream has finished its outer iteration, the worker reads the states,
 // retires converged problems (their solutions are copied back asynchronously), admits
-// queued requests in arrival order while the device-memory budget allows, and
+// queued requests (in arrival order up to a bounded overtaking, see admit()) while the
+// device-memory budget allows, and
 // launches the next iteration of every problem of that dimension together (one launch
 // per V-cycle level and per outer kernel for all of them).  Each request runs in a
 // problem slot: a handle re-targeted to the request's k and theta_beta.  Idle slots
@@ -76,6 +77,7 @@ struct Server {
   size_t bytes_in_use = 0;
   BatchRunner* run[2] = {nullptr, nullptr};
   cudaStream_t st[2] = {nullptr, nullptr};
+  cudaStream_t setup_st = nullptr;
   bool inflight[2] = {false, false};
   std::vector<Draining> draining;
   std::vector<cudaEvent_t> free_events;
@@ -117,16 +119,42 @@ struct Server {
     }
   }
 
-  // Admit queued requests in arrival order while slots and memory allow.
+  // Admit queued requests while slots and memory allow.  Arrival order is kept, except
+  // that a request whose shape has an idle slot, or that fits the free budget, may
+  // pass a head that would need slots evicted; the head is passed at most
+  // MAX_OVERTAKE times in a row (then idle slots are evicted for it), and only the
+  // first WINDOW queued requests are considered.
+  static constexpr int WINDOW = 64, MAX_OVERTAKE = 32;
+  int head_overtaken = 0;
+  size_t estimate(const ServeRequest* r) const {
+    return estimate_handle_bytes(r->dim, r->n, opts.precond_prec, opts.s, opts.restart, opts.maxit, 3);
+  }
+  bool has_idle(const ServeRequest* r) const {
+    auto it = pool.find(std::make_pair(r->dim, r->n));
+    return it != pool.end() && !it->second.empty();
+  }
+
   int admit() {
     for (;;) {
       ServeRequest* r = nullptr;
+      bool evict = false;
       {
         std::lock_guard<std::mutex> lk(mu);
         if (queue.empty()) return HELM_OK;
         const int active = runner_size(run[0]) + runner_size(run[1]);
         if (opts.max_active > 0 && active >= opts.max_active) return HELM_OK;
-        r = queue.front();
+        const size_t nscan = std::min<size_t>(queue.size(), WINDOW);
+        size_t pick = nscan;
+        for (size_t i = 0; i < nscan; ++i) {
+          const ServeRequest* q = queue[i];
+          const size_t est = estimate(q);
+          if (has_idle(q) || est > opts.budget_bytes || bytes_in_use + est <= opts.budget_bytes) { pick = i; break; }
+          if (i == 0 && (head_overtaken >= MAX_OVERTAKE || active == 0)) { pick = 0; evict = true; break; }
+        }
+        if (pick == nscan) return HELM_OK;  // wait for completions
+        r = queue[pick];
+        queue.erase(queue.begin() + pick);
+        head_overtaken = pick > 0 ? head_overtaken + 1 : 0;
       }
       const int di = r->dim == 3 ? 1 : 0;
       const auto key = std::make_pair(r->dim, r->n);
@@ -138,24 +166,28 @@ struct Server {
         stats.handles_reused += 1;
         TRY(retarget_handle(h, r->k, r->theta_beta, st[di]));
       } else {
-        const size_t est = estimate_handle_bytes(r->dim, r->n, opts.precond_prec, opts.s, opts.restart, opts.maxit, 3);
+        const size_t est = estimate(r);
         if (est > opts.budget_bytes) {
-          { std::lock_guard<std::mutex> lk(mu); queue.pop_front(); }
           set_error("request needs more device memory than the serving budget");
           finish_request(r, HELM_ENOMEM);
           continue;
         }
-        if (bytes_in_use + est > opts.budget_bytes) evict_idle(est);
-        if (bytes_in_use + est > opts.budget_bytes) return HELM_OK;  // wait for completions
+        if (evict && bytes_in_use + est > opts.budget_bytes) evict_idle(est);
+        if (bytes_in_use + est > opts.budget_bytes) {  // still no room: back to the head of the queue
+          std::lock_guard<std::mutex> lk(mu);
+          queue.push_front(r);
+          return HELM_OK;
+        }
         helm_grid g;
         g.dim = r->dim;
         g.n = r->n;
         g.ecs_frac = opts.ecs_frac;
         g.theta_gamma = opts.theta_gamma;
         const helm_opts o = handle_opts();
-        int rc = setup_handle(&g, nullptr, r->k, r->theta_beta, &o, st[di], &h);
+        // set up on a private stream: its synchronisation does not wait for the
+        // iteration in flight on the runner's stream
+        int rc = setup_handle(&g, nullptr, r->k, r->theta_beta, &o, setup_st, &h);
         if (rc != HELM_OK) {
-          { std::lock_guard<std::mutex> lk(mu); queue.pop_front(); }
           finish_request(r, rc);
           continue;
         }
@@ -163,7 +195,6 @@ struct Server {
         all_handles.push_back(h);
         stats.handles_created += 1;
       }
-      { std::lock_guard<std::mutex> lk(mu); queue.pop_front(); }
       owner[h] = r;
       // the source goes through the slot's dense staging vector (w, unused until the
       // problem's first outer iteration); stream order protects it
@@ -269,6 +300,10 @@ struct Server {
       }
       run[d] = runner_create(opts.precond_prec);
     }
+    if (rc == HELM_OK && cudaStreamCreateWithFlags(&setup_st, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("cudaStreamCreate failed");
+      rc = HELM_ECUDA;
+    }
     while (rc == HELM_OK) {
       rc = step();
       if (rc != HELM_OK) break;
@@ -294,6 +329,7 @@ struct Server {
     for (cudaEvent_t e : free_events) cudaEventDestroy(e);
     for (int d = 0; d < 2; ++d)
       if (st[d]) cudaStreamDestroy(st[d]);
+    if (setup_st) cudaStreamDestroy(setup_st);
   }
 };
 
