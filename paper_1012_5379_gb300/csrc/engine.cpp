@@ -811,33 +811,39 @@ struct ActiveSet {
   }
 };
 
-// A second stream per host thread for batched solves.
-static cudaStream_t side_stream() {
-  thread_local cudaStream_t s2 = nullptr;
-  if (!s2) cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
-  return s2;
+// Side streams per host thread for batched solves.
+constexpr int MAX_SETS = 4;
+static cudaStream_t side_stream(int k) {
+  thread_local cudaStream_t s[MAX_SETS] = {nullptr, nullptr, nullptr, nullptr};
+  if (!s[k]) cudaStreamCreateWithFlags(&s[k], cudaStreamNonBlocking);
+  return s[k];
 }
 
-// Batched solve.  With two or more problems the batch is split into two halves that
-// iterate on two streams: one half's latency-bound V-cycle levels run beside the
-// other half's FP64-bound outer passes.  Each problem's arithmetic does not depend
-// on the grouping, so results are the same as in one group or alone.
+// Batched solve.  The batch is split into two (fewer than 8 problems) or MAX_SETS sets
+// that iterate on their own streams: one set's latency-bound V-cycle levels run beside another's FP64-bound
+// outer passes.  Each problem's arithmetic does not depend on the grouping, so results
+// are the same as in one group or alone.
 template <typename C>
 static int solve_t(Handle* const* hs, int count, const double* const* b, double* const* x, double tol,
                    helm_info* infos, cudaStream_t st) {
-  const int nsets = count >= 2 ? 2 : 1;
-  cudaStream_t sts[2] = {st, nsets == 2 ? side_stream() : st};
-  if (nsets == 2 && !sts[1]) { set_error("cudaStreamCreate failed"); return HELM_ECUDA; }
-  ActiveSet<C> sets[2];
+  // measured on GB300: two sets for a handful of problems, four for larger batches
+  const int nsets = count >= 8 ? MAX_SETS : std::max(1, std::min(count, 2));
+  cudaStream_t sts[MAX_SETS];
+  sts[0] = st;
+  for (int k = 1; k < nsets; ++k) {
+    sts[k] = side_stream(k);
+    if (!sts[k]) { set_error("cudaStreamCreate failed"); return HELM_ECUDA; }
+  }
+  ActiveSet<C> sets[MAX_SETS];
   for (int p = 0; p < count; ++p) {
     TRY(begin_problem(hs[p], (const double2*)b[p], (const double2*)x[p], tol, st));
     sets[p % nsets].add(hs[p]);
   }
   cudaEvent_t ev = nullptr;
-  if (nsets == 2) {  // the side stream starts after the inputs are in place
+  if (nsets > 1) {  // the side streams start after the inputs are in place
     CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     CUDA_TRY(cudaEventRecord(ev, st));
-    CUDA_TRY(cudaStreamWaitEvent(sts[1], ev, 0));
+    for (int k = 1; k < nsets; ++k) CUDA_TRY(cudaStreamWaitEvent(sts[k], ev, 0));
   }
   std::vector<std::pair<Handle*, OuterState>> done;
   int max_maxit = 0;
@@ -846,8 +852,8 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
   // V-cycle.  Each half is relaunched as soon as its own iteration has finished, so
   // the two drift into different phases.
   int rc = HELM_OK;
-  bool inflight[2] = {false, false};
-  int rounds[2] = {0, 0};
+  bool inflight[MAX_SETS] = {false, false, false, false};
+  int rounds[MAX_SETS] = {0, 0, 0, 0};
   const int guard = 2 * max_maxit + 4;
   while (rc == HELM_OK) {
     bool busy = false;
@@ -868,9 +874,9 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
     }
     if (!busy) break;
   }
-  if (nsets == 2) {  // the main stream continues after the side stream's work
-    if (rc == HELM_OK) {
-      cudaError_t e = cudaEventRecord(ev, sts[1]);
+  if (nsets > 1) {  // the main stream continues after the side streams' work
+    for (int k = 1; k < nsets && rc == HELM_OK; ++k) {
+      cudaError_t e = cudaEventRecord(ev, sts[k]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
       if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = HELM_ECUDA; }
     }
