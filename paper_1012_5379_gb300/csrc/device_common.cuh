@@ -119,6 +119,28 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* sm) {
   __syncthreads();
 }
 
+// Per-thread sums of the partial slots t = tid, tid + threads, ... in a fixed order;
+// four slots' loads are in flight before their adds.
+template <int NV, typename T>
+__device__ __forceinline__ void sum_partials(const T* part, int ntiles, T (&acc)[NV]) {
+  const int tid = flat_tid(), nt = block_threads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = (T)0;
+  for (int t0 = tid; t0 < ntiles; t0 += 4 * nt) {
+    T v[4][NV];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u * nt;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[u][i] = t < ntiles ? __ldcg(part + (size_t)t * NPART + i) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] += v[u][i];
+  }
+}
+
 // Write this block's NV partial sums to slot `tile`, then report whether this block
 // is the last of `ntiles` blocks of its problem to arrive.  If so, the returned
 // block reduces all slots in a fixed order (independent of arrival order) and
@@ -143,11 +165,7 @@ __device__ __forceinline__ bool grid_sum_last(T (&v)[NV], void* partv, int tile,
   if (!s_last) return false;
   __threadfence();
   T acc[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = (T)0;
-  for (int t = tid; t < ntiles; t += block_threads())
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (size_t)t * NPART + i);
+  sum_partials<NV, T>(part, ntiles, acc);
   block_sum<NV, T>(acc, sm);
 #pragma unroll
   for (int i = 0; i < NV; ++i) tot[i] = acc[i];
@@ -195,14 +213,17 @@ __device__ inline void sweep_begin(SweepScalarsT<T>* sc, T beta2, int s) {
     return;
   }
   sc->m = s;
-  sc->G[0][0] = CT<CR>::make(beta2, 0);
   sc->Cf[1][0] = CT<CR>::make((T)1 / sqrt(beta2), 0);
 }
 
-// min || beta e1 - Hbar y || for the (M+1) x M Hessenberg matrix, complex Givens.
+// The sweep algebra works on register copies: every field it reads is loaded before
+// anything is computed (one memory latency instead of a chain), and the results are
+// stored at the end.
+
+// min || beta e1 - Hbar y || for the (M+1) x M Hessenberg matrix hh, complex Givens.
 // M is a compile-time constant so every array stays in registers.
 template <typename T, int M>
-__device__ __forceinline__ void sweep_lstsq(const typename CplxOf<T>::T (*Hh)[SMAX], T beta,
+__device__ __forceinline__ void sweep_lstsq(const typename CplxOf<T>::T (&hh)[SMAX + 1][SMAX], T beta,
                                             typename CplxOf<T>::T* y) {
   typedef typename CplxOf<T>::T CR;
   CR R[M + 1][M];
@@ -211,7 +232,7 @@ __device__ __forceinline__ void sweep_lstsq(const typename CplxOf<T>::T (*Hh)[SM
   for (int i = 0; i <= M; ++i) {
     g[i] = CT<CR>::make(i == 0 ? beta : (T)0, 0);
 #pragma unroll
-    for (int j = 0; j < M; ++j) R[i][j] = (i <= j + 1) ? Hh[i][j] : CT<CR>::make(0, 0);
+    for (int j = 0; j < M; ++j) R[i][j] = (i <= j + 1) ? hh[i][j] : CT<CR>::make(0, 0);
   }
 #pragma unroll
   for (int j = 0; j < M; ++j) {
@@ -247,24 +268,30 @@ __device__ __forceinline__ void sweep_lstsq(const typename CplxOf<T>::T (*Hh)[SM
   }
 }
 
+// Least-squares solution of the sweep and its update coefficients over the raw
+// vectors: x += sum_{k<M} xcoef[k] R_k, r = sum_{k<=M} rcoef[k] R_k.
 template <typename T, int M>
-__device__ __forceinline__ void sweep_finish(SweepScalarsT<T>* sc) {
+__device__ __forceinline__ void sweep_finish(SweepScalarsT<T>* sc, const typename CplxOf<T>::T (&hh)[SMAX + 1][SMAX],
+                                             const typename CplxOf<T>::T (&cf)[SMAX + 1][SMAX], T beta2) {
   typedef typename CplxOf<T>::T CR;
-  sc->m = M;
   CR y[M];
-  sweep_lstsq<T, M>(sc->Hh, sqrt(sc->beta2), y);
+  sweep_lstsq<T, M>(hh, sqrt(beta2), y);
+  CR xc[SMAX + 1], rc[SMAX + 1];
 #pragma unroll
-  for (int k = 0; k <= SMAX; ++k) { sc->xcoef[k] = CT<CR>::make(0, 0); sc->rcoef[k] = CT<CR>::make(0, 0); }
+  for (int k = 0; k <= SMAX; ++k) { xc[k] = CT<CR>::make(0, 0); rc[k] = CT<CR>::make(0, 0); }
 #pragma unroll
   for (int k = 0; k < M; ++k) {
     CR acc = CT<CR>::make(0, 0);
 #pragma unroll
-    for (int jj = k + 1; jj <= M; ++jj) acc = cadd(acc, cmul(y[jj - 1], sc->Cf[jj][k]));
-    sc->xcoef[k] = acc;
+    for (int jj = k + 1; jj <= M; ++jj) acc = cadd(acc, cmul(y[jj - 1], cf[jj][k]));
+    xc[k] = acc;
   }
-  sc->rcoef[0] = CT<CR>::make(1, 0);
+  rc[0] = CT<CR>::make(1, 0);
 #pragma unroll
-  for (int jj = 1; jj <= M; ++jj) sc->rcoef[jj] = CT<CR>::make(-y[jj - 1].x, -y[jj - 1].y);
+  for (int jj = 1; jj <= M; ++jj) rc[jj] = CT<CR>::make(-y[jj - 1].x, -y[jj - 1].y);
+  sc->m = M;
+#pragma unroll
+  for (int k = 0; k <= SMAX; ++k) { sc->xcoef[k] = xc[k]; sc->rcoef[k] = rc[k]; }
 }
 
 // After Arnoldi pass J: red[2k..2k+1] = <R_k, p_J> (k < J), red[2J] = ||p_J||^2.
@@ -272,42 +299,55 @@ __device__ __forceinline__ void sweep_finish(SweepScalarsT<T>* sc) {
 template <typename T, int J>
 __device__ __forceinline__ void sweep_after_pass(SweepScalarsT<T>* sc, const T* red) {
   typedef typename CplxOf<T>::T CR;
+  // every field the algebra reads, loaded first
+  CR cf[SMAX + 1][SMAX], hh[SMAX + 1][SMAX];
+#pragma unroll
+  for (int i = 1; i <= J; ++i)
+#pragma unroll
+    for (int k = 0; k < i; ++k) cf[i][k] = sc->Cf[i][k];
+#pragma unroll
+  for (int j = 0; j + 1 < J; ++j)
+#pragma unroll
+    for (int i = 0; i <= j + 1; ++i) hh[i][j] = sc->Hh[i][j];
+  const int s = sc->s;
+  const T beta2 = sc->beta2;
   CR g[J];
 #pragma unroll
-  for (int k = 0; k < J; ++k) {
-    g[k] = CT<CR>::make(red[2 * k], red[2 * k + 1]);
-    sc->G[k][J] = g[k];
-  }
+  for (int k = 0; k < J; ++k) g[k] = CT<CR>::make(red[2 * k], red[2 * k + 1]);
   const T gg = red[2 * J];
-  sc->G[J][J] = CT<CR>::make(gg, 0);
   CR h[J + 1];
   T hs = 0;
 #pragma unroll
   for (int i = 1; i <= J; ++i) {
     CR acc = CT<CR>::make(0, 0);
 #pragma unroll
-    for (int k = 0; k < i; ++k) acc = cadd(acc, cmul(fconj(sc->Cf[i][k]), g[k]));
+    for (int k = 0; k < i; ++k) acc = cadd(acc, cmul(fconj(cf[i][k]), g[k]));
     h[i] = acc;
-    sc->Hh[i - 1][J - 1] = acc;
+    hh[i - 1][J - 1] = acc;
     hs += fabs2(acc);
   }
   if (!isfinite(gg) || !isfinite(hs)) sc->status = 1;
   const T w2 = gg - hs;
   const T hn = w2 > (T)0 ? sqrt(w2) : (T)0;
-  sc->Hh[J][J - 1] = CT<CR>::make(hn, 0);
+  hh[J][J - 1] = CT<CR>::make(hn, 0);
   const bool breakdown = !(w2 > SweepTau<T>::v * gg);
-  if (breakdown || J == sc->s) {
-    sweep_finish<T, J>(sc);
+  if (breakdown || J == s) {
+    sweep_finish<T, J>(sc, hh, cf, beta2);
   } else if (J < SMAX) {
     const T inv = (T)1 / hn;
+    CR cn[J + 1];
 #pragma unroll
     for (int k = 0; k < J; ++k) {
       CR acc = CT<CR>::make(0, 0);
 #pragma unroll
-      for (int i = k + 1; i <= J; ++i) acc = cadd(acc, cmul(h[i], sc->Cf[i][k]));
-      sc->Cf[J + 1][k] = CT<CR>::make(-acc.x * inv, -acc.y * inv);
+      for (int i = k + 1; i <= J; ++i) acc = cadd(acc, cmul(h[i], cf[i][k]));
+      cn[k] = CT<CR>::make(-acc.x * inv, -acc.y * inv);
     }
-    sc->Cf[J + 1][J] = CT<CR>::make(inv, 0);
+    cn[J] = CT<CR>::make(inv, 0);
+#pragma unroll
+    for (int i = 0; i <= J; ++i) sc->Hh[i][J - 1] = hh[i][J - 1];
+#pragma unroll
+    for (int k = 0; k <= J; ++k) sc->Cf[J + 1][k] = cn[k];
   }
 }
 
@@ -320,6 +360,52 @@ __device__ inline void sweep_after_pass_rt(SweepScalarsT<T>* sc, int J, const T*
     case 3: sweep_after_pass<T, 3>(sc, red); break;
     default: sweep_after_pass<T, 4>(sc, red); break;
   }
+}
+
+// End of an Arnoldi pass: publish this block's sums; the last block of the problem
+// loads the sweep state and all partial sums with their loads in flight together,
+// runs the algebra on one thread in shared memory and writes the state back.  Every
+// thread of the block must call it.
+template <typename T, int J>
+__device__ inline void grid_sum_sweep(T (&v)[2 * J + 1], void* partv, int tile, int ntiles,
+                                      SweepScalarsT<T>* sc, T* sm) {
+  constexpr int NV = 2 * J + 1;
+  constexpr int WPT = 2;  // sweep-state words per thread (the state is < 2 x 256 words)
+  __shared__ int s_last;
+  __shared__ SweepScalarsT<T> ls;
+  __shared__ T stot[NV];
+  T* part = reinterpret_cast<T*>(partv);
+  block_sum<NV, T>(v, sm);
+  const int tid = flat_tid(), nt = block_threads();
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) part[(size_t)tile * NPART + i] = v[i];
+    __threadfence();
+    s_last = (atomicAdd(&sc->counter, 1u) == (unsigned)ntiles - 1u);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  int* gsrc = reinterpret_cast<int*>(sc);
+  int* sdst = reinterpret_cast<int*>(&ls);
+  const int words = sweep_words<T>();
+  int w[WPT];
+#pragma unroll
+  for (int q = 0; q < WPT; ++q) w[q] = tid + q * nt < words ? __ldcg(gsrc + tid + q * nt) : 0;
+  T acc[NV];
+  sum_partials<NV, T>(part, ntiles, acc);
+#pragma unroll
+  for (int q = 0; q < WPT; ++q)
+    if (tid + q * nt < words) sdst[tid + q * nt] = w[q];
+  block_sum<NV, T>(acc, sm);
+  if (tid == 0) {
+    sc->counter = 0u;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) stot[i] = acc[i];
+    sweep_after_pass<T, J>(&ls, stot);
+  }
+  __syncthreads();
+  for (int i = tid; i < words; i += nt) gsrc[i] = sdst[i];
 }
 
 // The last CTA of a pass: stage the sweep state in shared memory with one

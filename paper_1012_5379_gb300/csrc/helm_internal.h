@@ -41,7 +41,6 @@ struct SweepScalarsT {
   R beta2;                        // ||R_0||^2
   int m;                          // Krylov steps of this sweep (0: nothing to do)
   int s;                          // requested steps
-  CR G[SMAX + 1][SMAX + 1];       // G[k][j] = <R_k, R_j>, k <= j
   CR Cf[SMAX + 1][SMAX + 1];      // Arnoldi vectors over raw vectors
   CR Hh[SMAX + 1][SMAX];          // Hessenberg matrix of the sweep
   CR xcoef[SMAX + 1];             // x_new = x_old + sum_k xcoef[k] R_k

@@ -121,8 +121,8 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_i
   for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
   red[2 * J] = accn;
   pdl_trigger();  // the main work is done: let the next pass launch
-  if (grid_sum_last<2 * J + 1>(red, L.part, unit, nunits, &sc->counter, sm, tot))
-    block_sweep_after_pass<R, J>(sc, tot);
+  (void)tot;
+  grid_sum_sweep<R, J>(red, L.part, unit, nunits, sc, sm);
 }
 
 template <typename C, int J>
@@ -203,8 +203,8 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
   for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
   red[2 * J] = accn;
   pdl_trigger();  // the main work is done: let the next pass launch
-  if (grid_sum_last<2 * J + 1>(red, L.part, tile, ntiles, &sc->counter, sm, tot))
-    block_sweep_after_pass<R, J>(sc, tot);
+  (void)tot;
+  grid_sum_sweep<R, J>(red, L.part, tile, ntiles, sc, sm);
 }
 
 // ------------------------------------------------------------------ end of pre-smoothing
