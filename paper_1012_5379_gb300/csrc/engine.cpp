@@ -163,6 +163,18 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     CUDA_TRY(cudaMemsetAsync(L.sc, 0, scb, st));
     const size_t nparts = std::max<size_t>(std::max(L.ntiles, L.nflat), 1);
     TRY(dev_alloc(h.get(), &L.part, nparts * NPART * sizeof(double)));
+    // TMA maps of the raw vectors the 2D complex64 Arnoldi pass streams
+    if (h->dim == 2 && h->prec == HELM_C64 && L.P >= 64) {
+      std::vector<CUtensorMap> maps(TM_COUNT);
+      const void* vecs[TM_COUNT] = {L.b, L.r0, nullptr, nullptr, nullptr, nullptr};
+      for (int j = 0; j < h->s; ++j) vecs[TM_P0 + j] = L.p[j];
+      if (encode_level_tmaps(L.P, vecs, TM_COUNT, maps.data())) {
+        CUtensorMap* dtm = nullptr;
+        TRY(dev_alloc(h.get(), &dtm, TM_COUNT * sizeof(CUtensorMap)));
+        CUDA_TRY(cudaMemcpyAsync(dtm, maps.data(), TM_COUNT * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+        L.tm = dtm;
+      }
+    }
     // coefficients of M on this level (rediscretisation with spacing 2^l h)
     TRY(dev_alloc(h.get(), &L.coef64, 3 * L.n * sizeof(double2)));
     TRY(dev_alloc(h.get(), &L.coef, 3 * L.n * eb));
@@ -248,6 +260,7 @@ static LevelDev<C> make_leveldev(const Handle& h, int l) {
   typedef SweepScalarsT<typename RealOf<C>::T> SS;
   d.sc = (SS*)L.sc;
   d.part = L.part;
+  d.tm = L.tm;
   if (l + 1 < (int)h.lev.size()) {
     const HostLevel& Lc = h.lev[l + 1];
     d.nc = Lc.n;
@@ -298,7 +311,12 @@ struct Group {
   int dim = 2, nu1 = 1, nu2 = 1, s = 3, Lmax = 0, tc = 0, nprob = 0;
   TileCfg cfg{8};
   std::vector<Handle*> hs;
-  struct Depth { int n = 0, cnt = 0, ntiles = 0, nflat = 0; TileCfg cfg{8}; LevelDev<C>* d = nullptr; };
+  struct Depth {
+    int n = 0, cnt = 0, ntiles = 0, nflat = 0;
+    bool tma = true;  // every problem at this depth has TMA maps
+    TileCfg cfg{8};
+    LevelDev<C>* d = nullptr;
+  };
   std::vector<Depth> depth;      // t < tc
   LevelDev<C>* dcoarse = nullptr;  // [prob][Lmax - tc]
   int nlev_c = 0;
@@ -407,6 +425,7 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
       if (D.cnt > 0 && D.n != L.n) { set_error("batched problems must have n + 1 a power of two"); return HELM_EINVAL; }
       D.n = L.n;
       D.cnt += 1;
+      D.tma = D.tma && L.tm != nullptr;
       D.ntiles = L.ntiles;
       D.nflat = L.nflat;
       D.cfg.rows = zchunk(L.P);
@@ -514,7 +533,7 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
     for (int sw = 0; sw < g.nu1; ++sw) {
       for (int J = 1; J <= g.s; ++J) {
         Launch L(fine ? "vc.arnoldi.l0" : "vc.arnoldi.lc", st, pts * (E * (J + 1) + ph), pts * (8.0 * (2 * dim + 1) + 8.0 * J + 4));
-        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, true, st);
+        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, true, D.tma, st);
       }
       if (sw < g.nu1 - 1) {
         Launch L(fine ? "vc.update.l0" : "vc.update.lc", st, pts * E * (g.s + 3.0 + (sw == 0 ? 0 : 1)), 0);
@@ -548,7 +567,7 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
         const bool store = J < g.s || !last;
         Launch L(fine ? "vc.arnoldi.l0" : "vc.arnoldi.lc", st, pts * (E * (J + (store ? 1 : 0)) + ph),
                  pts * (8.0 * (2 * dim + 1) + 8.0 * J + 4));
-        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, D.cfg, false, store, st);
+        launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, D.cfg, false, store, D.tma, st);
       }
       Launch L(fine ? "vc.update.l0" : "vc.update.lc", st, pts * E * (last ? g.s + 2.0 : g.s + 4.0), 0);
       launch_update_flat<C>(dim, last ? UPD_XONLY : UPD_RESIDUAL, D.d, D.cnt, D.nflat, false, 1, false, st);
@@ -883,6 +902,10 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
     cudaEventDestroy(ev);
   }
   TRY(rc);
+  if (vcycle_take_error()) {
+    set_error("a V-cycle kernel's wait for its tile copies ran out");
+    return HELM_ETIMEOUT;
+  }
   for (int k = 0; k < nsets; ++k)
     for (Handle* h : sets[k].members) {  // only on a failed guard: report what they have
       OuterState s;

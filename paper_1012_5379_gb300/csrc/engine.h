@@ -47,6 +47,7 @@ struct HostLevel {
   float* phi = nullptr;     // padded phi or nullptr
   double phic = 0.0;
   void* sc = nullptr;          // SweepScalarsT<R> of the preconditioner precision
+  const CUtensorMap* tm = nullptr;  // TMA maps (2D complex64 grid-wide levels), device memory
   double* part = nullptr;
 };
 

@@ -7,6 +7,7 @@
 // n = 2^L - 1, so rows are aligned.  Kernels bounds-check every neighbour load, so
 // nothing outside [0, P^d) is ever touched.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -75,7 +76,11 @@ struct LevelDev {
   SweepScalarsT<typename RealOf<C>::T>* sc;   // this level's sweep state
   SweepScalarsT<typename RealOf<C>::T>* scc;  // coarser level's sweep state
   double* part;           // partial sums: ntiles * NPART slots (R or double)
+  const CUtensorMap* tm;  // 2D complex64 levels: TMA maps of b, r0, p_1..p_SMAX (else nullptr)
 };
+
+// TMA maps per level: b, r0, p_1..p_SMAX (in this order).
+constexpr int TM_B = 0, TM_R0 = 1, TM_P0 = 2, TM_COUNT = 2 + SMAX;
 
 // Dense LU factors of the coarsest operator (FP64), row-major, with pivots.
 constexpr int MAX_COARSE_LEVELS_HOST = 8;  // levels the staged coarse kernels hold
@@ -166,7 +171,7 @@ enum UpdateMode { UPD_RESTRICT = 0, UPD_RESIDUAL = 1, UPD_XONLY = 2 };
 // V-cycle passes (vcycle_c64.cu / vcycle_c128.cu), C = float2 or double2.
 template <typename C>
 void launch_arnoldi(int dim, int J, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
-                    bool store_p, cudaStream_t st);
+                    bool store_p, bool tma, cudaStream_t st);
 template <typename C>
 void launch_restrict(int dim, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
                      bool x_from_zero, bool nosmooth, cudaStream_t st);
@@ -197,6 +202,12 @@ template <typename C>
 void outer_residual(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCfg cfg, cudaStream_t st);
 template <typename C>
 void outer_apply_h(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCfg cfg, cudaStream_t st);
+// TMA maps of a 2D complex64 level (tma.cpp): a 136 x 18 float box (64 x 16 complex
+// points plus halo) over a P x P complex field.  False when the driver has no
+// tensor-map encoder or the layout does not meet its rules.
+bool encode_level_tmaps(int P, const void* const* vectors, int count, CUtensorMap* out);
+// Sticky device error flag of the V-cycle kernels (a wait ran out): read and clear.
+int vcycle_take_error();
 int outer_chunks(size_t vs);
 size_t outer_part_doubles(int chunks, int m);
 template <typename C>

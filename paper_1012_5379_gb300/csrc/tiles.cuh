@@ -125,6 +125,123 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_i
   grid_sum_sweep<R, J>(red, L.part, unit, nunits, sc, sm);
 }
 
+// ------------------------------------------------------------------ Arnoldi step J, TMA (2D, complex64)
+// The same pass with the raw vectors streamed by the tensor memory accelerator: a
+// 136 x 18 float box per raw vector (the 64 x 16 tile plus halo, from x0 - 2 so that
+// the box starts on a 16-byte boundary; out-of-range rows and columns arrive as
+// zero, which is the boundary value) lands in shared memory, two stages deep: while
+// the CTA works on one tile, the next tile's boxes are in flight.  Every wait is
+// bounded; on a timeout the CTA records the error, waits (bounded) for its own copies
+// and returns.
+constexpr int TMA_BX = T2X + 4, TMA_BY = T2Y + 2;                        // box in complex points
+constexpr unsigned TMA_BOX_BYTES = TMA_BX * TMA_BY * 8;                    // 9792
+constexpr unsigned TMA_BOX_STRIDE = (TMA_BOX_BYTES + 127) / 128 * 128;     // 9856
+HELM_HD constexpr unsigned tma_arnoldi_smem(int J) { return 2u * J * TMA_BOX_STRIDE; }
+
+template <int J>
+__global__ void __launch_bounds__(256, J <= 2 ? 4 : 3)
+k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, int r0_is_b, int store_p) {
+  typedef float R;
+  typedef float2 C;
+  extern __shared__ __align__(128) unsigned char tsm[];
+  __shared__ C vt[T2Y + 2][T2X + 2];
+  __shared__ R sm[32 * (2 * J + 1)];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int nunits = ceil_div(ntiles, tpc);
+  const int prob = blockIdx.x / nunits, unit = blockIdx.x - prob * nunits;
+  const LevelDev<C>& L = levs[prob];
+  auto* sc = L.sc;
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  pdl_wait();
+  if (sc->m < J) return;  // earlier breakdown or empty sweep: uniform for the problem
+  const int n = L.n, P = L.P;
+  const int ntx = ceil_div(P, T2X);
+  const CUtensorMap* tm[J];
+  C cf[J];
+#pragma unroll
+  for (int k = 0; k < J; ++k) {
+    tm[k] = L.tm + (k == 0 ? (r0_is_b ? TM_B : TM_R0) : TM_P0 + k - 1);
+    cf[k] = sc->Cf[J][k];
+  }
+  if (tid == 0)
+#pragma unroll
+    for (int k = 0; k < J; ++k) tmap_acquire(tm[k]);
+  __syncthreads();  // initialised barriers
+  const int t_beg = unit * tpc, t_end = min(ntiles, (unit + 1) * tpc);
+  auto issue = [&](int t, int stage) {
+    const int x0 = (t % ntx) * T2X, y0 = (t / ntx) * T2Y;
+    mbar_expect_tx(&bar[stage], J * TMA_BOX_BYTES);
+#pragma unroll
+    for (int k = 0; k < J; ++k)
+      tma_load_2d(tsm + (stage * J + k) * TMA_BOX_STRIDE, tm[k], 2 * (x0 - 2), y0 - 1, &bar[stage]);
+  };
+  if (tid == 0 && t_beg < t_end) issue(t_beg, 0);
+  C acc[J];
+#pragma unroll
+  for (int k = 0; k < J; ++k) acc[k] = czero<C>();
+  R accn = 0;
+  bool ok = true;
+  int it = 0;
+#pragma unroll 1
+  for (int tile = t_beg; tile < t_end; ++tile, ++it) {
+    const int stage = it & 1;
+    if (tid == 0 && tile + 1 < t_end) issue(tile + 1, stage ^ 1);  // that stage was released at the end of it - 1
+    const bool mine = mbar_wait(&bar[stage], (unsigned)((it >> 1) & 1));
+    if (!__syncthreads_and(mine)) { ok = false; break; }
+    const C* box[J];
+#pragma unroll
+    for (int k = 0; k < J; ++k) box[k] = reinterpret_cast<const C*>(tsm + (stage * J + k) * TMA_BOX_STRIDE);
+    // v_J on the tile plus halo: vt[r][c] is the point (x0 - 1 + c, y0 - 1 + r), box column c + 1
+    for (int q = tid; q < (T2Y + 2) * (T2X + 2); q += 256) {
+      const int r = q / (T2X + 2), c = q - r * (T2X + 2);
+      C v = czero<C>();
+#pragma unroll
+      for (int k = 0; k < J; ++k) v = cfma(cf[k], box[k][r * TMA_BX + c + 1], v);
+      vt[r][c] = v;
+    }
+    __syncthreads();
+    const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
+    const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+      const int x = x0 + ox, y = y0 + oy;
+      C p = czero<C>();
+      if (x < n && y < n) {
+        const Coef3<C> cy = ldcoef(L, y);
+        p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
+                     vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
+#pragma unroll
+        for (int k = 0; k < J; ++k) acc[k] = cdotacc(box[k][(oy + 1) * TMA_BX + ox + 2], p, acc[k]);
+        accn += cabs2(p);
+      }
+      if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, 0, P)] = p;
+    }
+    __syncthreads();  // vt and this stage are free for reuse
+  }
+  if (!ok) {
+    if (tid == 0) {
+      atomicExch(&g_vcycle_error, 1);
+      // the copies of this CTA that may still be landing (bounded)
+      mbar_wait(&bar[it & 1], (unsigned)((it >> 1) & 1));
+      if (t_beg + it + 1 < t_end) mbar_wait(&bar[(it + 1) & 1], (unsigned)(((it + 1) >> 1) & 1));
+    }
+    __syncthreads();
+    return;
+  }
+  R red[2 * J + 1];
+#pragma unroll
+  for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
+  red[2 * J] = accn;
+  pdl_trigger();  // the main work is done: let the next pass launch
+  grid_sum_sweep<R, J>(red, L.part, unit, nunits, sc, sm);
+}
+
 template <typename C, int J>
 __global__ void __launch_bounds__(256)
 k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is_b, int store_p) {

@@ -3,6 +3,7 @@
 #pragma once
 #include "tiles.cuh"
 #include <algorithm>
+#include <type_traits>
 #include "../../include/helm.h"
 
 namespace helm {
@@ -45,12 +46,13 @@ static inline void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 // (1/2 + t) tile times; the smallest such t up to 8 wins.  A function of the level size and of the kernel's
 // residency on the device only (it fixes the order of the pass's partial sums).
 template <typename K>
-static int tiles_per_cta(K kernel, int ntiles) {
+static int tiles_per_cta(K kernel, int ntiles, size_t smem = 0) {
   static thread_local K last_kernel = nullptr;
   static thread_local int slots = 0;
   if (kernel != last_kernel) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
     slots = per_sm * sm_count();
     last_kernel = kernel;
   }
@@ -64,9 +66,33 @@ static int tiles_per_cta(K kernel, int ntiles) {
   return best;
 }
 
+constexpr int TMA_MIN_TILES = 16384;  // 2D levels of 4095^2 and larger
+
+template <int J>
+static void arnoldi_tma2(const LevelDev<float2>* levs, int nprob, int ntiles, bool r0_is_b, bool store_p,
+                         cudaStream_t st) {
+  const size_t smem = tma_arnoldi_smem(J);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_arnoldi_tma2<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  const int t = tiles_per_cta(k_arnoldi_tma2<J>, ntiles, smem);
+  pdl_launch(k_arnoldi_tma2<J>, dim3(nprob * ceil_div(ntiles, t)), dim3(32, 8), smem, st, levs, ntiles, t,
+             r0_is_b ? 1 : 0, store_p ? 1 : 0);
+}
+
 template <typename C, int J>
 static void arnoldi_J(int dim, const LevelDev<C>* levs, int grid, int ntiles, TileCfg cfg, bool r0_is_b,
-                      bool store_p, cudaStream_t st) {
+                      bool store_p, bool tma, cudaStream_t st) {
+  if constexpr (std::is_same<C, float2>::value) {
+    // the TMA pipeline pays off on levels that stream from HBM; smaller levels are
+    // latency-bound and L2-resident
+    if (dim == 2 && tma && ntiles >= TMA_MIN_TILES) {
+      arnoldi_tma2<J>(levs, grid / ntiles, ntiles, r0_is_b, store_p, st);
+      return;
+    }
+  }
   if (dim == 2) {
     const int t = tiles_per_cta(k_arnoldi_t2<C, J>, ntiles);
     pdl_launch(k_arnoldi_t2<C, J>, dim3(grid / ntiles * ceil_div(ntiles, t)), dim3(dim3(32, 8)), 0, st, levs, ntiles, t,
@@ -78,13 +104,13 @@ static void arnoldi_J(int dim, const LevelDev<C>* levs, int grid, int ntiles, Ti
 
 template <typename C>
 void launch_arnoldi(int dim, int J, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
-                    bool store_p, cudaStream_t st) {
+                    bool store_p, bool tma, cudaStream_t st) {
   const int grid = nprob * ntiles;
   switch (J) {
-    case 1: arnoldi_J<C, 1>(dim, levs, grid, ntiles, cfg, r0_is_b, store_p, st); break;
-    case 2: arnoldi_J<C, 2>(dim, levs, grid, ntiles, cfg, r0_is_b, store_p, st); break;
-    case 3: arnoldi_J<C, 3>(dim, levs, grid, ntiles, cfg, r0_is_b, store_p, st); break;
-    default: arnoldi_J<C, 4>(dim, levs, grid, ntiles, cfg, r0_is_b, store_p, st); break;
+    case 1: arnoldi_J<C, 1>(dim, levs, grid, ntiles, cfg, r0_is_b, store_p, tma, st); break;
+    case 2: arnoldi_J<C, 2>(dim, levs, grid, ntiles, cfg, r0_is_b, store_p, tma, st); break;
+    case 3: arnoldi_J<C, 3>(dim, levs, grid, ntiles, cfg, r0_is_b, store_p, tma, st); break;
+    default: arnoldi_J<C, 4>(dim, levs, grid, ntiles, cfg, r0_is_b, store_p, tma, st); break;
   }
 }
 
@@ -208,7 +234,7 @@ void launch_store_output(int dim, int n, const LevelDev<C>* levs, void* dst, int
 }
 
 #define HELM_VCYCLE_INST(C)                                                                                   \
-  template void launch_arnoldi<C>(int, int, const LevelDev<C>*, int, int, TileCfg, bool, bool, cudaStream_t); \
+  template void launch_arnoldi<C>(int, int, const LevelDev<C>*, int, int, TileCfg, bool, bool, bool, cudaStream_t); \
   template void launch_restrict<C>(int, const LevelDev<C>*, int, int, TileCfg, bool, bool, bool,           \
                                     cudaStream_t);                                                          \
   template void launch_update_flat<C>(int, UpdateMode, const LevelDev<C>*, int, int, bool, int, bool,         \
