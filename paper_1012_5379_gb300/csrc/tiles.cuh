@@ -129,14 +129,15 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_i
 // The same pass with the raw vectors streamed by the tensor memory accelerator: a
 // 136 x 18 float box per raw vector (the 64 x 16 tile plus halo, from x0 - 2 so that
 // the box starts on a 16-byte boundary; out-of-range rows and columns arrive as
-// zero, which is the boundary value) lands in shared memory, two stages deep: while
-// the CTA works on one tile, the next tile's boxes are in flight.  Every wait is
+// zero, which is the boundary value) lands in shared memory, TMA_STAGES deep: while
+// the CTA works on one tile, the next tiles' boxes are in flight.  Every wait is
 // bounded; on a timeout the CTA records the error, waits (bounded) for its own copies
 // and returns.
 constexpr int TMA_BX = T2X + 4, TMA_BY = T2Y + 2;                        // box in complex points
 constexpr unsigned TMA_BOX_BYTES = TMA_BX * TMA_BY * 8;                    // 9792
 constexpr unsigned TMA_BOX_STRIDE = (TMA_BOX_BYTES + 127) / 128 * 128;     // 9856
-HELM_HD constexpr unsigned tma_arnoldi_smem(int J) { return 2u * J * TMA_BOX_STRIDE; }
+constexpr int TMA_STAGES = 2;                                             // tiles in flight per CTA
+HELM_HD constexpr unsigned tma_arnoldi_smem(int J) { return (unsigned)TMA_STAGES * J * TMA_BOX_STRIDE; }
 
 template <int J>
 __global__ void __launch_bounds__(256, J <= 2 ? 4 : 3)
@@ -146,15 +147,15 @@ k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, i
   extern __shared__ __align__(128) unsigned char tsm[];
   __shared__ C vt[T2Y + 2][T2X + 2];
   __shared__ R sm[32 * (2 * J + 1)];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[TMA_STAGES];
   const int nunits = ceil_div(ntiles, tpc);
   const int prob = blockIdx.x / nunits, unit = blockIdx.x - prob * nunits;
   const LevelDev<C>& L = levs[prob];
   auto* sc = L.sc;
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+#pragma unroll
+    for (int q = 0; q < TMA_STAGES; ++q) mbar_init(&bar[q], 1);
     mbar_fence_init();
   }
   pdl_wait();
@@ -180,7 +181,8 @@ k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, i
     for (int k = 0; k < J; ++k)
       tma_load_2d(tsm + (stage * J + k) * TMA_BOX_STRIDE, tm[k], 2 * (x0 - 2), y0 - 1, &bar[stage]);
   };
-  if (tid == 0 && t_beg < t_end) issue(t_beg, 0);
+  if (tid == 0)
+    for (int q = 0; q < TMA_STAGES - 1 && t_beg + q < t_end; ++q) issue(t_beg + q, q);
   C acc[J];
 #pragma unroll
   for (int k = 0; k < J; ++k) acc[k] = czero<C>();
@@ -189,9 +191,11 @@ k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, i
   int it = 0;
 #pragma unroll 1
   for (int tile = t_beg; tile < t_end; ++tile, ++it) {
-    const int stage = it & 1;
-    if (tid == 0 && tile + 1 < t_end) issue(tile + 1, stage ^ 1);  // that stage was released at the end of it - 1
-    const bool mine = mbar_wait(&bar[stage], (unsigned)((it >> 1) & 1));
+    const int stage = it % TMA_STAGES;
+    // the stage of tile it + STAGES - 1 is the one tile it - 1 released at its end
+    if (tid == 0 && tile + TMA_STAGES - 1 < t_end)
+      issue(tile + TMA_STAGES - 1, (it + TMA_STAGES - 1) % TMA_STAGES);
+    const bool mine = mbar_wait(&bar[stage], (unsigned)((it / TMA_STAGES) & 1));
     if (!__syncthreads_and(mine)) { ok = false; break; }
     const C* box[J];
 #pragma unroll
@@ -228,8 +232,8 @@ k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, i
     if (tid == 0) {
       atomicExch(&g_vcycle_error, 1);
       // the copies of this CTA that may still be landing (bounded)
-      mbar_wait(&bar[it & 1], (unsigned)((it >> 1) & 1));
-      if (t_beg + it + 1 < t_end) mbar_wait(&bar[(it + 1) & 1], (unsigned)(((it + 1) >> 1) & 1));
+      for (int u = it; u < it + TMA_STAGES && t_beg + u < t_end; ++u)
+        mbar_wait(&bar[u % TMA_STAGES], (unsigned)((u / TMA_STAGES) & 1));
     }
     __syncthreads();
     return;

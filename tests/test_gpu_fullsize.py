@@ -2,7 +2,8 @@
 
 - One V-cycle on the 2D 1023^2 grid (k = 160, theta_beta 0.3, random source) against
   the oracle's V-cycle at every point: c64 within 5e-5, c128 within 1e-11 relative
-  (the tolerances of the smaller V-cycle tests).
+  (the tolerances of the smaller V-cycle tests); the same on 4095^2 (c64), whose
+  finest level takes the TMA-fed pass.
 - The four 1023^2 FGMRES solves of the benchmark step (theta_beta 0.1 / 0.2 / 0.3 /
   0.5, complex64 preconditioner, no restart, tol 1e-6): the true residual, recomputed
   with the oracle's H, meets the tolerance, and the iteration count stays within
@@ -53,6 +54,20 @@ def test_vcycle_1023_matches_oracle(helm, source, prec, tol):
     h.precond_apply(r, z)
     got = z.cpu().numpy().astype(np.complex128)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol
+
+
+def test_vcycle_4095_matches_oracle_c64(helm):
+    """The finest level of 4095^2 runs the TMA-fed Arnoldi pass."""
+    n, k = 4095, 0.156 * 4096
+    src = I.random_source(2, n, 1001)
+    levels = O.build_hierarchy(2, n, 0.3, k=k)
+    want = O.vcycle(levels, src, 1, 1, 3)
+    h = helm.Handle(2, n, 0.3, k=k, precision="c64", maxit=1)
+    r = torch.from_numpy(src).cuda().to(torch.complex64)
+    z = torch.empty_like(r)
+    h.precond_apply(r, z)
+    got = z.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 5e-5
 
 
 @pytest.mark.parametrize("tb", [0.1, 0.2, 0.3, 0.5])
