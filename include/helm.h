@@ -44,7 +44,8 @@ extern "C" {
 #define HELM_ENOMEM -2   /* device allocation failed or serving budget exceeded */
 #define HELM_ENOCONV -3  /* maxit reached before tol; x holds the last iterate */
 #define HELM_ENUMERIC -4 /* NaN/Inf in a residual norm */
-#define HELM_ETIMEOUT -5 /* a bounded wait ran out (serving poll) */
+#define HELM_ETIMEOUT -5 /* a bounded wait ran out (serving wait; a V-cycle kernel's wait for its
+                            tile copies, after which the handle's results are invalid) */
 #define HELM_ECUDA -6    /* CUDA runtime error */
 #define HELM_EAGAIN -7   /* serving: request not finished yet */
 
@@ -118,7 +119,7 @@ int helm_apply_operator(helm_handle* h, int which, const void* v, void* w, int p
  *   info: filled on return (may be NULL).
  * Blocks the calling thread until the solve finishes (it reads convergence flags
  * from the device each iteration).  Returns HELM_OK, HELM_ENOCONV (maxit reached,
- * x holds the last iterate), HELM_ENUMERIC, HELM_EINVAL or HELM_ECUDA. */
+ * x holds the last iterate), HELM_ENUMERIC, HELM_EINVAL, HELM_ETIMEOUT or HELM_ECUDA. */
 int helm_solve(helm_handle* h, const double* b, double* x, double tol, helm_info* info,
                void* stream);
 
