@@ -463,24 +463,4 @@ __device__ inline void grid_sum_sweep(T (&v)[2 * J + 1], void* partv, int tile, 
   for (int i = tid; i < words; i += nt) gsrc[i] = sdst[i];
 }
 
-// The last CTA of a pass: stage the sweep state in shared memory with one
-// cooperative copy, run the algebra on one thread, copy back.  Every thread of the
-// block must call it.
-template <typename T, int J>
-__device__ inline void block_sweep_after_pass(SweepScalarsT<T>* sc, const T* tot) {
-  __shared__ SweepScalarsT<T> ls;
-  __shared__ T stot[2 * SMAX + 1];
-  const int tid = flat_tid(), nt = block_threads();
-  int* gsrc = reinterpret_cast<int*>(sc);
-  int* sdst = reinterpret_cast<int*>(&ls);
-  const int words = sweep_words<T>();
-  for (int i = tid; i < words; i += nt) sdst[i] = __ldcg(gsrc + i);
-  if (tid == 0)
-    for (int i = 0; i <= 2 * J; ++i) stot[i] = tot[i];
-  __syncthreads();
-  if (tid == 0) sweep_after_pass<T, J>(&ls, stot);
-  __syncthreads();
-  for (int i = tid; i < words; i += nt) gsrc[i] = sdst[i];
-}
-
 }  // namespace helm

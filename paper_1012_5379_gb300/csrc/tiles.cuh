@@ -116,12 +116,11 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_i
     }
     __syncthreads();  // the next tile rewrites vt
   }
-  R red[2 * J + 1], tot[2 * J + 1];
+  R red[2 * J + 1];
 #pragma unroll
   for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
   red[2 * J] = accn;
   pdl_trigger();  // the main work is done: let the next pass launch
-  (void)tot;
   grid_sum_sweep<R, J>(red, L.part, unit, nunits, sc, sm);
 }
 
@@ -319,12 +318,11 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
       for (int k = 0; k < J; ++k) rawc[k] = rawn[k];
     }
   }
-  R red[2 * J + 1], tot[2 * J + 1];
+  R red[2 * J + 1];
 #pragma unroll
   for (int k = 0; k < J; ++k) { red[2 * k] = acc[k].x; red[2 * k + 1] = acc[k].y; }
   red[2 * J] = accn;
   pdl_trigger();  // the main work is done: let the next pass launch
-  (void)tot;
   grid_sum_sweep<R, J>(red, L.part, tile, ntiles, sc, sm);
 }
 
