@@ -60,8 +60,25 @@ template <typename C> __device__ __forceinline__ C czero() { return CT<C>::make(
 template <typename C> __device__ __forceinline__ C from_d(double2 v) {
   return CT<C>::make((typename CT<C>::R)v.x, (typename CT<C>::R)v.y);
 }
-__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+// binary32 -> binary64 widening (exact) on the integer pipes: the sign is kept, the
+// exponent re-biased by 1023 - 127 = 896 and the 23 fraction bits moved to the top of
+// the 52-bit field.  Zero, subnormals, infinities and NaNs take the converting
+// instruction, which on this part issues to the FP64 pipe (the bound of the outer
+// passes); normal numbers need none.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u >= 254u) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(widen(v.x), widen(v.y)); }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
+// Change of complex type (exact unless it narrows).
+template <typename Cout> __device__ __forceinline__ Cout to_c(float2 v);
+template <> __device__ __forceinline__ float2 to_c<float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ double2 to_c<double2>(float2 v) { return to_d(v); }
+template <typename Cout> __device__ __forceinline__ Cout to_c(double2 v) { return from_d<Cout>(v); }
 
 __device__ __forceinline__ double2 dconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double dabs2(double2 a) { return a.x * a.x + a.y * a.y; }

@@ -257,6 +257,7 @@ static LevelDev<C> make_leveldev(const Handle& h, int l) {
   d.cc = (const C*)L.coef + 2 * L.n;
   d.phi = L.phi;
   d.phic = L.phic;
+  d.phir = (typename RealOf<C>::T)L.phic;
   typedef SweepScalarsT<typename RealOf<C>::T> SS;
   d.sc = (SS*)L.sc;
   d.part = L.part;

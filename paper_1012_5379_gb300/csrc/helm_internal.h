@@ -69,10 +69,11 @@ struct LevelDev {
   C* bc;                  // coarser level's b (restriction target)
   const C* xcb;           // coarser level's output (prolongation source)
   const C* ca;            // 1D coefficients of u_{i-1}  (length n)
-  const C* cd;            // 1D coefficients of u_i
-  const C* cc;            // 1D coefficients of u_{i+1}
+  const C* cd;            // 1D coefficients of u_i      (= ca + n)
+  const C* cc;            // 1D coefficients of u_{i+1}  (= ca + 2n)
   const float* phi;       // phi field in padded layout, or nullptr
   double phic;            // constant phi when phi == nullptr
+  typename RealOf<C>::T phir;  // phic rounded to the level's precision (no conversion per point)
   SweepScalarsT<typename RealOf<C>::T>* sc;   // this level's sweep state
   SweepScalarsT<typename RealOf<C>::T>* scc;  // coarser level's sweep state
   double* part;           // partial sums: ntiles * NPART slots (R or double)

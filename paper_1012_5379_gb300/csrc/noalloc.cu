@@ -177,6 +177,7 @@ int run_noalloc(const helm_grid* grid, double k, double theta_beta, int nu1, int
     d.cc = cf + 2 * nl;
     d.phi = nullptr;
     d.phic = k * k;
+    d.phir = (typename RealOf<C>::T)d.phic;
     d.sc = (SS*)(base + o_sc) + l;
     d.part = (double*)(base + o_part);
     {

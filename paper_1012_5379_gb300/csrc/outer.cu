@@ -105,7 +105,7 @@ k_hstencil2(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
         if (x < n && y < n) {
           const HCoef cy = ldh(O.ca, O.cd, O.cc, y, n);
           double2 diag = cadd(cx.d, cy.d);
-          diag.x -= O.phi ? (double)__ldg(O.phi + pidx(x, y, 0, P)) : O.phic;
+          diag.x -= O.phi ? widen(__ldg(O.phi + pidx(x, y, 0, P))) : O.phic;
           double2 p = cmul(diag, v0);
           p = cfma(cx.a, vl, p);
           p = cfma(cx.c, vr, p);
@@ -176,7 +176,7 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
           if (inside(x, y, z, n)) {
             const HCoef cz = ldh(O.ca, O.cd, O.cc, z, n);
             double2 diag = cadd(cadd(cx.d, cy.d), cz.d);
-            diag.x -= O.phi ? (double)__ldg(O.phi + pidx(x, y, z, P)) : O.phic;
+            diag.x -= O.phi ? widen(__ldg(O.phi + pidx(x, y, z, P))) : O.phic;
             double2 p = cmul(diag, v0);
             p = cfma(cx.a, vl, p);
             p = cfma(cx.c, vr, p);

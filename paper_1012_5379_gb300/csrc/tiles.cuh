@@ -47,8 +47,9 @@ __device__ __forceinline__ C stencil5(const Coef3<C>& cx, const Coef3<C>& cy, ty
 }
 
 // ------------------------------------------------------------------ Arnoldi step J
+// Complex128 holds twice the registers per raw vector: two CTAs per SM.
 template <typename C, int J>
-__global__ void __launch_bounds__(256, J <= 2 ? 4 : 3)
+__global__ void __launch_bounds__(256, sizeof(C) == 16 ? 2 : (J <= 2 ? 4 : 3))
 k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_is_b, int store_p) {
   typedef typename CT<C>::R R;
   __shared__ C vt[T2Y + 2][T2X + 2];
@@ -62,6 +63,8 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_i
   const int n = L.n, P = L.P;
   const int ntx = ceil_div(P, T2X);
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  const StencilRegs<C> S(L);
+  C* const pJ = L.p[J - 1];
   const C* Rk[J];
   C cf[J];
 #pragma unroll
@@ -98,21 +101,22 @@ k_arnoldi_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_i
       vt[hy + 1][hx + 1] = v;
     }
     __syncthreads();
-    const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+    const Coef3<C> cx0 = S.coef(x0 + lx), cx1 = S.coef(x0 + lx + 32);
+    Coef3<C> cy;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
       const int x = x0 + ox, y = y0 + oy;
+      if ((q & 1) == 0) cy = S.coef(y);  // one row per pair of points
       C p = czero<C>();
       if (x < n && y < n) {
-        const Coef3<C> cy = ldcoef(L, y);
-        p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
+        p = stencil5((q & 1) ? cx1 : cx0, cy, S.phi_at(x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
                      vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
 #pragma unroll
         for (int k = 0; k < J; ++k) acc[k] = cdotacc(raw[q][k], p, acc[k]);
         accn += cabs2(p);
       }
-      if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, 0, P)] = p;
+      if (store_p && x < P && y < P) pJ[pidx(x, y, 0, P)] = p;
     }
     __syncthreads();  // the next tile rewrites vt
   }
@@ -161,6 +165,8 @@ k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, i
   if (sc->m < J) return;  // earlier breakdown or empty sweep: uniform for the problem
   const int n = L.n, P = L.P;
   const int ntx = ceil_div(P, T2X);
+  const StencilRegs<C> S(L);
+  C* const pJ = L.p[J - 1];
   const CUtensorMap* tm[J];
   C cf[J];
 #pragma unroll
@@ -209,21 +215,22 @@ k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, i
     }
     __syncthreads();
     const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
-    const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+    const Coef3<C> cx0 = S.coef(x0 + lx), cx1 = S.coef(x0 + lx + 32);
+    Coef3<C> cy;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
       const int x = x0 + ox, y = y0 + oy;
+      if ((q & 1) == 0) cy = S.coef(y);  // one row per pair of points
       C p = czero<C>();
       if (x < n && y < n) {
-        const Coef3<C> cy = ldcoef(L, y);
-        p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
+        p = stencil5((q & 1) ? cx1 : cx0, cy, S.phi_at(x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
                      vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
 #pragma unroll
         for (int k = 0; k < J; ++k) acc[k] = cdotacc(box[k][(oy + 1) * TMA_BX + ox + 2], p, acc[k]);
         accn += cabs2(p);
       }
-      if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, 0, P)] = p;
+      if (store_p && x < P && y < P) pJ[pidx(x, y, 0, P)] = p;
     }
     __syncthreads();  // vt and this stage are free for reuse
   }
@@ -288,7 +295,9 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
       vb[z & 3][hy + 1][hx + 1] = w;
     }
   };
-  const Coef3<C> cx = ldcoef(L, x), cy = ldcoef(L, y);
+  const StencilRegs<C> S(L);
+  C* const pJ = L.p[J - 1];
+  const Coef3<C> cx = S.coef(x), cy = S.coef(y);
   C acc[J];
 #pragma unroll
   for (int k = 0; k < J; ++k) acc[k] = czero<C>();
@@ -303,8 +312,8 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
       const int s0 = z & 3;
       C p = czero<C>();
       if (inside(x, y, z, n)) {
-        const Coef3<C> cz = ldcoef(L, z);
-        p = stencil5(cx, cy, phi_at(L, x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
+        const Coef3<C> cz = S.coef(z);
+        p = stencil5(cx, cy, S.phi_at(x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
                      vb[s0][ly][lx + 1], vb[s0][ly + 2][lx + 1]);
         p = cfma(cz.d, vb[s0][ly + 1][lx + 1], p);
         p = cfma(cz.a, vb[(z - 1) & 3][ly + 1][lx + 1], p);
@@ -313,7 +322,7 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
         for (int k = 0; k < J; ++k) acc[k] = cdotacc(rawc[k], p, acc[k]);
         accn += cabs2(p);
       }
-      if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, z, P)] = p;
+      if (store_p && x < P && y < P) pJ[pidx(x, y, z, P)] = p;
 #pragma unroll
       for (int k = 0; k < J; ++k) rawc[k] = rawn[k];
     }
@@ -347,6 +356,8 @@ k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
   UpdCoef<C> u = load_upd(L, r0_is_b);
   if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
+  C* const xa = L.xa;
+  C* const bc = L.bc;
   R acc = 0;
   const int t_end = min(ntiles, (unit + 1) * tpc);
 #pragma unroll 1
@@ -360,7 +371,7 @@ k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_
       upd_point(u, x, y, 0, n, P, dx, r);
       if (x < P && y < P) {
         const size_t id = pidx(x, y, 0, P);
-        L.xa[id] = (x < n && y < n) ? cadd(x_from_zero ? czero<C>() : L.xa[id], dx) : czero<C>();
+        xa[id] = (x < n && y < n) ? cadd(x_from_zero ? czero<C>() : xa[id], dx) : czero<C>();
       }
       rt[oy][ox] = r;
     }
@@ -382,7 +393,7 @@ k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_
     const int Ix = x0 / 2 + lx, Iy = y0 / 2 + ly;
     if (Ix < Pc && Iy < Pc) {
       const bool valid = Ix < nc && Iy < nc;
-      L.bc[pidx(Ix, Iy, 0, Pc)] = valid ? out : czero<C>();
+      bc[pidx(Ix, Iy, 0, Pc)] = valid ? out : czero<C>();
       if (valid) acc += cabs2(out);
     }
     __syncthreads();  // the next tile rewrites rt
@@ -411,6 +422,8 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
   const int x = x0 + lx, y = y0 + ly;
   UpdCoef<C> u = load_upd(L, r0_is_b);
   if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
+  C* const xa = L.xa;
+  C* const bc = L.bc;
   const bool halo = tid < T3X + 1 + T3Y;
   const int hx = tid < T3X + 1 ? tid : T3X;
   const int hy = tid < T3X + 1 ? T3Y : tid - (T3X + 1);
@@ -423,7 +436,7 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
       upd_point(u, x, y, z, n, P, dx, r);
       if (z < zend && x < P && y < P) {
         const size_t id = pidx(x, y, z, P);
-        L.xa[id] = inside(x, y, z, n) ? cadd(x_from_zero ? czero<C>() : L.xa[id], dx) : czero<C>();
+        xa[id] = inside(x, y, z, n) ? cadd(x_from_zero ? czero<C>() : xa[id], dx) : czero<C>();
       }
       rb[z & 3][ly][lx] = r;
       if (halo) {
@@ -447,7 +460,7 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
         const int Ix = x0 / 2 + cx, Iy = y0 / 2 + cy, Iz = z / 2 - 1;
         if (Ix < Pc && Iy < Pc && Iz < Pc) {
           const bool valid = Ix < nc && Iy < nc && Iz < nc;
-          L.bc[pidx(Ix, Iy, Iz, Pc)] = valid ? out : czero<C>();
+          bc[pidx(Ix, Iy, Iz, Pc)] = valid ? out : czero<C>();
           if (valid) acc += cabs2(out);
         }
       }
@@ -475,8 +488,15 @@ k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc) {
   pdl_wait();
   const int ntx = ceil_div(P, T2X);
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  const StencilRegs<C> S(L);
+  const C* const xa = L.xa;
+  const C* const xcb = L.xcb;
+  const C* const bv = L.b;
+  C* const xb = L.xb;
+  C* const r0 = L.r0;
+  const int nc = L.nc, Pc = L.Pc;
   auto form = [&](int xx, int yy) -> C {
-    return cadd(ldc((const C*)L.xa, xx, yy, 0, n, P), interp(L, xx, yy, 0, 2));
+    return cadd(ldc(xa, xx, yy, 0, n, P), interp(xcb, n, nc, Pc, xx, yy, 0, 2));
   };
   R acc = 0;
   const int t_end = min(ntiles, (unit + 1) * tpc);
@@ -494,23 +514,24 @@ k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc) {
       vt[hy + 1][hx + 1] = form(x0 + hx, y0 + hy);
     }
     __syncthreads();
-    const Coef3<C> cx0 = ldcoef(L, x0 + lx), cx1 = ldcoef(L, x0 + lx + 32);
+    const Coef3<C> cx0 = S.coef(x0 + lx), cx1 = S.coef(x0 + lx + 32);
+    Coef3<C> cy;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
       const int x = x0 + ox, y = y0 + oy;
+      if ((q & 1) == 0) cy = S.coef(y);  // one row per pair of points
       if (x < P && y < P) {
         C r = czero<C>(), xo = czero<C>();
         if (x < n && y < n) {
-          const Coef3<C> cy = ldcoef(L, y);
-          const C p = stencil5((q & 1) ? cx1 : cx0, cy, phi_at(L, x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
+          const C p = stencil5((q & 1) ? cx1 : cx0, cy, S.phi_at(x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
                                vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
-          r = csub(__ldg(L.b + pidx(x, y, 0, P)), p);
+          r = csub(__ldg(bv + pidx(x, y, 0, P)), p);
           xo = vt[oy + 1][ox + 1];
           acc += cabs2(r);
         }
-        L.xb[pidx(x, y, 0, P)] = xo;
-        L.r0[pidx(x, y, 0, P)] = r;
+        xb[pidx(x, y, 0, P)] = xo;
+        r0[pidx(x, y, 0, P)] = r;
       }
     }
     __syncthreads();  // the next tile rewrites vt
@@ -540,14 +561,21 @@ k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
   const bool halo = tid < HALO3;
   int hx = 0, hy = 0;
   if (halo) halo_coord<T3X, T3Y>(tid, hx, hy);
+  const StencilRegs<C> S(L);
+  const C* const xa = L.xa;
+  const C* const xcb = L.xcb;
+  const C* const bv = L.b;
+  C* const xb = L.xb;
+  C* const r0 = L.r0;
+  const int nc = L.nc, Pc = L.Pc;
   auto form = [&](int xx, int yy, int zz) -> C {
-    return cadd(ldc((const C*)L.xa, xx, yy, zz, n, P), interp(L, xx, yy, zz, 3));
+    return cadd(ldc(xa, xx, yy, zz, n, P), interp(xcb, n, nc, Pc, xx, yy, zz, 3));
   };
   auto load_plane = [&](int z) {
     vb[z & 3][ly + 1][lx + 1] = form(x, y, z);
     if (halo) vb[z & 3][hy + 1][hx + 1] = form(x0 + hx, y0 + hy, z);
   };
-  const Coef3<C> cx = ldcoef(L, x), cy = ldcoef(L, y);
+  const Coef3<C> cx = S.coef(x), cy = S.coef(y);
   R acc = 0;
   if (zbeg < P) {
     load_plane(zbeg - 1);
@@ -559,18 +587,18 @@ k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
       if (x < P && y < P) {
         C r = czero<C>(), xo = czero<C>();
         if (inside(x, y, z, n)) {
-          const Coef3<C> cz = ldcoef(L, z);
-          C p = stencil5(cx, cy, phi_at(L, x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
+          const Coef3<C> cz = S.coef(z);
+          C p = stencil5(cx, cy, S.phi_at(x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
                          vb[s0][ly][lx + 1], vb[s0][ly + 2][lx + 1]);
           p = cfma(cz.d, vb[s0][ly + 1][lx + 1], p);
           p = cfma(cz.a, vb[(z - 1) & 3][ly + 1][lx + 1], p);
           p = cfma(cz.c, vb[(z + 1) & 3][ly + 1][lx + 1], p);
-          r = csub(__ldg(L.b + pidx(x, y, z, P)), p);
+          r = csub(__ldg(bv + pidx(x, y, z, P)), p);
           xo = vb[s0][ly + 1][lx + 1];
           acc += cabs2(r);
         }
-        L.xb[pidx(x, y, z, P)] = xo;
-        L.r0[pidx(x, y, z, P)] = r;
+        xb[pidx(x, y, z, P)] = xo;
+        r0[pidx(x, y, z, P)] = r;
       }
     }
   }

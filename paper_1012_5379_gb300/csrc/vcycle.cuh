@@ -40,17 +40,46 @@ __device__ __forceinline__ Coef3<C> ldcoef(const LevelDev<C>& L, int i) {
 template <typename C>
 __device__ __forceinline__ typename CT<C>::R phi_at(const LevelDev<C>& L, int x, int y, int z) {
   typedef typename CT<C>::R R;
-  return L.phi ? (R)__ldg(L.phi + pidx(x, y, z, L.P)) : (R)L.phic;
+  return L.phi ? (R)__ldg(L.phi + pidx(x, y, z, L.P)) : L.phir;
 }
+
+// What a tile loop's stencil reads of its level, copied once into registers: the 1D
+// coefficients (one array of 3n: a, then d, then c), the phi field or its constant,
+// and the sizes.  (Read through the descriptor, these fields are fetched again for
+// every point.)
+template <typename C>
+struct StencilRegs {
+  typedef typename CT<C>::R R;
+  const C* coef3;
+  const float* phi;
+  R phic;
+  int n, P;
+  __device__ __forceinline__ explicit StencilRegs(const LevelDev<C>& L)
+      : coef3(L.ca), phi(L.phi), phic(L.phir), n(L.n), P(L.P) {}
+  __device__ __forceinline__ Coef3<C> coef(int i) const {
+    Coef3<C> r;
+    if ((unsigned)i < (unsigned)n) {
+      r.a = __ldg(coef3 + i);
+      r.d = __ldg(coef3 + n + i);
+      r.c = __ldg(coef3 + 2 * n + i);
+    } else {
+      r.a = r.d = r.c = czero<C>();
+    }
+    return r;
+  }
+  __device__ __forceinline__ R phi_at(int x, int y, int z) const {
+    return phi ? (R)__ldg(phi + pidx(x, y, z, P)) : phic;
+  }
+};
 
 // ------------------------------------------------------------------ prolongation
 // Vertex-centred bi/trilinear interpolation of the coarser output at fine node i:
 // odd i -> coarse (i-1)/2 with weight 1; even i -> coarse i/2-1 and i/2 with 1/2.
 template <typename C, bool NC = true>
-__device__ __forceinline__ C interp(const LevelDev<C>& L, int x, int y, int z, int dim) {
+__device__ __forceinline__ C interp(const C* xcb, int n, int nc, int Pc, int x, int y, int z, int dim) {
   typedef typename CT<C>::R R;
   C acc = czero<C>();
-  if (!inside(x, y, z, L.n)) return acc;
+  if (!inside(x, y, z, n)) return acc;
   int ix[2], iy[2], iz[2];
   R wx, wy, wz;
   int nx, ny, nz;
@@ -62,8 +91,12 @@ __device__ __forceinline__ C interp(const LevelDev<C>& L, int x, int y, int z, i
   const R w = wx * wy * wz;
   for (int c = 0; c < nz; ++c)
     for (int b = 0; b < ny; ++b)
-      for (int a = 0; a < nx; ++a) acc = cadd(acc, ldc<C, NC>(L.xcb, ix[a], iy[b], iz[c], L.nc, L.Pc));
+      for (int a = 0; a < nx; ++a) acc = cadd(acc, ldc<C, NC>(xcb, ix[a], iy[b], iz[c], nc, Pc));
   return cscale(acc, w);
+}
+template <typename C, bool NC = true>
+__device__ __forceinline__ C interp(const LevelDev<C>& L, int x, int y, int z, int dim) {
+  return interp<C, NC>(L.xcb, L.n, L.nc, L.Pc, x, y, z, dim);
 }
 
 // ------------------------------------------------------------------ sweep end
@@ -179,7 +212,7 @@ k_load_input(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, const Ci
     const int y = (int)((i / P) % P);
     const int z = dim == 3 ? (int)(i / ((size_t)P * P)) : 0;
     C v = czero<C>();
-    if (inside(x, y, z, n)) v = from_d<C>(to_d(src[((size_t)z * n + y) * n + x]));
+    if (inside(x, y, z, n)) v = to_c<C>(src[((size_t)z * n + y) * n + x]);
     L.b[i] = v;
     acc += cabs2(v);
   }
@@ -203,7 +236,7 @@ k_store_output(const LevelDev<C>* __restrict__ levs, int dim, Cout* __restrict__
     const int x = (int)(i % n);
     const int y = (int)((i / n) % n);
     const int z = dim == 3 ? (int)(i / ((size_t)n * n)) : 0;
-    dst[i] = from_d<Cout>(to_d(L.xb[pidx(x, y, z, P)]));
+    dst[i] = to_c<Cout>(L.xb[pidx(x, y, z, P)]);
   }
 }
 
