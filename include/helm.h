@@ -77,6 +77,9 @@ typedef struct {
   int restart;      /* outer FGMRES restart length m, 0 = none       [0] */
   int maxit;        /* max preconditioner applications per solve     [400] */
 } helm_opts;
+/* The Krylov basis length m = min(restart, maxit) (maxit without restart) is at most
+ * HELM_MAX_BASIS; helm_setup returns HELM_EINVAL above it. */
+#define HELM_MAX_BASIS 1536
 
 typedef struct {
   int iters;           /* preconditioner applications (outer iterations) */

@@ -138,6 +138,10 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     return HELM_EINVAL;
   }
   h->m = h->restart > 0 ? std::min(h->restart, h->maxit) : h->maxit;
+  if (h->m > HELM_MAX_BASIS) {
+    set_error("Krylov basis length min(restart, maxit) exceeds HELM_MAX_BASIS");
+    return HELM_EINVAL;
+  }
   const size_t eb = elem_bytes(h->prec);
 
   // ------------------------------------------------ levels

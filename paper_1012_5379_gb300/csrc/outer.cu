@@ -371,20 +371,24 @@ size_t outer_part_doubles(int chunks, int m) {
 }
 
 // ------------------------------------------------------------------ new Arnoldi vector
-// Givens update of column j once h_{j+1,j} is known (last block of k_vnew).
+// Givens update of column j once h_{j+1,j} is known (last block of k_vnew).  The
+// column's entries 0..j (hc) and the earlier rotations (cs, sn) are read from shared
+// memory, where the whole block staged them: the j rotations are a sequential chain
+// whose carried value stays in registers, so no step waits on a global load.
 template <typename C>
-__device__ void givens_step(const OuterDev<C>& O, OuterState* st, int j, double hn) {
+__device__ void givens_step(const OuterDev<C>& O, OuterState* st, int j, double hn, const double2* hc,
+                            const double* cs, const double2* sn_prev) {
   const int M1 = st->m + 1;
   double2* Hc = O.Hm + (size_t)j * M1;
-  Hc[j + 1] = make_double2(hn, 0);
+  double2 t0 = hc[0];
   for (int i = 0; i < j; ++i) {
-    const double c = O.cs[i];
-    const double2 s = O.sn[i];
-    const double2 t0 = Hc[i], t1 = Hc[i + 1];
+    const double c = cs[i];
+    const double2 s = sn_prev[i];
+    const double2 t1 = hc[i + 1];
     Hc[i] = cadd(make_double2(c * t0.x, c * t0.y), cmul(s, t1));
-    Hc[i + 1] = csub(make_double2(c * t1.x, c * t1.y), cmul(dconj(s), t0));
+    t0 = csub(make_double2(c * t1.x, c * t1.y), cmul(dconj(s), t0));
   }
-  const double2 a = Hc[j], b = Hc[j + 1];
+  const double2 a = t0, b = make_double2(hn, 0);
   const double na = sqrt(dabs2(a)), nb = sqrt(dabs2(b));
   const double r = hypot(na, nb);
   double c;
@@ -403,6 +407,12 @@ __device__ void givens_step(const OuterDev<C>& O, OuterState* st, int j, double 
   const double2 g0 = O.g[j];
   O.g[j] = make_double2(c * g0.x, c * g0.y);
   O.g[j + 1] = cmul(make_double2(-sn.x, sn.y), g0);
+}
+
+// Shared memory of k_vnew: the scaled column h (m+1), then the staging of the Givens
+// update: column j (m+1), sines (m), cosines (m).
+HELM_HD constexpr size_t vnew_smem_bytes(int m) {
+  return (size_t)(m + 1) * 16 + (size_t)(m + 1) * 16 + (size_t)m * 16 + (size_t)m * 8;
 }
 
 // start = 1: v_0 = w / beta (w holds the true residual).
@@ -461,6 +471,19 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
     }
     double red[2] = {accu, (double)accb}, tot[2];
     if (grid_sum_last<2>(red, O.part, unit, chunks, &st->counter, sm, tot)) {
+      const int mm = st->m;
+      double2* hc = sh + (mm + 1);
+      double2* sn_prev = hc + (mm + 1);
+      double* cs = reinterpret_cast<double*>(sn_prev + mm);
+      if (!start) {
+        const double2* Hc = O.Hm + (size_t)j * (mm + 1);
+        for (int i = tid; i <= j; i += blockDim.x) hc[i] = __ldcg(Hc + i);
+        for (int i = tid; i < j; i += blockDim.x) {
+          sn_prev[i] = __ldcg(O.sn + i);
+          cs[i] = __ldcg(O.cs + i);
+        }
+        __syncthreads();
+      }
       if (tid == 0) {
         sweep_begin(O.sc0, (typename CT<C>::R)tot[1], O.s);
         if (start) {
@@ -470,7 +493,7 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
         } else {
           const double hn = sqrt(tot[0]);
           O.vscale[jn] = hn > 0.0 ? 1.0 / hn : 0.0;
-          givens_step(O, st, j, hn);
+          givens_step(O, st, j, hn, hc, cs, sn_prev);
           st->iters += 1;
           st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
           // lucky breakdown: the new direction vanishes against H z_j
@@ -581,7 +604,15 @@ void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start,
     pad = (size_t)per_sm / 3 + 1024;
     cudaFuncSetAttribute(k_vnew<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(pad, 160 * 1024));
   }
-  const size_t smem = std::max<size_t>((size_t)(m + 1) * sizeof(double2), pad);
+  const size_t need = vnew_smem_bytes(m);
+  if (need > 160 * 1024) {
+    static size_t configured = 0;
+    if (need > configured) {
+      cudaFuncSetAttribute(k_vnew<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+      configured = need;
+    }
+  }
+  const size_t smem = std::max<size_t>(need, pad);
   const int resident = resident_grid(k_vnew<C>, 256, smem);
   k_vnew<C><<<std::min(nprob * chunks, resident), 256, smem, s>>>(od, nprob, chunks, start ? 1 : 0);
 }
