@@ -137,6 +137,25 @@ def traffic_for(kernel_class: str, alg_bytes_per_launch: float):
     return rec["dram_bytes"] / rec["algorithmic_bytes"] * alg_bytes_per_launch
 
 
+def vcycle_hbm(classes, peak_gbs):
+    """Algorithmic bandwidth of the V-cycle kernel classes (vc.*): the library's
+    algorithmic bytes of each class over its CUDA-event time, and their total, as a
+    fraction of the measured HBM copy bandwidth.  Levels whose vectors fit in L2
+    (129 MB; every level of a 1023^2 problem) can read above it."""
+    out, tb, tms = {}, 0.0, 0.0
+    for c, v in sorted(classes.items()):
+        if not c.startswith("vc.") or v["ms"] <= 0 or v["bytes"] <= 0:
+            continue
+        gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+        out[c] = {"GB/s": round(gbs, 1), "frac": round(gbs / peak_gbs, 3)}
+        tb += v["bytes"]
+        tms += v["ms"]
+    if tms <= 0:
+        return None
+    gbs = tb / (tms * 1e-3) / 1e9
+    return {"achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs, "classes": out}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -288,6 +307,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks, "iters_per_beta": dict(zip([str(t) for t in BETAS], iters)),
             "solves_per_s": len(BETAS) * args.steps * world / (ms_total * 1e-3),
             "ms_steps": ms_steps, "kernel_classes_warmup": classes, "sequential": seq,
+            "vcycle_hbm": vcycle_hbm(classes, pk.get("hbm_gbs", 6800.0)),
             "solve_mode": "batched: the four theta_beta solves of a step share every launch (helm_batch_solve)"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
@@ -364,6 +384,7 @@ def run_precond(args):
     classes = helm.profile_end()
     print(json.dumps({"mode": "precond", "dim": dim, "n": n, "ms_per_vcycle": 1e3 * dt,
                       "mpts_per_s": n ** dim / dt / 1e6,
+                      "vcycle_hbm": vcycle_hbm(classes, peaks().get("hbm_gbs", 6800.0)),
                       "classes_us_per_vcycle": {c: round(1e3 * v["ms"] / args.reps, 1) for c, v in classes.items()},
                       "launches_per_vcycle": {c: v["launches"] // args.reps for c, v in classes.items()}}),
           flush=True)

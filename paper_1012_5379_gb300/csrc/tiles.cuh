@@ -205,13 +205,28 @@ k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, i
     const C* box[J];
 #pragma unroll
     for (int k = 0; k < J; ++k) box[k] = reinterpret_cast<const C*>(tsm + (stage * J + k) * TMA_BOX_STRIDE);
-    // v_J on the tile plus halo: vt[r][c] is the point (x0 - 1 + c, y0 - 1 + r), box column c + 1
-    for (int q = tid; q < (T2Y + 2) * (T2X + 2); q += 256) {
-      const int r = q / (T2X + 2), c = q - r * (T2X + 2);
+    // v_J on the tile plus halo: vt[r][c] is the point (x0 - 1 + c, y0 - 1 + r), box
+    // column c + 1.  Each thread forms its own four points and keeps their raw values
+    // for the dot products; the first HALO2 threads form the halo.
+    C raw[4][J];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
       C v = czero<C>();
 #pragma unroll
-      for (int k = 0; k < J; ++k) v = cfma(cf[k], box[k][r * TMA_BX + c + 1], v);
-      vt[r][c] = v;
+      for (int k = 0; k < J; ++k) {
+        raw[q][k] = box[k][(oy + 1) * TMA_BX + ox + 2];
+        v = cfma(cf[k], raw[q][k], v);
+      }
+      vt[oy + 1][ox + 1] = v;
+    }
+    if (tid < HALO2) {
+      int hx, hy;
+      halo_coord<T2X, T2Y>(tid, hx, hy);
+      C v = czero<C>();
+#pragma unroll
+      for (int k = 0; k < J; ++k) v = cfma(cf[k], box[k][(hy + 1) * TMA_BX + hx + 2], v);
+      vt[hy + 1][hx + 1] = v;
     }
     __syncthreads();
     const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
@@ -227,7 +242,7 @@ k_arnoldi_tma2(const LevelDev<float2>* __restrict__ levs, int ntiles, int tpc, i
         p = stencil5((q & 1) ? cx1 : cx0, cy, S.phi_at(x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
                      vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
 #pragma unroll
-        for (int k = 0; k < J; ++k) acc[k] = cdotacc(box[k][(oy + 1) * TMA_BX + ox + 2], p, acc[k]);
+        for (int k = 0; k < J; ++k) acc[k] = cdotacc(raw[q][k], p, acc[k]);
         accn += cabs2(p);
       }
       if (store_p && x < P && y < P) pJ[pidx(x, y, 0, P)] = p;
@@ -295,9 +310,7 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
       vb[z & 3][hy + 1][hx + 1] = w;
     }
   };
-  const StencilRegs<C> S(L);
-  C* const pJ = L.p[J - 1];
-  const Coef3<C> cx = S.coef(x), cy = S.coef(y);
+  const Coef3<C> cx = ldcoef(L, x), cy = ldcoef(L, y);
   C acc[J];
 #pragma unroll
   for (int k = 0; k < J; ++k) acc[k] = czero<C>();
@@ -312,8 +325,8 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
       const int s0 = z & 3;
       C p = czero<C>();
       if (inside(x, y, z, n)) {
-        const Coef3<C> cz = S.coef(z);
-        p = stencil5(cx, cy, S.phi_at(x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
+        const Coef3<C> cz = ldcoef(L, z);
+        p = stencil5(cx, cy, phi_at(L, x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
                      vb[s0][ly][lx + 1], vb[s0][ly + 2][lx + 1]);
         p = cfma(cz.d, vb[s0][ly + 1][lx + 1], p);
         p = cfma(cz.a, vb[(z - 1) & 3][ly + 1][lx + 1], p);
@@ -322,7 +335,7 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
         for (int k = 0; k < J; ++k) acc[k] = cdotacc(rawc[k], p, acc[k]);
         accn += cabs2(p);
       }
-      if (store_p && x < P && y < P) pJ[pidx(x, y, z, P)] = p;
+      if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, z, P)] = p;
 #pragma unroll
       for (int k = 0; k < J; ++k) rawc[k] = rawn[k];
     }
@@ -422,8 +435,6 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
   const int x = x0 + lx, y = y0 + ly;
   UpdCoef<C> u = load_upd(L, r0_is_b);
   if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
-  C* const xa = L.xa;
-  C* const bc = L.bc;
   const bool halo = tid < T3X + 1 + T3Y;
   const int hx = tid < T3X + 1 ? tid : T3X;
   const int hy = tid < T3X + 1 ? T3Y : tid - (T3X + 1);
@@ -436,7 +447,7 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
       upd_point(u, x, y, z, n, P, dx, r);
       if (z < zend && x < P && y < P) {
         const size_t id = pidx(x, y, z, P);
-        xa[id] = inside(x, y, z, n) ? cadd(x_from_zero ? czero<C>() : xa[id], dx) : czero<C>();
+        L.xa[id] = inside(x, y, z, n) ? cadd(x_from_zero ? czero<C>() : L.xa[id], dx) : czero<C>();
       }
       rb[z & 3][ly][lx] = r;
       if (halo) {
@@ -460,7 +471,7 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
         const int Ix = x0 / 2 + cx, Iy = y0 / 2 + cy, Iz = z / 2 - 1;
         if (Ix < Pc && Iy < Pc && Iz < Pc) {
           const bool valid = Ix < nc && Iy < nc && Iz < nc;
-          bc[pidx(Ix, Iy, Iz, Pc)] = valid ? out : czero<C>();
+          L.bc[pidx(Ix, Iy, Iz, Pc)] = valid ? out : czero<C>();
           if (valid) acc += cabs2(out);
         }
       }
@@ -561,21 +572,14 @@ k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
   const bool halo = tid < HALO3;
   int hx = 0, hy = 0;
   if (halo) halo_coord<T3X, T3Y>(tid, hx, hy);
-  const StencilRegs<C> S(L);
-  const C* const xa = L.xa;
-  const C* const xcb = L.xcb;
-  const C* const bv = L.b;
-  C* const xb = L.xb;
-  C* const r0 = L.r0;
-  const int nc = L.nc, Pc = L.Pc;
   auto form = [&](int xx, int yy, int zz) -> C {
-    return cadd(ldc(xa, xx, yy, zz, n, P), interp(xcb, n, nc, Pc, xx, yy, zz, 3));
+    return cadd(ldc((const C*)L.xa, xx, yy, zz, n, P), interp(L, xx, yy, zz, 3));
   };
   auto load_plane = [&](int z) {
     vb[z & 3][ly + 1][lx + 1] = form(x, y, z);
     if (halo) vb[z & 3][hy + 1][hx + 1] = form(x0 + hx, y0 + hy, z);
   };
-  const Coef3<C> cx = S.coef(x), cy = S.coef(y);
+  const Coef3<C> cx = ldcoef(L, x), cy = ldcoef(L, y);
   R acc = 0;
   if (zbeg < P) {
     load_plane(zbeg - 1);
@@ -587,18 +591,18 @@ k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
       if (x < P && y < P) {
         C r = czero<C>(), xo = czero<C>();
         if (inside(x, y, z, n)) {
-          const Coef3<C> cz = S.coef(z);
-          C p = stencil5(cx, cy, S.phi_at(x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
+          const Coef3<C> cz = ldcoef(L, z);
+          C p = stencil5(cx, cy, phi_at(L, x, y, z), vb[s0][ly + 1][lx + 1], vb[s0][ly + 1][lx], vb[s0][ly + 1][lx + 2],
                          vb[s0][ly][lx + 1], vb[s0][ly + 2][lx + 1]);
           p = cfma(cz.d, vb[s0][ly + 1][lx + 1], p);
           p = cfma(cz.a, vb[(z - 1) & 3][ly + 1][lx + 1], p);
           p = cfma(cz.c, vb[(z + 1) & 3][ly + 1][lx + 1], p);
-          r = csub(__ldg(bv + pidx(x, y, z, P)), p);
+          r = csub(__ldg(L.b + pidx(x, y, z, P)), p);
           xo = vb[s0][ly + 1][lx + 1];
           acc += cabs2(r);
         }
-        xb[pidx(x, y, z, P)] = xo;
-        r0[pidx(x, y, z, P)] = r;
+        L.xb[pidx(x, y, z, P)] = xo;
+        L.r0[pidx(x, y, z, P)] = r;
       }
     }
   }
