@@ -258,6 +258,23 @@ def run_ours(args, rank, world, local_rank):
                 "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / nl,
                 "algorithmic_bytes_per_launch": d["bytes"] / nl}
 
+    # one V-cycle of the workload on its own (no concurrent outer passes): its passes'
+    # algorithmic bandwidth against HBM
+    r64 = b.to(torch.complex64)
+    z64 = torch.empty_like(r64)
+    for _ in range(3):
+        handles[0].precond_apply(r64, z64)
+    torch.cuda.synchronize()
+    helm.profile_begin("")
+    for _ in range(10):
+        handles[0].precond_apply(r64, z64)
+    torch.cuda.synchronize()
+    vc_alone = vcycle_hbm(helm.profile_end(), pk.get("hbm_gbs", 6800.0))
+    if vc_alone:
+        vc_alone["note"] = ("10 V-cycles of the theta_beta 0.1 problem alone; every level of a 1023^2 "
+                            "problem fits in L2 (129 MB), so the passes are latency-bound, not HBM-bound")
+    del r64, z64
+
     # the same step solved one problem at a time (context: what batching buys)
     seq = None
     if args.sequential_steps > 0:
@@ -307,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks, "iters_per_beta": dict(zip([str(t) for t in BETAS], iters)),
             "solves_per_s": len(BETAS) * args.steps * world / (ms_total * 1e-3),
             "ms_steps": ms_steps, "kernel_classes_warmup": classes, "sequential": seq,
-            "vcycle_hbm": vcycle_hbm(classes, pk.get("hbm_gbs", 6800.0)),
+            "vcycle_hbm": vc_alone,
             "solve_mode": "batched: the four theta_beta solves of a step share every launch (helm_batch_solve)"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters)

@@ -371,24 +371,55 @@ size_t outer_part_doubles(int chunks, int m) {
 }
 
 // ------------------------------------------------------------------ new Arnoldi vector
-// Givens update of column j once h_{j+1,j} is known (last block of k_vnew).  The
-// column's entries 0..j (hc) and the earlier rotations (cs, sn) are read from shared
-// memory, where the whole block staged them: the j rotations are a sequential chain
-// whose carried value stays in registers, so no step waits on a global load.
+// Givens update of column j once h_{j+1,j} is known (last block of k_vnew, warp 0).
+// The column's entries 0..j (hc) and the earlier rotations (cs, sn) were staged in
+// shared memory by the whole block.  Rotation i maps the running entry t_i and the
+// untouched h_{i+1} to the final H[i] = c_i t_i + s_i h_{i+1} and to
+// t_{i+1} = c_i h_{i+1} - conj(s_i) t_i, an affine map of t_i.  A dependent chain of j
+// such maps costs j x ~14 FP64 latencies on one thread (on this part every FP64
+// instruction occupies its pipe for 64 cycles), so the warp splits the chain into 32
+// segments, composes each segment's maps, scans the compositions across lanes, and
+// every lane then walks its own segment from the exact entering t.
 template <typename C>
-__device__ void givens_step(const OuterDev<C>& O, OuterState* st, int j, double hn, const double2* hc,
-                            const double* cs, const double2* sn_prev) {
+__device__ void givens_step_warp(const OuterDev<C>& O, OuterState* st, int j, double hn, const double2* hc,
+                                 const double* cs, const double2* sn_prev, double2* t_last) {
+  const int lane = threadIdx.x & 31;
   const int M1 = st->m + 1;
   double2* Hc = O.Hm + (size_t)j * M1;
-  double2 t0 = hc[0];
-  for (int i = 0; i < j; ++i) {
+  const int per = (j + 31) / 32;
+  const int i0 = min(j, lane * per), i1 = min(j, i0 + per);
+  // composition (al, be) of this lane's maps t -> A_i t + B_i, A_i = -conj(s_i), B_i = c_i h_{i+1}
+  double2 al = make_double2(1, 0), be = make_double2(0, 0);
+  for (int i = i0; i < i1; ++i) {
+    const double2 A = make_double2(-sn_prev[i].x, sn_prev[i].y);
+    const double2 B = make_double2(cs[i] * hc[i + 1].x, cs[i] * hc[i + 1].y);
+    be = cfma(A, be, B);
+    al = cmul(A, al);
+  }
+  // inclusive scan: lane l holds the composition of segments 0..l (earlier maps first)
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double2 pa = shfl_up_c(al, o), pb = shfl_up_c(be, o);
+    if (lane >= o) {
+      be = cfma(al, pb, be);
+      al = cmul(al, pa);
+    }
+  }
+  const double2 ea = shfl_up_c(al, 1), eb = shfl_up_c(be, 1);
+  const double2 h0 = hc[0];
+  double2 t = lane == 0 ? h0 : cfma(ea, h0, eb);  // t_{i0}
+  for (int i = i0; i < i1; ++i) {
     const double c = cs[i];
     const double2 s = sn_prev[i];
     const double2 t1 = hc[i + 1];
-    Hc[i] = cadd(make_double2(c * t0.x, c * t0.y), cmul(s, t1));
-    t0 = csub(make_double2(c * t1.x, c * t1.y), cmul(dconj(s), t0));
+    Hc[i] = cadd(make_double2(c * t.x, c * t.y), cmul(s, t1));
+    t = csub(make_double2(c * t1.x, c * t1.y), cmul(dconj(s), t));
   }
-  const double2 a = t0, b = make_double2(hn, 0);
+  if (i1 == j && i0 < i1) *t_last = t;  // the lane holding rotation j-1
+  if (j == 0 && lane == 0) *t_last = h0;
+  __syncwarp();
+  if (lane != 0) return;
+  const double2 a = *t_last, b = make_double2(hn, 0);
   const double na = sqrt(dabs2(a)), nb = sqrt(dabs2(b));
   const double r = hypot(na, nb);
   double c;
@@ -484,6 +515,8 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
         }
         __syncthreads();
       }
+      __shared__ double2 t_last;
+      if (!start && tid < 32) givens_step_warp(O, st, j, tid == 0 ? sqrt(tot[0]) : 0.0, hc, cs, sn_prev, &t_last);
       if (tid == 0) {
         sweep_begin(O.sc0, (typename CT<C>::R)tot[1], O.s);
         if (start) {
@@ -493,11 +526,10 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
         } else {
           const double hn = sqrt(tot[0]);
           O.vscale[jn] = hn > 0.0 ? 1.0 / hn : 0.0;
-          givens_step(O, st, j, hn, hc, cs, sn_prev);
           st->iters += 1;
           st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
           // lucky breakdown: the new direction vanishes against H z_j
-        const bool breakdown = !(hn > 1e-14 * sqrt(st->wnorm2));
+          const bool breakdown = !(hn > 1e-14 * sqrt(st->wnorm2));
           if (!isfinite(st->rel_est)) { st->done = 3; st->status = -4; st->cycle_end = 1; }
           else if (st->rel_est <= st->tol || st->iters >= st->maxit || j + 1 >= st->m || breakdown) st->cycle_end = 1;
           else st->j = jn;
