@@ -205,16 +205,20 @@ k_load_input(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, const Ci
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
   pdl_wait();
-  const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
+  // CTAs take rows (z, y) of the padded layout in turn; threads stride along x
+  const int nrows = dim == 3 ? P * P : P;
+  C* const b = L.b;
   typename CT<C>::R acc = 0;
-  for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < npts; i += (size_t)ntiles * blockDim.x) {
-    const int x = (int)(i % P);
-    const int y = (int)((i / P) % P);
-    const int z = dim == 3 ? (int)(i / ((size_t)P * P)) : 0;
-    C v = czero<C>();
-    if (inside(x, y, z, n)) v = to_c<C>(src[((size_t)z * n + y) * n + x]);
-    L.b[i] = v;
-    acc += cabs2(v);
+  for (int row = tile; row < nrows; row += ntiles) {
+    const int y = dim == 3 ? row % P : row, z = dim == 3 ? row / P : 0;
+    const bool rin = y < n && z < n;
+    const size_t base = (size_t)row * P, sbase = ((size_t)z * n + y) * n;
+    for (int x = threadIdx.x; x < P; x += blockDim.x) {
+      C v = czero<C>();
+      if (rin && x < n) v = to_c<C>(src[sbase + x]);
+      b[base + x] = v;
+      acc += cabs2(v);
+    }
   }
   typename CT<C>::R red[1] = {acc}, tot[1];
   pdl_trigger();  // the main work is done: let the next pass launch
@@ -231,12 +235,13 @@ k_store_output(const LevelDev<C>* __restrict__ levs, int dim, Cout* __restrict__
   const LevelDev<C>& L = levs[0];
   const int n = L.n, P = L.P;
   pdl_wait();
-  const size_t npts = dim == 3 ? (size_t)n * n * n : (size_t)n * n;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % n);
-    const int y = (int)((i / n) % n);
-    const int z = dim == 3 ? (int)(i / ((size_t)n * n)) : 0;
-    dst[i] = to_c<Cout>(L.xb[pidx(x, y, z, P)]);
+  // CTAs take rows (z, y) of the natural layout in turn; threads stride along x
+  const int nrows = dim == 3 ? n * n : n;
+  const C* const xb = L.xb;
+  for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int y = dim == 3 ? row % n : row, z = dim == 3 ? row / n : 0;
+    const size_t dbase = (size_t)row * n, sbase = ((size_t)z * P + y) * P;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) dst[dbase + x] = to_c<Cout>(xb[sbase + x]);
   }
 }
 
