@@ -181,6 +181,9 @@ typedef struct {
   int queued, active, peak_active;
   size_t bytes_in_use, peak_bytes;
   int handles_created, handles_reused;
+  long long group_builds;  /* problem groups (re)built on membership changes (whole library) */
+  long long graph_builds;  /* V-cycle CUDA graphs captured and instantiated (whole library) */
+  double build_s;          /* host seconds spent in both */
 } helm_serve_counters;
 
 /* Start a server on the current device (opts may be NULL: all defaults). */

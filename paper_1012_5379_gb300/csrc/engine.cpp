@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -580,6 +582,20 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
   }
 }
 
+// Host work of group (re)builds and V-cycle graph captures, for the serving counters.
+static std::atomic<long long> g_group_builds{0}, g_graph_builds{0}, g_build_ns{0};
+struct BuildTimer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  ~BuildTimer() {
+    g_build_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+void build_stats(long long* groups, long long* graphs, double* seconds) {
+  *groups = g_group_builds.load();
+  *graphs = g_graph_builds.load();
+  *seconds = 1e-9 * (double)g_build_ns.load();
+}
+
 // The V-cycle as one CUDA graph: captured once per group on a private stream (and
 // again whenever profiling starts or stops, so timed launches become event nodes),
 // replayed on the caller's stream.
@@ -587,6 +603,8 @@ template <typename C>
 static int run_vcycle_graph(Group<C>& g, cudaStream_t st) {
   const int gen = profile_generation();
   if (!g.vexec || g.vexec_gen != gen) {
+    BuildTimer timer;
+    g_graph_builds += 1;
     if (g.vexec) { cudaGraphExecDestroy(g.vexec); g.vexec = nullptr; }
     release(g.vrecs);
     g.vkernels = 0;
@@ -769,6 +787,8 @@ struct ActiveSet {
     fresh = true;
   }
   int rebuild(cudaStream_t st) {
+    BuildTimer timer;
+    g_group_builds += 1;
     own.reset();
     g = nullptr;
     dirty = false;

@@ -109,6 +109,8 @@ int serve_submit(Server* s, int dim, int n, double k, double theta_beta, const d
 int serve_poll(Server* s, long long ticket, helm_info* info, double* latency);
 int serve_wait(Server* s, long long ticket, double timeout_s, helm_info* info, double* latency);
 int serve_stats(Server* s, helm_serve_counters* out);
+// Group (re)builds, V-cycle graph captures and the host seconds spent in both.
+void build_stats(long long* groups, long long* graphs, double* seconds);
 int serve_stop(Server* s);
 int retarget_handle(Handle* h, double k, double theta_beta, cudaStream_t st);
 size_t estimate_handle_bytes(int dim, int n, int prec, int s, int restart, int maxit, int coarsest);

@@ -435,6 +435,7 @@ int serve_stats(Server* s, helm_serve_counters* out) {
   if (!s || !out) { set_error("NULL argument"); return HELM_EINVAL; }
   std::lock_guard<std::mutex> lk(s->mu);
   *out = s->stats;
+  build_stats(&out->group_builds, &out->graph_builds, &out->build_s);
   return HELM_OK;
 }
 

@@ -47,7 +47,8 @@ class helm_serve_counters(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
                 ("queued", ctypes.c_int), ("active", ctypes.c_int), ("peak_active", ctypes.c_int),
                 ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
-                ("handles_created", ctypes.c_int), ("handles_reused", ctypes.c_int)]
+                ("handles_created", ctypes.c_int), ("handles_reused", ctypes.c_int),
+                ("group_builds", ctypes.c_longlong), ("graph_builds", ctypes.c_longlong), ("build_s", ctypes.c_double)]
 
 
 class HelmError(RuntimeError):
