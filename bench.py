@@ -619,19 +619,24 @@ def run_serve(args):
     ok = sum(1 for x in results if x[2] == 0)
     work = sum(float(r.work.n) ** r.work.dim * x[0].iters for r, x in zip(stream, results))
     torch.cuda.empty_cache()
-    # sequential complex128 baseline: per-shape solve time from a sample of the stream's requests
+    # sequential baselines (complex128 and complex64 preconditioner): the solve time per
+    # outer iteration of each shape, from a sample of the stream's requests solved one at
+    # a time, times the iterations each request took when served (a problem's iterations
+    # do not depend on what it was batched with)
     seq = {}
+    served_iters = np.array([x[0].iters for x in results], dtype=float)
     for prec in ("c128", "c64"):
-        per_shape = {}
+        per_shape, per_iter = {}, {}
         for sh in shapes:
             sample = [r for r in stream if (r.work.dim, r.work.n) == sh][:args.seq_sample]
             bs = [srcs[sh][0].to("cuda") for _ in sample]
             xs = [torch.zeros_like(b) for b in bs]
-            times, _ = _seq_solves(helm, [r.work for r in sample], prec, bs, xs)
+            times, infos = _seq_solves(helm, [r.work for r in sample], prec, bs, xs)
             per_shape[sh] = float(np.mean(times))
+            per_iter[sh] = float(np.sum(times)) / max(1, sum(i.iters for i in infos))
             del bs, xs
             torch.cuda.empty_cache()
-        svc = np.array([per_shape[(r.work.dim, r.work.n)] for r in stream])
+        svc = np.array([per_iter[(r.work.dim, r.work.n)] for r in stream]) * served_iters
         arr = np.array([r.arrival for r in stream])
         fin = np.empty_like(arr)
         prev = 0.0
@@ -641,7 +646,8 @@ def run_serve(args):
         slat = fin - arr
         seq[prec] = {"solves_per_s": len(stream) / float(fin.max()), "p50_s": float(np.percentile(slat, 50)),
                      "p99_s": float(np.percentile(slat, 99)),
-                     "solve_s_per_shape": {f"{d}D {n}": v for (d, n), v in per_shape.items()}}
+                     "solve_s_per_shape": {f"{d}D {n}": v for (d, n), v in per_shape.items()},
+                     "solve_s_per_iteration": {f"{d}D {n}": v for (d, n), v in per_iter.items()}}
     line = {"mode": "serve", "metric": "solves/s", "value": len(stream) / t_total, "unit": "solves/s",
             "higher_is_better": True, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "requests": len(stream), "ok": ok, "rate_per_s": args.rate,

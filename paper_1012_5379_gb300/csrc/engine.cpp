@@ -346,6 +346,7 @@ struct Group {
   cudaGraphExec_t vexec = nullptr;
   int vexec_gen = -1;
   int vkernels = 0;
+  int direct_runs = 0;           // V-cycles launched directly (before the graph is captured)
   std::vector<GraphRec> vrecs;
   ~Group() {
     if (vexec) cudaGraphExecDestroy(vexec);
@@ -689,9 +690,19 @@ static double sub_points(const typename Group<C>::Sub& o, int dim) {
   return (double)o.cnt * (dim == 3 ? P * P * P : P * P);
 }
 
+// A group's first V-cycles are launched directly; the graph is captured once the group
+// has lived that long (serving and batches rebuild groups whenever membership changes,
+// and a capture costs more host time than a few direct launches).
+constexpr int GRAPH_AFTER = 3;
+
 template <typename C>
 static int run_iteration(Group<C>& g, cudaStream_t st) {
-  TRY(run_vcycle_graph<C>(g, st));
+  if (g.direct_runs < GRAPH_AFTER) {
+    run_vcycle<C>(g, st);
+    g.direct_runs += 1;
+  } else {
+    TRY(run_vcycle_graph<C>(g, st));
+  }
   const double E = sizeof(C);
   for (const auto& o : g.outer) {
     Launch L("out.apply_h", st, sub_points<C>(o, g.dim) * (16.0 + 2 * E + (g.hs[0]->has_phi ? 4.0 : 0.0)),
@@ -779,7 +790,17 @@ struct ActiveSet {
   OuterState* pin = nullptr;
   size_t pin_cap = 0;
   size_t n_read = 0;       // members whose state the last iterate() enqueued for reading
-  ~ActiveSet() { if (pin) cudaFreeHost(pin); }
+  // device copies: the members' state pointers (uploaded at each rebuild) and the
+  // gathered states
+  OuterState** d_src = nullptr;
+  OuterState* d_stage = nullptr;
+  size_t d_cap = 0;
+  std::vector<OuterState*> h_src;
+  ~ActiveSet() {
+    if (pin) cudaFreeHost(pin);
+    if (d_src) cudaFree(d_src);
+    if (d_stage) cudaFree(d_stage);
+  }
 
   void add(Handle* h) {
     members.push_back(h);
@@ -801,12 +822,31 @@ struct ActiveSet {
     g = own.get();
     return build_group<C>(members.data(), (int)members.size(), st, g, arena);
   }
+  // The members' state pointers on the device, for the per-iteration gather.
+  int upload_state_pointers(cudaStream_t st) {
+    if (d_cap < members.size()) {
+      if (d_src) CUDA_TRY(cudaFree(d_src));
+      if (d_stage) CUDA_TRY(cudaFree(d_stage));
+      d_src = nullptr;
+      d_stage = nullptr;
+      d_cap = std::max<size_t>(2 * members.size(), 16);
+      CUDA_TRY(cudaMalloc(&d_src, d_cap * sizeof(OuterState*)));
+      CUDA_TRY(cudaMalloc(&d_stage, d_cap * sizeof(OuterState)));
+    }
+    h_src.resize(members.size());
+    for (size_t p = 0; p < members.size(); ++p) h_src[p] = members[p]->st;
+    CUDA_TRY(cudaMemcpyAsync(d_src, h_src.data(), h_src.size() * sizeof(OuterState*), cudaMemcpyHostToDevice, st));
+    return HELM_OK;
+  }
   // Enqueue one outer iteration of every member (plus the first cycle end of new
   // members) and the copy of every member's state to pinned host memory.
   int iterate(cudaStream_t st) {
     n_read = 0;
     if (members.empty()) return HELM_OK;
-    if (dirty) TRY(rebuild(st));
+    if (dirty) {
+      TRY(rebuild(st));
+      TRY(upload_state_pointers(st));
+    }
     if (fresh) {
       run_cycle_end<C>(*g, st);
       fresh = false;
@@ -825,8 +865,11 @@ struct ActiveSet {
       pin_cap = std::max<size_t>(2 * members.size(), 16);
       CUDA_TRY(cudaMallocHost(&pin, sizeof(OuterState) * pin_cap));
     }
-    for (size_t p = 0; p < members.size(); ++p)
-      CUDA_TRY(cudaMemcpyAsync(pin + p, members[p]->st, sizeof(OuterState), cudaMemcpyDeviceToHost, st));
+    {
+      Launch L("io.state", st, 0, 0);
+      gather_states(d_src, d_stage, (int)members.size(), st);
+    }
+    CUDA_TRY(cudaMemcpyAsync(pin, d_stage, members.size() * sizeof(OuterState), cudaMemcpyDeviceToHost, st));
     n_read = members.size();
     return HELM_OK;
   }

@@ -219,6 +219,8 @@ template <typename C>
 void outer_backsolve(const OuterDev<C>* od, int nprob, cudaStream_t st);
 template <typename C>
 void outer_solution(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t st);
+// dst[p] = *src[p] for p < count (device pointers).
+void gather_states(OuterState* const* src, OuterState* dst, int count, cudaStream_t st);
 
 // Layout conversions and the stand-alone operator (convert.cu).
 void convert_dense_to_padded_c128(int dim, int n, const double2* src, double2* dst, cudaStream_t st);

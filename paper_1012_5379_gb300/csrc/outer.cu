@@ -657,6 +657,22 @@ void outer_solution(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStr
   k_solution<C><<<nprob * chunks, 256, (size_t)(m + 1) * sizeof(double2), s>>>(od, chunks);
 }
 
+// The outer states of a set's problems gathered into one array (one copy to the host
+// per iteration instead of one per problem).
+__global__ void __launch_bounds__(256) k_gather_states(OuterState* const* __restrict__ src, OuterState* dst,
+                                                       int count) {
+  constexpr int W = (int)(sizeof(OuterState) / sizeof(unsigned));
+  static_assert(sizeof(OuterState) % sizeof(unsigned) == 0, "OuterState is copied in 32-bit words");
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count * W; i += gridDim.x * blockDim.x) {
+    const int p = i / W, w = i - p * W;
+    reinterpret_cast<unsigned*>(dst + p)[w] = reinterpret_cast<const unsigned*>(src[p])[w];
+  }
+}
+void gather_states(OuterState* const* src, OuterState* dst, int count, cudaStream_t s) {
+  constexpr int W = (int)(sizeof(OuterState) / sizeof(unsigned));
+  k_gather_states<<<std::max(1, std::min(64, (count * W + 255) / 256)), 256, 0, s>>>(src, dst, count);
+}
+
 #define HELM_OUTER_INST(C)                                                                              \
   template void outer_residual<C>(int, const OuterDev<C>*, int, int, TileCfg, cudaStream_t);           \
   template void outer_apply_h<C>(int, const OuterDev<C>*, int, int, TileCfg, cudaStream_t);            \
