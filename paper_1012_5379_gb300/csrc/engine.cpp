@@ -61,19 +61,19 @@ static int upload_level_coefficients(Handle* h, int l, double theta_beta, cudaSt
   HostLevel& L = h->lev[l];
   std::vector<cplx> a, d, c;
   stencil_coefficients(grid_spacings(L.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
-  std::vector<double2> c64(3 * L.n);
+  double2* c64 = reinterpret_cast<double2*>(h->stage + h->stage_coef[l]);
   for (int i = 0; i < L.n; ++i) {
     c64[i] = make_double2(a[i].real(), a[i].imag());
     c64[L.n + i] = make_double2(d[i].real(), d[i].imag());
     c64[2 * L.n + i] = make_double2(c[i].real(), c[i].imag());
   }
-  CUDA_TRY(cudaMemcpyAsync(L.coef64, c64.data(), 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(L.coef64, c64, 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
   if (h->prec == HELM_C128) {
-    CUDA_TRY(cudaMemcpyAsync(L.coef, c64.data(), 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(L.coef, c64, 3 * L.n * sizeof(double2), cudaMemcpyHostToDevice, st));
   } else {
-    std::vector<float2> c32(3 * L.n);
+    float2* c32 = reinterpret_cast<float2*>(c64 + 3 * L.n);
     for (int i = 0; i < 3 * L.n; ++i) c32[i] = make_float2((float)c64[i].x, (float)c64[i].y);
-    CUDA_TRY(cudaMemcpyAsync(L.coef, c32.data(), 3 * L.n * sizeof(float2), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(L.coef, c32, 3 * L.n * sizeof(float2), cudaMemcpyHostToDevice, st));
   }
   return HELM_OK;
 }
@@ -96,10 +96,12 @@ static int factor_coarsest(Handle* h, double theta_beta, cudaStream_t st) {
   std::vector<cplx> A = dense_operator(h->dim, Lc.n, a, d, c, phic);
   std::vector<int> perm;
   if (!lu_factor(A, cm, perm)) { set_error("coarsest operator is singular"); return HELM_ENUMERIC; }
-  std::vector<double2> Ad(A.size());
+  double2* Ad = reinterpret_cast<double2*>(h->stage + h->stage_lu);
+  int* pv = reinterpret_cast<int*>(h->stage + h->stage_piv);
   for (size_t i = 0; i < A.size(); ++i) Ad[i] = make_double2(A[i].real(), A[i].imag());
-  CUDA_TRY(cudaMemcpyAsync(h->lu, Ad.data(), Ad.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(h->piv, perm.data(), cm * sizeof(int), cudaMemcpyHostToDevice, st));
+  for (int i = 0; i < cm; ++i) pv[i] = perm[i];
+  CUDA_TRY(cudaMemcpyAsync(h->lu, Ad, A.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(h->piv, pv, cm * sizeof(int), cudaMemcpyHostToDevice, st));
   return HELM_OK;
 }
 
@@ -146,6 +148,23 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   }
   const size_t eb = elem_bytes(h->prec);
 
+  // ------------------------------------------------ page-locked upload staging
+  {
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t off = r256(sizeof(OuterState));
+    h->stage_lu = off;
+    off += r256((size_t)cm * cm * sizeof(double2));
+    h->stage_piv = off;
+    off += r256((size_t)cm * sizeof(int));
+    h->stage_coef.resize(nlev);
+    for (int l = 0; l < nlev; ++l) {
+      h->stage_coef[l] = off;
+      off += r256(3 * (size_t)sizes[l] * (sizeof(double2) + eb));
+    }
+    void* p = nullptr;
+    CUDA_TRY(cudaMallocHost(&p, off));
+    h->stage = static_cast<char*>(p);
+  }
   // ------------------------------------------------ levels
   h->lev.resize(nlev);
   for (int l = 0; l < nlev; ++l) {
@@ -363,9 +382,12 @@ struct Group {
 struct GroupArena {
   void* p = nullptr;
   size_t cap = 0;
+  void* hp = nullptr;      // page-locked staging of the descriptor uploads (same layout as p)
+  size_t hcap = 0;
   cudaStream_t cap_stream = nullptr;
   ~GroupArena() {
     if (p) cudaFree(p);
+    if (hp) cudaFreeHost(hp);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 };
@@ -496,6 +518,13 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
       CUDA_TRY(cudaMalloc(&arena->p, 2 * bytes));
       arena->cap = 2 * bytes;
     }
+    if (arena->hcap < bytes) {
+      if (arena->hp) CUDA_TRY(cudaFreeHost(arena->hp));
+      arena->hp = nullptr;
+      arena->hcap = 0;
+      CUDA_TRY(cudaMallocHost(&arena->hp, 2 * bytes));
+      arena->hcap = 2 * bytes;
+    }
     if (!arena->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&arena->cap_stream, cudaStreamNonBlocking));
     g->owns = false;
     g->dmem = arena->p;
@@ -503,10 +532,23 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   } else {
     CUDA_TRY(cudaMalloc(&g->dmem, bytes));
   }
+  // Arena groups upload from the arena's page-locked staging: the copies then never wait
+  // for the work already queued on the stream (a set's stream may carry request
+  // inputs and results), and the previous group's copies have completed, since its
+  // iteration has.  Other groups upload from pageable memory and synchronise below.
   char* cur = (char*)g->dmem;
+  char* hstage = arena ? static_cast<char*>(arena->hp) : nullptr;
   auto put = [&](const void* src, size_t nb) -> void* {
     void* dst = cur;
-    if (nb) cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, st);
+    if (nb) {
+      const void* from = src;
+      if (hstage) {
+        char* hs = hstage + (cur - (char*)g->dmem);
+        std::memcpy(hs, src, nb);
+        from = hs;
+      }
+      cudaMemcpyAsync(dst, from, nb, cudaMemcpyHostToDevice, st);
+    }
     cur += (nb + 63) / 64 * 64;
     return dst;
   };
@@ -516,7 +558,7 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   g->lev0 = (LevelDev<C>*)put(lev0.data(), lev0.size() * sizeof(LevelDev<C>));
   for (size_t q = 0; q < subs.size(); ++q) g->outer[q].d = (OuterDev<C>*)put(subs[q].data(), subs[q].size() * sizeof(OuterDev<C>));
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaStreamSynchronize(st));
+  if (!arena) CUDA_TRY(cudaStreamSynchronize(st));
   return HELM_OK;
 }
 
@@ -744,7 +786,7 @@ static int begin_problem(Handle* h, const double2* b_dense, const double2* x_den
     if (x_dense) convert_dense_to_padded_c128(h->dim, h->n, x_dense, h->xpad, st);
   }
   if (!x_dense) CUDA_TRY(cudaMemsetAsync(h->xpad, 0, h->vs * sizeof(double2), st));
-  OuterState s0;
+  OuterState& s0 = *reinterpret_cast<OuterState*>(h->stage);
   std::memset(&s0, 0, sizeof(s0));
   s0.m = h->m;
   s0.maxit = h->maxit;
@@ -794,10 +836,11 @@ struct ActiveSet {
   // gathered states
   OuterState** d_src = nullptr;
   OuterState* d_stage = nullptr;
+  OuterState** h_src = nullptr;  // page-locked source of d_src
   size_t d_cap = 0;
-  std::vector<OuterState*> h_src;
   ~ActiveSet() {
     if (pin) cudaFreeHost(pin);
+    if (h_src) cudaFreeHost(h_src);
     if (d_src) cudaFree(d_src);
     if (d_stage) cudaFree(d_stage);
   }
@@ -827,15 +870,18 @@ struct ActiveSet {
     if (d_cap < members.size()) {
       if (d_src) CUDA_TRY(cudaFree(d_src));
       if (d_stage) CUDA_TRY(cudaFree(d_stage));
+      if (h_src) CUDA_TRY(cudaFreeHost(h_src));
       d_src = nullptr;
       d_stage = nullptr;
+      h_src = nullptr;
       d_cap = std::max<size_t>(2 * members.size(), 16);
       CUDA_TRY(cudaMalloc(&d_src, d_cap * sizeof(OuterState*)));
       CUDA_TRY(cudaMalloc(&d_stage, d_cap * sizeof(OuterState)));
+      CUDA_TRY(cudaMallocHost(&h_src, d_cap * sizeof(OuterState*)));
     }
-    h_src.resize(members.size());
+    // the previous upload from h_src has completed: the set's last iteration has
     for (size_t p = 0; p < members.size(); ++p) h_src[p] = members[p]->st;
-    CUDA_TRY(cudaMemcpyAsync(d_src, h_src.data(), h_src.size() * sizeof(OuterState*), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_src, h_src, members.size() * sizeof(OuterState*), cudaMemcpyHostToDevice, st));
     return HELM_OK;
   }
   // Enqueue one outer iteration of every member (plus the first cycle end of new
@@ -1092,6 +1138,7 @@ static void destroy_group_cache(Handle* h) {
 Handle::~Handle() {
   destroy_group_cache(this);
   for (void* p : allocs) cudaFree(p);
+  if (stage) cudaFreeHost(stage);
 }
 
 }  // namespace helm

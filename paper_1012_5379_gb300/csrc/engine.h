@@ -84,6 +84,13 @@ struct Handle {
   size_t bytes = 0;
   std::vector<void*> allocs;
   void* group_cache = nullptr;   // single-problem group (engine-owned)
+  // page-locked staging of the small uploads that re-target the handle and start a
+  // problem (pageable sources would make an upload wait for the stream's queued work):
+  // the outer state, the coarsest LU and pivots, each level's coefficients (FP64 and
+  // the preconditioner precision), at fixed offsets
+  char* stage = nullptr;
+  size_t stage_lu = 0, stage_piv = 0;
+  std::vector<size_t> stage_coef;  // per level: FP64 block, then the level-precision block
   ~Handle();
 };
 
