@@ -885,7 +885,7 @@ struct ActiveSet {
     return HELM_OK;
   }
   // Enqueue one outer iteration of every member (plus the first cycle end of new
-  // members) and the copy of every member's state to pinned host memory.
+  // members), the gather of the members' states and their copy to pinned host memory.
   int iterate(cudaStream_t st) {
     n_read = 0;
     if (members.empty()) return HELM_OK;
