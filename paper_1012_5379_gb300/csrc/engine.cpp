@@ -21,6 +21,16 @@ namespace helm {
 static size_t elem_bytes(int prec) { return prec == HELM_C128 ? sizeof(double2) : sizeof(float2); }
 
 
+static int sm_count_host() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  }
+  return sms;
+}
+
 // Sizes of the tiles of the marching kernels: 2D warps march `rows` rows, chosen to
 // give about four CTAs per SM on a single problem; 3D CTAs march 16 planes.
 static TileCfg default_tiles(int dim, int P) {
@@ -175,7 +185,9 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     const TileCfg cfg = default_tiles(h->dim, L.P);
     if (l == 0) h->cfg = cfg;
     L.ntiles = vtiles(h->dim, L.P);
-    L.nflat = (int)std::max<size_t>(1, std::min<size_t>(1024, (L.np + 1023) / 1024));
+    // flat passes: one wave of four CTAs per SM at most (their occupancy), so every CTA
+    // streams an equal share and no partial second wave trails
+    L.nflat = (int)std::max<size_t>(1, std::min<size_t>(std::min(1024, 4 * sm_count_host()), (L.np + 1023) / 1024));
     TRY(dev_alloc(h.get(), &L.b, L.np * eb));
     TRY(dev_alloc(h.get(), &L.xa, L.np * eb));
     TRY(dev_alloc(h.get(), &L.xb, L.np * eb));

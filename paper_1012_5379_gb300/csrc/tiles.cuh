@@ -353,46 +353,55 @@ k_arnoldi_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is
 // level's first sweep.  Tiles sit at even fine offsets, so a 64 x 16 fine tile maps
 // onto a 32 x 8 coarse tile (one coarse point per thread); r is formed on the tile
 // plus one row/column above (x0+64, y0+16).
-template <typename C>
-__global__ void __launch_bounds__(256)
-k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_is_b, int x_from_zero,
-              int nosmooth) {
+// The tiles of one CTA with the sweep's raw-vector count M fixed, so that every load
+// of a tile (M + 1 raw vectors and x at four points per thread) is issued before the
+// first is used.
+template <typename C, int M>
+__device__ __forceinline__ void restrict_tiles(const LevelDev<C>& L, const UpdCoef<C>& u, int unit, int tpc,
+                                               int ntiles, int x_from_zero, C (*rt)[T2X + 1],
+                                               typename CT<C>::R& acc) {
   typedef typename CT<C>::R R;
-  __shared__ C rt[T2Y + 1][T2X + 1];
-  __shared__ R sm[32];
-  const int nunits = ceil_div(ntiles, tpc);
-  const int prob = blockIdx.x / nunits, unit = blockIdx.x - prob * nunits;
-  const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
-  pdl_wait();
   const int ntx = ceil_div(P, T2X);
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
-  UpdCoef<C> u = load_upd(L, r0_is_b);
-  if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
   C* const xa = L.xa;
   C* const bc = L.bc;
-  R acc = 0;
   const int t_end = min(ntiles, (unit + 1) * tpc);
 #pragma unroll 1
   for (int tile = unit * tpc; tile < t_end; ++tile) {
     const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
+    constexpr int QB = M >= 3 ? 2 : 4;  // points whose loads are in flight together (registers)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
-      const int x = x0 + ox, y = y0 + oy;
-      C dx, r;
-      upd_point(u, x, y, 0, n, P, dx, r);
-      if (x < P && y < P) {
-        const size_t id = pidx(x, y, 0, P);
-        xa[id] = (x < n && y < n) ? cadd(x_from_zero ? czero<C>() : xa[id], dx) : czero<C>();
+    for (int q0 = 0; q0 < 4; q0 += QB) {
+      C v[QB][M + 1], xv[QB];
+#pragma unroll
+      for (int b = 0; b < QB; ++b) {
+        const int q = q0 + b;
+        const int x = x0 + lx + 32 * (q & 1), y = y0 + ly + 8 * (q >> 1);
+#pragma unroll
+        for (int k = 0; k <= M; ++k) v[b][k] = ldc(u.Rk[k], x, y, 0, n, P);
+        xv[b] = (x_from_zero || x >= n || y >= n) ? czero<C>() : xa[pidx(x, y, 0, P)];
       }
-      rt[oy][ox] = r;
+#pragma unroll
+      for (int b = 0; b < QB; ++b) {
+        const int q = q0 + b;
+        const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+        const int x = x0 + ox, y = y0 + oy;
+        C dx = czero<C>(), r = czero<C>();
+#pragma unroll
+        for (int k = 0; k < M; ++k) dx = cfma(u.xc[k], v[b][k], dx);
+#pragma unroll
+        for (int k = 0; k <= M; ++k) r = cfma(u.rc[k], v[b][k], r);
+        if (x < P && y < P) xa[pidx(x, y, 0, P)] = (x < n && y < n) ? cadd(xv[b], dx) : czero<C>();
+        rt[oy][ox] = r;
+      }
     }
     if (tid < T2X + 1 + T2Y) {
       const int hx = tid < T2X + 1 ? tid : T2X;
       const int hy = tid < T2X + 1 ? T2Y : tid - (T2X + 1);
-      C dx, r;
-      upd_point(u, x0 + hx, y0 + hy, 0, n, P, dx, r);
+      C r = czero<C>();
+#pragma unroll
+      for (int k = 0; k <= M; ++k) r = cfma(u.rc[k], ldc(u.Rk[k], x0 + hx, y0 + hy, 0, n, P), r);
       rt[hy][hx] = r;
     }
     __syncthreads();
@@ -411,6 +420,31 @@ k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_
     }
     __syncthreads();  // the next tile rewrites rt
   }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256, sizeof(C) == 16 ? 2 : 3)
+k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_is_b, int x_from_zero,
+              int nosmooth) {
+  typedef typename CT<C>::R R;
+  __shared__ C rt[T2Y + 1][T2X + 1];
+  __shared__ R sm[32];
+  const int nunits = ceil_div(ntiles, tpc);
+  const int prob = blockIdx.x / nunits, unit = blockIdx.x - prob * nunits;
+  const LevelDev<C>& L = levs[prob];
+  pdl_wait();
+  UpdCoef<C> u = load_upd(L, r0_is_b);
+  if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
+  R acc = 0;
+  switch (u.m) {  // uniform over the grid
+    case 0: restrict_tiles<C, 0>(L, u, unit, tpc, ntiles, x_from_zero, rt, acc); break;
+    case 1: restrict_tiles<C, 1>(L, u, unit, tpc, ntiles, x_from_zero, rt, acc); break;
+    case 2: restrict_tiles<C, 2>(L, u, unit, tpc, ntiles, x_from_zero, rt, acc); break;
+    case 3: restrict_tiles<C, 3>(L, u, unit, tpc, ntiles, x_from_zero, rt, acc); break;
+    case 4: restrict_tiles<C, 4>(L, u, unit, tpc, ntiles, x_from_zero, rt, acc); break;
+    default: break;
+  }
+  static_assert(SMAX == 4, "restrict_tiles is instantiated for m = 0..4");
   R red[1] = {acc}, tot[1];
   pdl_trigger();  // the main work is done: let the next pass launch
   if (grid_sum_last<1>(red, L.part, unit, nunits, &L.sc->counter, sm, tot)) {
@@ -514,9 +548,11 @@ k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc) {
 #pragma unroll 1
   for (int tile = unit * tpc; tile < t_end; ++tile) {
     const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
+    C bq[4];  // b at the owned points, loaded with the first phase's reads
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
+      bq[q] = ldc(bv, x0 + ox, y0 + oy, 0, n, P);
       vt[oy + 1][ox + 1] = form(x0 + ox, y0 + oy);
     }
     if (tid < HALO2) {
@@ -537,7 +573,7 @@ k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc) {
         if (x < n && y < n) {
           const C p = stencil5((q & 1) ? cx1 : cx0, cy, S.phi_at(x, y, 0), vt[oy + 1][ox + 1], vt[oy + 1][ox],
                                vt[oy + 1][ox + 2], vt[oy][ox + 1], vt[oy + 2][ox + 1]);
-          r = csub(__ldg(bv + pidx(x, y, 0, P)), p);
+          r = csub(bq[q], p);
           xo = vt[oy + 1][ox + 1];
           acc += cabs2(r);
         }

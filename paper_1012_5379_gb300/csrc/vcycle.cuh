@@ -140,10 +140,48 @@ __device__ __forceinline__ void upd_point(const UpdCoef<C>& u, int x, int y, int
 // Pointwise end of a sweep: x += dx (in place on xa or xb, or from zero) and, in
 // residual mode, r0 <- r (in place) with ||r||^2 starting the next sweep.  Every
 // vector is zero at the padding positions, so this is a plain stream over the padded
-// index (UF_U points per thread at a time, all loads before the stores).
+// index (UF_U points per thread and round; 2 when a point reads four or more raw
+// vectors).  The body is instantiated per number of raw vectors M (uniform: the
+// sweep's length), so every load of a round is issued before the first is used.
 constexpr int UF_U = 4;
+template <typename C, int M, bool WANT_R>
+__device__ __forceinline__ void update_flat_body(const UpdCoef<C>& u, C* xo, C* r0out, size_t npts, size_t i_beg,
+                                                 size_t stride, bool x_from_zero, typename CT<C>::R& acc) {
+  constexpr int NV = WANT_R ? M + 1 : M;  // raw vectors read per point
+  constexpr int UF = NV >= 4 ? 2 : UF_U;  // points per thread and round (registers)
+  for (size_t i0 = i_beg; i0 < npts; i0 += UF * stride) {
+    C v[UF][NV > 0 ? NV : 1], xv[UF];
+#pragma unroll
+    for (int q = 0; q < UF; ++q) {
+      const size_t i = i0 + q * stride;
+      xv[q] = czero<C>();
+      if (i < npts) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[q][k] = u.Rk[k][i];
+        if (!x_from_zero) xv[q] = xo[i];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < UF; ++q) {
+      const size_t i = i0 + q * stride;
+      if (i >= npts) continue;
+      C dx = czero<C>();
+#pragma unroll
+      for (int k = 0; k < M; ++k) dx = cfma(u.xc[k], v[q][k], dx);
+      xo[i] = cadd(xv[q], dx);
+      if (WANT_R) {
+        C r = czero<C>();
+#pragma unroll
+        for (int k = 0; k <= M; ++k) r = cfma(u.rc[k], v[q][k < NV ? k : 0], r);
+        r0out[i] = r;
+        acc += cabs2(r);
+      }
+    }
+  }
+}
+
 template <typename C>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(C) == 16 ? 2 : 4)
 k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mode, int r0_is_b, int xsel,
               int x_from_zero) {
   __shared__ typename CT<C>::R sm[32];
@@ -153,40 +191,28 @@ k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mod
   pdl_wait();
   const UpdCoef<C> u = load_upd(L, r0_is_b);
   C* xo = xsel ? L.xb : L.xa;
+  C* r0out = L.r0;
   const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
   const bool want_r = (mode == UPD_RESIDUAL);
   const size_t stride = (size_t)ntiles * blockDim.x;
+  const size_t i_beg = (size_t)tile * blockDim.x + threadIdx.x;
+  const bool xz = x_from_zero != 0;
   typename CT<C>::R acc = 0;
-  for (size_t i0 = (size_t)tile * blockDim.x + threadIdx.x; i0 < npts; i0 += UF_U * stride) {
-    C xn[UF_U], rn[UF_U];
-#pragma unroll
-    for (int q = 0; q < UF_U; ++q) {
-      const size_t i = i0 + q * stride;
-      C dx = czero<C>(), r = czero<C>();
-      if (i < npts) {
-#pragma unroll
-        for (int k = 0; k <= SMAX; ++k) {
-          if (k < u.m || (want_r && k == u.m)) {
-            const C v = u.Rk[k][i];
-            if (k < u.m) dx = cfma(u.xc[k], v, dx);
-            r = cfma(u.rc[k], v, r);
-          }
-        }
-        xn[q] = cadd(x_from_zero ? czero<C>() : xo[i], dx);
-      }
-      rn[q] = r;
-    }
-#pragma unroll
-    for (int q = 0; q < UF_U; ++q) {
-      const size_t i = i0 + q * stride;
-      if (i >= npts) continue;
-      xo[i] = xn[q];
-      if (want_r) {
-        L.r0[i] = rn[q];
-        acc += cabs2(rn[q]);
-      }
-    }
+  switch (u.m) {  // uniform over the grid
+#define HELM_UF_CASE(MM)                                                                    \
+    case MM:                                                                                \
+      if (want_r) update_flat_body<C, MM, true>(u, xo, r0out, npts, i_beg, stride, xz, acc); \
+      else update_flat_body<C, MM, false>(u, xo, r0out, npts, i_beg, stride, xz, acc);       \
+      break;
+    HELM_UF_CASE(0)
+    HELM_UF_CASE(1)
+    HELM_UF_CASE(2)
+    HELM_UF_CASE(3)
+    HELM_UF_CASE(4)
+#undef HELM_UF_CASE
+    default: break;
   }
+  static_assert(SMAX == 4, "update_flat_body is instantiated for m = 0..4");
   if (!want_r) return;
   typename CT<C>::R red[1] = {acc}, tot[1];
   pdl_trigger();  // the main work is done: let the next pass launch
