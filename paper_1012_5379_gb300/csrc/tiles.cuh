@@ -452,6 +452,77 @@ k_restrict_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc, int r0_
   }
 }
 
+// The z-march of one 3D restriction tile with the sweep's raw-vector count M fixed:
+// the next plane's raw values (own point and halo point) and x are loaded before the
+// current plane is processed, so each plane's loads overlap the previous plane's work.
+template <typename C, int M>
+__device__ __forceinline__ void restrict3_march(const LevelDev<C>& L, const UpdCoef<C>& u, int x0, int y0, int zbeg,
+                                                int zend, int x_from_zero, C (*rb)[T3Y + 1][T3X + 1],
+                                                typename CT<C>::R& acc) {
+  typedef typename CT<C>::R R;
+  const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+  const int x = x0 + lx, y = y0 + ly;
+  const bool halo = tid < T3X + 1 + T3Y;
+  const int hx = tid < T3X + 1 ? tid : T3X;
+  const int hy = tid < T3X + 1 ? T3Y : tid - (T3X + 1);
+  const bool emit = tid < (T3X / 2) * (T3Y / 2);
+  const int cx = tid % (T3X / 2), cy = tid / (T3X / 2);
+  C* const xa = L.xa;
+  C* const bc = L.bc;
+  C vn[M + 1], hn[M + 1], xn;
+  auto load = [&](int z) {
+#pragma unroll
+    for (int k = 0; k <= M; ++k) vn[k] = ldc(u.Rk[k], x, y, z, n, P);
+    xn = (x_from_zero || !inside(x, y, z, n)) ? czero<C>() : xa[pidx(x, y, z, P)];
+    if (halo) {
+#pragma unroll
+      for (int k = 0; k <= M; ++k) hn[k] = ldc(u.Rk[k], x0 + hx, y0 + hy, z, n, P);
+    }
+  };
+  load(zbeg);
+  for (int z = zbeg; z <= zend; ++z) {
+    C vc[M + 1], hc[M + 1];
+    const C xc = xn;
+#pragma unroll
+    for (int k = 0; k <= M; ++k) { vc[k] = vn[k]; hc[k] = hn[k]; }
+    if (z < zend) load(z + 1);
+    C dx = czero<C>(), r = czero<C>();
+#pragma unroll
+    for (int k = 0; k < M; ++k) dx = cfma(u.xc[k], vc[k], dx);
+#pragma unroll
+    for (int k = 0; k <= M; ++k) r = cfma(u.rc[k], vc[k], r);
+    if (z < zend && x < P && y < P) xa[pidx(x, y, z, P)] = inside(x, y, z, n) ? cadd(xc, dx) : czero<C>();
+    rb[z & 3][ly][lx] = r;
+    if (halo) {
+      C r2 = czero<C>();
+#pragma unroll
+      for (int k = 0; k <= M; ++k) r2 = cfma(u.rc[k], hc[k], r2);
+      rb[z & 3][hy][hx] = r2;
+    }
+    __syncthreads();
+    if ((z & 1) == 0 && z > zbeg && emit) {
+      const int fx = 2 * cx + 1, fy = 2 * cy + 1;
+      C out = czero<C>();
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int ddx = -1; ddx <= 1; ++ddx) {
+            const R wgt = (R)((ddx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25) * (dz == 0 ? 0.5 : 0.25));
+            out = cadd(out, cscale(rb[(z - 1 + dz) & 3][fy + dy][fx + ddx], wgt));
+          }
+      const int Ix = x0 / 2 + cx, Iy = y0 / 2 + cy, Iz = z / 2 - 1;
+      if (Ix < Pc && Iy < Pc && Iz < Pc) {
+        const bool valid = Ix < nc && Iy < nc && Iz < nc;
+        bc[pidx(Ix, Iy, Iz, Pc)] = valid ? out : czero<C>();
+        if (valid) acc += cabs2(out);
+      }
+    }
+  }
+}
+
 template <typename C>
 __global__ void __launch_bounds__(256)
 k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_is_b, int x_from_zero, int nosmooth) {
@@ -460,55 +531,22 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
   __shared__ R sm[32];
   const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
-  const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
+  const int P = L.P;
   pdl_wait();
   const int ntx = ceil_div(P, T3X), nty = ceil_div(P, T3Y);
   const int x0 = (tile % ntx) * T3X, y0 = ((tile / ntx) % nty) * T3Y;
   const int zbeg = (tile / (ntx * nty)) * zc, zend = min(zbeg + zc, P);
-  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
-  const int x = x0 + lx, y = y0 + ly;
   UpdCoef<C> u = load_upd(L, r0_is_b);
   if (nosmooth) { u.m = 0; u.rc[0] = CT<C>::make(1, 0); }
-  const bool halo = tid < T3X + 1 + T3Y;
-  const int hx = tid < T3X + 1 ? tid : T3X;
-  const int hy = tid < T3X + 1 ? T3Y : tid - (T3X + 1);
-  const bool emit = tid < (T3X / 2) * (T3Y / 2);
-  const int cx = tid % (T3X / 2), cy = tid / (T3X / 2);
   R acc = 0;
   if (zbeg < P) {
-    for (int z = zbeg; z <= zend; ++z) {
-      C dx, r;
-      upd_point(u, x, y, z, n, P, dx, r);
-      if (z < zend && x < P && y < P) {
-        const size_t id = pidx(x, y, z, P);
-        L.xa[id] = inside(x, y, z, n) ? cadd(x_from_zero ? czero<C>() : L.xa[id], dx) : czero<C>();
-      }
-      rb[z & 3][ly][lx] = r;
-      if (halo) {
-        C d2, r2;
-        upd_point(u, x0 + hx, y0 + hy, z, n, P, d2, r2);
-        rb[z & 3][hy][hx] = r2;
-      }
-      __syncthreads();
-      if ((z & 1) == 0 && z > zbeg && emit) {
-        const int fx = 2 * cx + 1, fy = 2 * cy + 1;
-        C out = czero<C>();
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-          for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int ddx = -1; ddx <= 1; ++ddx) {
-              const R wgt = (R)((ddx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25) * (dz == 0 ? 0.5 : 0.25));
-              out = cadd(out, cscale(rb[(z - 1 + dz) & 3][fy + dy][fx + ddx], wgt));
-            }
-        const int Ix = x0 / 2 + cx, Iy = y0 / 2 + cy, Iz = z / 2 - 1;
-        if (Ix < Pc && Iy < Pc && Iz < Pc) {
-          const bool valid = Ix < nc && Iy < nc && Iz < nc;
-          L.bc[pidx(Ix, Iy, Iz, Pc)] = valid ? out : czero<C>();
-          if (valid) acc += cabs2(out);
-        }
-      }
+    switch (u.m) {  // uniform over the grid
+      case 0: restrict3_march<C, 0>(L, u, x0, y0, zbeg, zend, x_from_zero, rb, acc); break;
+      case 1: restrict3_march<C, 1>(L, u, x0, y0, zbeg, zend, x_from_zero, rb, acc); break;
+      case 2: restrict3_march<C, 2>(L, u, x0, y0, zbeg, zend, x_from_zero, rb, acc); break;
+      case 3: restrict3_march<C, 3>(L, u, x0, y0, zbeg, zend, x_from_zero, rb, acc); break;
+      case 4: restrict3_march<C, 4>(L, u, x0, y0, zbeg, zend, x_from_zero, rb, acc); break;
+      default: break;
     }
   }
   R red[1] = {acc}, tot[1];
@@ -620,8 +658,11 @@ k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
   if (zbeg < P) {
     load_plane(zbeg - 1);
     load_plane(zbeg);
+    C bnext = ldc((const C*)L.b, x, y, zbeg, n, P);  // b of the next plane, loaded a plane ahead
     for (int z = zbeg; z < zend; ++z) {
+      const C bcur = bnext;
       load_plane(z + 1);
+      if (z + 1 < zend) bnext = ldc((const C*)L.b, x, y, z + 1, n, P);
       __syncthreads();
       const int s0 = z & 3;
       if (x < P && y < P) {
@@ -633,7 +674,7 @@ k_prolong_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc) {
           p = cfma(cz.d, vb[s0][ly + 1][lx + 1], p);
           p = cfma(cz.a, vb[(z - 1) & 3][ly + 1][lx + 1], p);
           p = cfma(cz.c, vb[(z + 1) & 3][ly + 1][lx + 1], p);
-          r = csub(__ldg(L.b + pidx(x, y, z, P)), p);
+          r = csub(bcur, p);
           xo = vb[s0][ly + 1][lx + 1];
           acc += cabs2(r);
         }
