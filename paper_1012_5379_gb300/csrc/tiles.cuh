@@ -557,33 +557,12 @@ k_restrict_t3(const LevelDev<C>* __restrict__ levs, int ntiles, int zc, int r0_i
 }
 
 // ------------------------------------------------------------------ coarse correction
-// x_b = x_a + P e_c, r0 = b - M x_b, ||r0||^2 starts post-smoothing.  2D: the coarse
-// correction under a tile and its halo (coarse columns x0/2 - 1 .. x0/2 + 32, rows
-// y0/2 - 1 .. y0/2 + 8) is staged in shared memory together with the tile's x_a and b
-// reads, so the bilinear interpolation's parity-dependent reads hit shared memory.
-constexpr int CT2X = T2X / 2 + 2, CT2Y = T2Y / 2 + 2;  // 34 x 10 coarse points
-
-template <typename C>
-__device__ __forceinline__ C interp_tile(const C (*ct)[CT2X], int x, int y, int x0, int y0, int n) {
-  typedef typename CT<C>::R R;
-  if (!inside(x, y, 0, n)) return czero<C>();
-  // coarse index of fine i: odd -> (i-1)/2 (weight 1), even -> i/2 - 1 and i/2 (1/2 each);
-  // local to the staged tile, whose first coarse column / row is x0/2 - 1 / y0/2 - 1
-  const int cx = (x & 1) ? (x - 1) / 2 : x / 2 - 1, cy = (y & 1) ? (y - 1) / 2 : y / 2 - 1;
-  const int lx = cx - (x0 / 2 - 1), ly = cy - (y0 / 2 - 1);
-  const int nx = (x & 1) ? 1 : 2, ny = (y & 1) ? 1 : 2;
-  C acc = czero<C>();
-  for (int b = 0; b < ny; ++b)
-    for (int a = 0; a < nx; ++a) acc = cadd(acc, ct[ly + b][lx + a]);
-  return cscale(acc, (R)((nx == 2 ? 0.5 : 1.0) * (ny == 2 ? 0.5 : 1.0)));
-}
-
+// x_b = x_a + P e_c, r0 = b - M x_b, ||r0||^2 starts post-smoothing.
 template <typename C>
 __global__ void __launch_bounds__(256)
 k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc) {
   typedef typename CT<C>::R R;
   __shared__ C vt[T2Y + 2][T2X + 2];
-  __shared__ C ct[CT2Y][CT2X];
   __shared__ R sm[32];
   const int nunits = ceil_div(ntiles, tpc);
   const int prob = blockIdx.x / nunits, unit = blockIdx.x - prob * nunits;
@@ -599,34 +578,26 @@ k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc) {
   C* const xb = L.xb;
   C* const r0 = L.r0;
   const int nc = L.nc, Pc = L.Pc;
-  int hx = 0, hy = 0;
-  if (tid < HALO2) halo_coord<T2X, T2Y>(tid, hx, hy);
+  auto form = [&](int xx, int yy) -> C {
+    return cadd(ldc(xa, xx, yy, 0, n, P), interp(xcb, n, nc, Pc, xx, yy, 0, 2));
+  };
   R acc = 0;
   const int t_end = min(ntiles, (unit + 1) * tpc);
 #pragma unroll 1
   for (int tile = unit * tpc; tile < t_end; ++tile) {
     const int x0 = (tile % ntx) * T2X, y0 = (tile / ntx) * T2Y;
-    // reads of the tile: the coarse correction (staged), x_a at the owned points and
-    // the halo point, b at the owned points
-    for (int i = tid; i < CT2X * CT2Y; i += 256) {
-      const int cyl = i / CT2X, cxl = i - cyl * CT2X;
-      ct[cyl][cxl] = ldc(xcb, x0 / 2 - 1 + cxl, y0 / 2 - 1 + cyl, 0, nc, Pc);
-    }
-    C xq[4], bq[4], xh = czero<C>();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int x = x0 + lx + 32 * (q & 1), y = y0 + ly + 8 * (q >> 1);
-      xq[q] = ldc(xa, x, y, 0, n, P);
-      bq[q] = ldc(bv, x, y, 0, n, P);
-    }
-    if (tid < HALO2) xh = ldc(xa, x0 + hx, y0 + hy, 0, n, P);
-    __syncthreads();
+    C bq[4];  // b at the owned points, loaded with the first phase's reads
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ox = lx + 32 * (q & 1), oy = ly + 8 * (q >> 1);
-      vt[oy + 1][ox + 1] = cadd(xq[q], interp_tile<C>(ct, x0 + ox, y0 + oy, x0, y0, n));
+      bq[q] = ldc(bv, x0 + ox, y0 + oy, 0, n, P);
+      vt[oy + 1][ox + 1] = form(x0 + ox, y0 + oy);
     }
-    if (tid < HALO2) vt[hy + 1][hx + 1] = cadd(xh, interp_tile<C>(ct, x0 + hx, y0 + hy, x0, y0, n));
+    if (tid < HALO2) {
+      int hx, hy;
+      halo_coord<T2X, T2Y>(tid, hx, hy);
+      vt[hy + 1][hx + 1] = form(x0 + hx, y0 + hy);
+    }
     __syncthreads();
     const Coef3<C> cx0 = S.coef(x0 + lx), cx1 = S.coef(x0 + lx + 32);
     Coef3<C> cy;
@@ -648,7 +619,7 @@ k_prolong_t2(const LevelDev<C>* __restrict__ levs, int ntiles, int tpc) {
         r0[pidx(x, y, 0, P)] = r;
       }
     }
-    __syncthreads();  // the next tile rewrites vt and ct
+    __syncthreads();  // the next tile rewrites vt
   }
   R red[1] = {acc}, tot[1];
   pdl_trigger();  // the main work is done: let the next pass launch
