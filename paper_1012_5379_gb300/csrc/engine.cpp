@@ -22,12 +22,12 @@ static size_t elem_bytes(int prec) { return prec == HELM_C128 ? sizeof(double2) 
 
 
 static int sm_count_host() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {  // thread-safe initialisation
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-  }
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    return v;
+  }();
   return sms;
 }
 

@@ -353,13 +353,12 @@ k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
 // SM (so the persistent grids, one or two CTAs per SM, get equal shares), at most one
 // per 256 points.
 int outer_chunks(size_t vs) {
-  static int units = 0;
-  if (units == 0) {
+  static const int units = [] {  // thread-safe initialisation
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    units = 2 * std::max(1, sms);
-  }
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+    return 2 * std::max(1, sms);
+  }();
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)units, (vs + DOT_THREADS - 1) / DOT_THREADS));
 }
 
@@ -615,7 +614,7 @@ static int resident_grid(K kernel, int threads, size_t smem) {
 template <typename C>
 void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t s) {
   const size_t smem = (size_t)(DOT_THREADS / 32) * 2 * (m + 1) * sizeof(double);
-  static size_t configured = 0;
+  thread_local size_t configured = 0;  // per host thread; setting the attribute again is harmless
   if (smem > 48 * 1024 && smem > configured) {
     cudaFuncSetAttribute(k_dots<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = smem;
@@ -628,7 +627,7 @@ void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start,
   // Shared memory is padded so that at most two CTAs fit on an SM: the persistent
   // grid of two CTAs per SM then places exactly two on every SM, and the FP64 work
   // (the bound of this pass) is spread evenly.
-  static size_t pad = 0;
+  thread_local size_t pad = 0;
   if (pad == 0) {
     int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -638,7 +637,7 @@ void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start,
   }
   const size_t need = vnew_smem_bytes(m);
   if (need > 160 * 1024) {
-    static size_t configured = 0;
+    thread_local size_t configured = 0;
     if (need > configured) {
       cudaFuncSetAttribute(k_vnew<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
       configured = need;

@@ -15,13 +15,13 @@ namespace helm {
 // the launch latency and the dependent's prologue then overlap the predecessor's
 // reduction tail.
 static inline int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
+  // initialised once, thread-safely (serving and callers' threads launch concurrently)
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+    return v;
+  }();
   return n;
 }
 template <typename... KArgs, typename... Args>
@@ -72,7 +72,7 @@ template <int J>
 static void arnoldi_tma2(const LevelDev<float2>* levs, int nprob, int ntiles, bool r0_is_b, bool store_p,
                          cudaStream_t st) {
   const size_t smem = tma_arnoldi_smem(J);
-  static bool configured = false;
+  thread_local bool configured = false;  // the attribute is per function; setting it again is harmless
   if (!configured) {
     cudaFuncSetAttribute(k_arnoldi_tma2<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
@@ -154,8 +154,8 @@ template <typename C>
 void launch_coarse_smem(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
                         int nu1, int nu2, size_t smem_bytes, cudaStream_t st) {
   // the static part (descriptors, sweep scalars) counts against the same limit: allow
-  // the largest dynamic part the device offers, once
-  static bool configured = false;
+  // the largest dynamic part the device offers, once per host thread
+  thread_local bool configured = false;
   if (!configured) {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa;
@@ -173,10 +173,11 @@ void launch_coarse_smem(int dim, const LevelDev<C>* levs, int nlev, int lev_stri
 // does not depend on the other problems of its launch).
 template <typename C>
 static int coarse_cluster_size() {
-  static int csize = 0;
-  if (csize == 0) {
+  // the largest cluster the device can place, found once (thread-safe initialisation)
+  static const int csize = [] {
     cudaFuncSetAttribute(k_coarse_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    for (int c = CLUSTER_MAX; c >= 1 && csize == 0; c >>= 1) {
+    int found = 0;
+    for (int c = CLUSTER_MAX; c >= 1 && found == 0; c >>= 1) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(c);
       cfg.blockDim = dim3(CLUSTER_THREADS);
@@ -189,11 +190,11 @@ static int coarse_cluster_size() {
       cfg.numAttrs = 1;
       int nclusters = 0;
       if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_cluster<C>, &cfg) == cudaSuccess && nclusters > 0)
-        csize = c;
+        found = c;
     }
     cudaGetLastError();
-    if (csize == 0) csize = 1;
-  }
+    return found == 0 ? 1 : found;
+  }();
   return csize;
 }
 
