@@ -121,9 +121,10 @@ class Level:
     phi: object                 # scalar or (n,)*dim array
     coef_h: Optional[tuple] = None   # ECS operator H (theta_beta = 0), finest level only
     lu: Optional[np.ndarray] = None  # dense coarsest matrix (coarsest level only)
+    shift: complex = 1.0        # M uses shift * phi: 1 for CSG, 1 + i eps for the CSL variant
 
     def apply(self, u):
-        return apply_operator(u, self.coef, self.phi)
+        return apply_operator(u, self.coef, self.shift * np.asarray(self.phi))
 
     def apply_h(self, u):
         return apply_operator(u, self.coef_h, self.phi)
@@ -131,13 +132,20 @@ class Level:
 
 def build_hierarchy(dim: int, n: int, theta_beta: float, theta_gamma: float = 0.5,
                     ecs_frac: float = 0.125, k: Optional[float] = None,
-                    phi: Optional[np.ndarray] = None, coarsest: int = 3) -> List[Level]:
+                    phi: Optional[np.ndarray] = None, coarsest: int = 3,
+                    csl_eps: float = 0.0) -> List[Level]:
     """Rediscretised hierarchy of M^CSG (Sec. 3.1, Prop. 3.1).
 
     Each level uses the same complex map with doubled real spacing; phi is sampled
     at the level's nodes (constant k: phi = k^2 everywhere; a field given on the
     fine nodes is sampled at the coincident coarse nodes).  The finest level also
     carries H (theta_beta = 0, Sec. 2 after Eq. csg_dis).
+
+    ``csl_eps`` > 0 gives the complex shifted Laplacian variant of the preconditioner
+    (Sec. 1 and Sec. 2: the shift (1 + eps i) k^2 of Erlangga, Oosterlee and Vuik):
+    M = L - (1 + i eps) phi on every level; with theta_beta = 0 this is M^CSL on the
+    real interior grid (the ECS layers stay), with theta_beta > 0 both devices
+    combine.  H is never shifted.
     """
     if (k is None) == (phi is None):
         raise ValueError("give exactly one of k (constant) or phi (field)")
@@ -147,7 +155,7 @@ def build_hierarchy(dim: int, n: int, theta_beta: float, theta_gamma: float = 0.
         if li > 0 and not np.isscalar(cur_phi):
             cur_phi = _inject(cur_phi)
         sp = spacings(nl, ecs_frac, theta_gamma, theta_beta)
-        lev = Level(n=nl, dim=dim, coef=coefficients_1d(sp), phi=cur_phi)
+        lev = Level(n=nl, dim=dim, coef=coefficients_1d(sp), phi=cur_phi, shift=complex(1.0, csl_eps))
         if li == 0:
             lev.coef_h = coefficients_1d(spacings(nl, ecs_frac, theta_gamma, 0.0))
         levels.append(lev)

@@ -127,6 +127,30 @@ def test_closed_form_dirichlet_eigenpairs(dim, n):
         assert np.linalg.norm(got - lam * mode) <= 1e-12 * abs(lam) * np.linalg.norm(mode) + 1e-9
 
 
+@pytest.mark.parametrize("dim,n,eps", [(2, 31, 0.5), (3, 15, 0.25)])
+def test_closed_form_csl_eigenpairs(dim, n, eps):
+    """Complex shifted Laplacian variant without stretching: the sine modes stay
+    eigenvectors and the shift moves every eigenvalue by -(1 + i eps) k^2 (Sec. 2:
+    the CSL spectrum is the Laplacian's translated by the shift), while H is unshifted."""
+    k = 9.0
+    lev = O.build_hierarchy(dim, n, 0.0, theta_gamma=0.0, ecs_frac=WF, k=k, csl_eps=eps)[0]
+    h = 1.0 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    for js in [(1,) * dim, (2, 5, 3)[:dim], (n,) * dim]:
+        mode = np.ones((n,) * dim)
+        lap = 0.0
+        for ax, j in enumerate(js):
+            shape = [1] * dim
+            shape[ax] = n
+            mode = mode * np.sin(j * np.pi * x).reshape(shape)
+            lap += 4.0 / h ** 2 * np.sin(j * np.pi * h / 2) ** 2
+        lam = lap - (1 + 1j * eps) * k * k
+        got = lev.apply(mode.astype(np.complex128))
+        assert np.linalg.norm(got - lam * mode) <= 1e-12 * abs(lam) * np.linalg.norm(mode) + 1e-9
+        got_h = lev.apply_h(mode.astype(np.complex128))
+        assert np.linalg.norm(got_h - (lap - k * k) * mode) <= 1e-12 * abs(lap) * np.linalg.norm(mode) + 1e-9
+
+
 def test_uniform_rotation_identity():
     """theta_beta = theta_gamma = theta: every spacing is h e^{i theta}, so the
     Laplacian part is e^{-2 i theta} times the real one (closed form)."""
