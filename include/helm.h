@@ -76,6 +76,10 @@ typedef struct {
   int precond_prec; /* HELM_C64 or HELM_C128                         [HELM_C64] */
   int restart;      /* outer FGMRES restart length m, 0 = none       [0] */
   int maxit;        /* max preconditioner applications per solve     [400] */
+  double csl_eps;   /* complex shift of the preconditioner: M = L - (1 + i csl_eps) phi
+                     * (Sec. 1, Sec. 2: the complex shifted Laplacian of Erlangga, Oosterlee
+                     * and Vuik); 0 = the complex stretched grid alone; with theta_beta = 0
+                     * and csl_eps > 0 the preconditioner is M^CSL.  Finite, >= 0.  [0] */
 } helm_opts;
 /* The Krylov basis length m = min(restart, maxit) (maxit without restart) is at most
  * HELM_MAX_BASIS; helm_setup returns HELM_EINVAL above it. */
@@ -95,9 +99,12 @@ typedef struct {
  *         (natural order), or NULL for a constant wavenumber `k` (phi = k^2).  The
  *         field is copied; coarse levels sample it at their nodes.
  *   theta_beta: CSG interior angle in radians, 0 <= theta_beta < pi/2 (Sec. 2).
- *   opts may be NULL (all defaults).
- * Errors: HELM_EINVAL (dim, n, angles, ecs_frac, opts out of range), HELM_ENOMEM,
- * HELM_ECUDA.  The call synchronises `stream` before returning. */
+ *   opts may be NULL (all defaults).  opts->csl_eps > 0 (constant k only) adds the
+ *         complex shift of the CSL variant: M = L - (1 + i csl_eps) k^2 on every level,
+ *         the stretched-grid angle applying as well (theta_beta = 0: pure CSL).
+ * Errors: HELM_EINVAL (dim, n, angles, ecs_frac, opts out of range, csl_eps with a
+ * phi field), HELM_ENOMEM, HELM_ECUDA.  The call synchronises `stream` before
+ * returning. */
 int helm_setup(const helm_grid* grid, const float* phi, double k, double theta_beta,
                const helm_opts* opts, void* stream, helm_handle** out);
 
@@ -229,7 +236,8 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes);
  * cudaMalloc/cudaFree.  The paper has no counterpart: this is an interface variant
  * of helm_precond_apply.
  *   grid, theta_beta, opts: as for helm_setup (constant wavenumber k only; opts may be
- *     NULL; restart and maxit are ignored; precond_prec selects the arithmetic).
+ *     NULL; restart and maxit are ignored; precond_prec selects the arithmetic;
+ *     csl_eps must be 0: HELM_EINVAL otherwise).
  *   r, z: device arrays of n^dim complex numbers in precision `prec`, natural order.
  * All working memory lives in one fixed 4 MiB device array inside the library, which
  * every GPU that loads the library holds until the process exits.  Grids whose

@@ -71,6 +71,13 @@ static int upload_level_coefficients(Handle* h, int l, double theta_beta, cudaSt
   HostLevel& L = h->lev[l];
   std::vector<cplx> a, d, c;
   stencil_coefficients(grid_spacings(L.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
+  // Complex shift of M (constant k): the diagonal's extra -i eps k^2 is spread over the
+  // d axes' diagonal coefficients (every point's diagonal adds one per axis), so the
+  // kernels' -phi stays real and nothing else changes.
+  if (h->csl_eps != 0.0) {
+    const cplx per_axis(0.0, -h->csl_eps * h->k * h->k / h->dim);
+    for (auto& v : d) v += per_axis;
+  }
   double2* c64 = reinterpret_cast<double2*>(h->stage + h->stage_coef[l]);
   for (int i = 0; i < L.n; ++i) {
     c64[i] = make_double2(a[i].real(), a[i].imag());
@@ -103,7 +110,7 @@ static int factor_coarsest(Handle* h, double theta_beta, cudaStream_t st) {
       for (int y = 0; y < Lc.n; ++y)
         for (int x = 0; x < Lc.n; ++x) phic[(z * Lc.n + y) * Lc.n + x] = pad[((size_t)z * Lc.P + y) * Lc.P + x];
   }
-  std::vector<cplx> A = dense_operator(h->dim, Lc.n, a, d, c, phic);
+  std::vector<cplx> A = dense_operator(h->dim, Lc.n, a, d, c, phic, cplx(1.0, h->csl_eps));
   std::vector<int> perm;
   if (!lu_factor(A, cm, perm)) { set_error("coarsest operator is singular"); return HELM_ENUMERIC; }
   double2* Ad = reinterpret_cast<double2*>(h->stage + h->stage_lu);
@@ -135,6 +142,7 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   h->prec = o.precond_prec ? o.precond_prec : HELM_C64;
   h->restart = o.restart > 0 ? o.restart : 0;
   h->maxit = o.maxit > 0 ? o.maxit : 400;
+  h->csl_eps = o.csl_eps;
   if (h->dim != 2 && h->dim != 3) { set_error("dim must be 2 or 3"); return HELM_EINVAL; }
   if (h->n < 1 || h->n > (h->dim == 2 ? 32767 : 2047)) { set_error("n out of range"); return HELM_EINVAL; }
   if (!(h->ecs > 0 && h->ecs < 0.5)) { set_error("ecs_frac must be in (0, 0.5)"); return HELM_EINVAL; }
@@ -143,6 +151,8 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   if (h->s > SMAX) { set_error("s must be in 1..4"); return HELM_EINVAL; }
   if (h->nu1 > 8 || h->nu2 > 8) { set_error("nu1, nu2 must be <= 8"); return HELM_EINVAL; }
   if (h->prec != HELM_C64 && h->prec != HELM_C128) { set_error("precond_prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
+  if (!(std::isfinite(h->csl_eps) && h->csl_eps >= 0.0)) { set_error("csl_eps must be finite and >= 0"); return HELM_EINVAL; }
+  if (h->csl_eps != 0.0 && phi) { set_error("the complex shift (csl_eps) needs a constant k"); return HELM_EINVAL; }
   if (!phi && !std::isfinite(k)) { set_error("k must be finite"); return HELM_EINVAL; }
   const std::vector<int> sizes = level_sizes(h->n, h->coarsest);
   const int nlev = (int)sizes.size();

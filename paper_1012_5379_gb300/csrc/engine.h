@@ -55,6 +55,7 @@ struct Handle {
   int dim = 2, n = 0, prec = HELM_C64;
   int nu1 = 1, nu2 = 1, s = 3, coarsest = 3, restart = 0, maxit = 400, m = 0;
   double theta_beta = 0, theta_gamma = 0.5, ecs = 0.125, k = 0;
+  double csl_eps = 0;             // complex shift of M: L - (1 + i csl_eps) phi
   bool has_phi = false;
   TileCfg cfg{8};
   std::vector<HostLevel> lev;

@@ -46,14 +46,14 @@ void stencil_coefficients(const std::vector<cplx>& sp, std::vector<cplx>& a, std
 
 // Dense matrix of M = sum_axes L_axis - diag(phi) on an n^dim grid (natural order).
 std::vector<cplx> dense_operator(int dim, int n, const std::vector<cplx>& a, const std::vector<cplx>& d,
-                                 const std::vector<cplx>& c, const std::vector<double>& phi) {
+                                 const std::vector<cplx>& c, const std::vector<double>& phi, cplx shift) {
   const int m = dim == 3 ? n * n * n : n * n;
   std::vector<cplx> A((size_t)m * m, cplx(0, 0));
   for (int z = 0; z < (dim == 3 ? n : 1); ++z)
     for (int y = 0; y < n; ++y)
       for (int x = 0; x < n; ++x) {
         const int row = (z * n + y) * n + x;
-        cplx diag = d[x] + d[y] + (dim == 3 ? d[z] : cplx(0, 0)) - phi[row];
+        cplx diag = d[x] + d[y] + (dim == 3 ? d[z] : cplx(0, 0)) - shift * phi[row];
         A[(size_t)row * m + row] += diag;
         auto add = [&](int xx, int yy, int zz, cplx v) {
           if (xx < 0 || yy < 0 || zz < 0 || xx >= n || yy >= n || zz >= n) return;

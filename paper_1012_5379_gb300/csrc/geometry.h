@@ -10,8 +10,9 @@ typedef std::complex<double> cplx;
 std::vector<cplx> grid_spacings(int n, double ecs, double theta_gamma, double theta_beta);
 void stencil_coefficients(const std::vector<cplx>& sp, std::vector<cplx>& a, std::vector<cplx>& d,
                           std::vector<cplx>& c);
+// Dense matrix of L - shift * diag(phi) on n^dim nodes (shift 1: CSG; 1 + i eps: CSL variant).
 std::vector<cplx> dense_operator(int dim, int n, const std::vector<cplx>& a, const std::vector<cplx>& d,
-                                 const std::vector<cplx>& c, const std::vector<double>& phi);
+                                 const std::vector<cplx>& c, const std::vector<double>& phi, cplx shift = cplx(1, 0));
 bool lu_factor(std::vector<cplx>& A, int m, std::vector<int>& perm);
 std::vector<int> level_sizes(int n, int coarsest);
 

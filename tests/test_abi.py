@@ -76,15 +76,36 @@ def test_setup_rejects_a_basis_longer_than_the_limit(lib):
                     ("theta_gamma", ctypes.c_double)]
 
     class Opts(ctypes.Structure):
-        _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")]
+        _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")] + \
+                   [("csl_eps", ctypes.c_double)]
     hdr = open(os.path.join(ROOT, "include", "helm.h")).read()
     limit = int(re.search(r"#define HELM_MAX_BASIS (\d+)", hdr).group(1))
     lib.helm_setup.restype = ctypes.c_int
     lib.helm_last_error.restype = ctypes.c_char_p
     out = ctypes.c_void_p()
     g = Grid(2, 15, 0.125, 0.5)
-    o = Opts(0, 0, 0, 0, 0, 0, limit + 1)
+    o = Opts(0, 0, 0, 0, 0, 0, limit + 1, 0.0)
     rc = lib.helm_setup(ctypes.byref(g), None, ctypes.c_double(1.0), ctypes.c_double(0.3), ctypes.byref(o), None,
                         ctypes.byref(out))
     assert rc == -1 and out.value is None
     assert b"HELM_MAX_BASIS" in lib.helm_last_error()
+
+
+def test_setup_rejects_a_negative_complex_shift(lib):
+    """csl_eps (the complex shifted Laplacian variant's shift) must be finite and >= 0."""
+    class Grid(ctypes.Structure):
+        _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
+                    ("theta_gamma", ctypes.c_double)]
+
+    class Opts(ctypes.Structure):
+        _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")] + \
+                   [("csl_eps", ctypes.c_double)]
+    lib.helm_setup.restype = ctypes.c_int
+    lib.helm_last_error.restype = ctypes.c_char_p
+    out = ctypes.c_void_p()
+    g = Grid(2, 15, 0.125, 0.5)
+    o = Opts(0, 0, 0, 0, 0, 0, 0, -0.5)
+    rc = lib.helm_setup(ctypes.byref(g), None, ctypes.c_double(1.0), ctypes.c_double(0.0), ctypes.byref(o), None,
+                        ctypes.byref(out))
+    assert rc == -1 and out.value is None
+    assert b"csl_eps" in lib.helm_last_error()

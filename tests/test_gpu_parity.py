@@ -64,6 +64,56 @@ def test_operator_apply(helm, dim, n, prec, field):
         assert rel(wt.cpu().numpy(), want) < tol
 
 
+# ------------------------------------------------------------------ complex shifted Laplacian variant
+@pytest.mark.parametrize("dim,n,prec,tb,eps", [(2, 63, "c128", 0.0, 0.5), (3, 15, "c128", 0.0, 0.5),
+                                               (2, 127, "c64", 0.0, 0.5), (2, 63, "c128", 0.2, 0.25)])
+def test_csl_operator_and_vcycle(helm, dim, n, prec, tb, eps):
+    """M = L - (1 + i eps) k^2: the CSL shift alone (theta_beta = 0) or combined with
+    the stretched grid; the operators and one V-cycle against the oracle's."""
+    k = 0.15 * (n + 1)
+    levels = O.build_hierarchy(dim, n, tb, TG, WF, k=k, csl_eps=eps)
+    h = helm.Handle(dim, n, tb, k=k, precision=prec, csl_eps=eps)
+    v = I.random_source(dim, n, 7)
+    for which in "MH":
+        want = levels[0].apply(v) if which == "M" else levels[0].apply_h(v)
+        vt = dev(v, prec)
+        wt = torch.empty_like(vt)
+        h.apply_operator(vt, wt, which)
+        assert rel(wt.cpu().numpy(), want) < (1e-13 if prec == "c128" else 1e-6), which
+    want = O.vcycle(levels, v)
+    vt = dev(v, prec)
+    zt = torch.empty_like(vt)
+    h.precond_apply(vt, zt)
+    assert rel(zt.cpu().numpy(), want) < (1e-11 if prec == "c128" else 5e-5)
+
+
+def test_csl_solve(helm):
+    """FGMRES preconditioned by the CSL V-cycle (theta_beta = 0, eps = 0.5) on 127^2,
+    k = 20: true residual under the oracle's H, iterations within +10% (+1)."""
+    n, k, eps, tol = 127, 20.0, 0.5, 1e-6
+    b = I.random_source(2, n, 33)
+    levels = O.build_hierarchy(2, n, 0.0, TG, WF, k=k, csl_eps=eps)
+    _, io = O.fgmres(levels[0].apply_h, lambda v: O.vcycle(levels, v), b, tol=tol, restart=0, maxit=200)
+    h = helm.Handle(2, n, 0.0, k=k, precision="c64", csl_eps=eps)
+    bt = dev(b)
+    xt = torch.zeros_like(bt)
+    info = h.solve(bt, xt, tol)
+    x = xt.cpu().numpy()
+    assert info.status == 0
+    assert np.linalg.norm(b - levels[0].apply_h(x)) / np.linalg.norm(b) <= tol * 1.0001
+    assert info.iters <= int(1.1 * io.iters) + 1
+
+
+def test_csl_argument_checks(helm):
+    """A negative or non-finite shift, or a shift with a k field, is refused."""
+    for bad in (-0.1, float("nan")):
+        with pytest.raises(helm.HelmError):
+            helm.Handle(2, 31, 0.0, k=5.0, csl_eps=bad)
+    phi = torch.full((31, 31), 25.0, dtype=torch.float32, device="cuda")
+    with pytest.raises(helm.HelmError):
+        helm.Handle(2, 31, 0.0, phi=phi, csl_eps=0.5)
+
+
 # ------------------------------------------------------------------ one V-cycle
 VC_CASES = [
     (2, 15, "c128"), (2, 31, "c128"), (2, 63, "c128"), (2, 127, "c128"), (2, 255, "c128"),
