@@ -137,6 +137,18 @@ def traffic_for(kernel_class: str, alg_bytes_per_launch: float):
     return rec["dram_bytes"] / rec["algorithmic_bytes"] * alg_bytes_per_launch
 
 
+def reduce_over_ranks(seconds, work, device):
+    """Whole-job figures of a multi-rank run: the slowest rank's time and the work of
+    all ranks (weak scaling: every rank solves its own replica of the step)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds, 0.0], dtype=torch.float64, device=device)
+    w = torch.tensor([work, 0.0], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t[0].item()), float(w[0].item())
+
+
 def vcycle_hbm(classes, peak_gbs):
     """Algorithmic bandwidth of the V-cycle kernel classes (vc.*): the library's
     algorithmic bytes of each class over its CUDA-event time, and their total, as a
@@ -229,11 +241,7 @@ def run_ours(args, rank, world, local_rank):
     pts = float(N * N)
     work = pts * sum(sum(i) for i in all_iters)
     if world > 1:
-        t = torch.tensor([ms_total, work], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        ms_total, work = float(tmax[0].item()), float(t[1].item())
+        ms_total, work = reduce_over_ranks(ms_total, work, dev)
     value = work / (ms_total * 1e-3) / 1e6
 
     # roofline of the dominant kernel class, live from the timed region
@@ -306,10 +314,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         et = time.perf_counter() - t0
         if world > 1:
-            t = torch.tensor([et, ework], dtype=torch.float64, device=dev)
-            dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-            et, ework = float(t[0].item()), float(t[1].item())
+            et, ework = reduce_over_ranks(et, ework, dev)
         e2e = {"value": ework / et / 1e6, "unit": UNIT, "h2d_bytes_per_step": len(BETAS) * N * N * 16,
                "d2h_bytes_per_step": len(BETAS) * N * N * 16, "steps": args.e2e_steps,
                "api": "helm_batch_solve_host"}
