@@ -26,6 +26,10 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
   unpinned.
 * ``fgmres``: pinned (sparse direct solve, manufactured solution, paper Table 2
   iteration counts as a soft band).
+* ``polysmoother`` (the third-degree polynomial smoother of Sec. 4): pinned by the
+  paper's Fig. ex1 (which phi maps the spectrum inside the unit circle), the critical
+  angle of Fig. critical_parameters and the stability of Fig. hierarchy_spectrum_smoother;
+  its V-cycle ``vcycle_poly`` has no printed value beyond those and is unpinned as a cycle.
 """
 from .helmholtz import (  # noqa: F401
     Level,
