@@ -229,6 +229,18 @@ int helm_workspace_bytes(const helm_handle* h, size_t* bytes);
 /* Levels of the hierarchy and their sizes (sizes may be NULL). */
 int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes);
 
+/* The third-degree polynomial smoother (Sec. 4) of one level: real spacing h,
+ * constant k, CSG angle theta_beta, layer angle theta_gamma, dimension dim.  p has
+ * p(0) = 1, p(t1) = p(t2) = 0 and p(t0) = e^{i phi} at the vertices of the spectrum's
+ * bounding triangle (Prop. 3.1); phi is chosen by the first- and second-order
+ * stability conditions (Sec. 4.3, 4.4; the midpoint of the longest admissible arc on
+ * a 0.05 degree grid, 0 where the first-order condition holds for every phi).
+ * Writes phi (radians) and w[0..5] = re, im of the three Richardson weights of
+ * p(t) = (1 - w1 t)(1 - w2 t)(1 - w3 t).  Host only (no device work).  HELM_EINVAL if
+ * no stable polynomial exists (theta_beta too small for this k and h, Sec. 4.5). */
+int helm_poly_smoother(double k, double h, double theta_beta, double theta_gamma, int dim, double* phi,
+                       double* w);
+
 /* One V(nu1, nu2) cycle, z ~ (M^CSG)^{-1} r, for a small grid without allocating any
  * device memory.  For callers that cannot let a library call cudaMalloc: programs
  * whose device memory is reserved up front by a pooling allocator, and

@@ -9,7 +9,10 @@
 #include <vector>
 #include <string>
 
+#include <cmath>
+
 #include "../../include/helm.h"
+#include "geometry.h"
 #include "engine.h"
 #include "profiler.h"
 #include <cstring>
@@ -204,6 +207,28 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes) {
   if (sizes)
     for (int i = 0; i < (int)lev.size() && i < max_sizes; ++i) sizes[i] = lev[i].n;
   return HELM_OK;
+}
+
+int helm_poly_smoother(double k, double h, double theta_beta, double theta_gamma, int dim, double* phi,
+                       double* w) {
+  HELM_GUARD({
+    if (!phi || !w) { helm::set_error("NULL argument"); return HELM_EINVAL; }
+    if (!(std::isfinite(k) && h > 0 && std::isfinite(h) && theta_beta >= 0 && theta_gamma > theta_beta &&
+          theta_gamma < M_PI / 2 && (dim == 2 || dim == 3))) {
+      helm::set_error("need finite k, h > 0, 0 <= theta_beta < theta_gamma < pi/2, dim 2 or 3");
+      return HELM_EINVAL;
+    }
+    helm::cplx ws[3];
+    if (!helm::poly_smoother(k, h, theta_beta, theta_gamma, dim, phi, ws)) {
+      helm::set_error("no stable third-degree polynomial smoother for this k, h and theta_beta");
+      return HELM_EINVAL;
+    }
+    for (int j = 0; j < 3; ++j) {
+      w[2 * j] = ws[j].real();
+      w[2 * j + 1] = ws[j].imag();
+    }
+    return HELM_OK;
+  })
 }
 
 int helm_precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, const helm_opts* opts,

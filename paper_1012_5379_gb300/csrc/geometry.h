@@ -14,6 +14,10 @@ void stencil_coefficients(const std::vector<cplx>& sp, std::vector<cplx>& a, std
 std::vector<cplx> dense_operator(int dim, int n, const std::vector<cplx>& a, const std::vector<cplx>& d,
                                  const std::vector<cplx>& c, const std::vector<double>& phi, cplx shift = cplx(1, 0));
 bool lu_factor(std::vector<cplx>& A, int m, std::vector<int>& perm);
+// Third-degree polynomial smoother of a level (Sec. 4): its mapping angle phi and the
+// weights w of the three Richardson steps x <- x + w_j (b - M x); false if no stable
+// polynomial exists under the first- and second-order conditions.
+bool poly_smoother(double k, double h, double theta_beta, double theta_gamma, int dim, double* phi, cplx w[3]);
 std::vector<int> level_sizes(int n, int coarsest);
 
 }  // namespace helm

@@ -31,7 +31,8 @@ _STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ENOCONV
 
 # names declared in include/helm.h (checked by the CPU test suite)
 EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_operator", "helm_solve",
-           "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_last_error",
+           "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_poly_smoother",
+           "helm_last_error",
            "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc",
            "helm_batch_solve_host", "helm_serve_start", "helm_serve_submit", "helm_serve_poll", "helm_serve_wait",
            "helm_serve_stats", "helm_serve_stop")
@@ -107,6 +108,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_workspace_bytes.restype = ip
     lib.helm_levels.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
     lib.helm_levels.restype = ip
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.helm_poly_smoother.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ip, dp,
+                                       dp]
+    lib.helm_poly_smoother.restype = ip
     lib.helm_last_error.argtypes = []
     lib.helm_last_error.restype = ctypes.c_char_p
     lib.helm_precond_apply_noalloc.argtypes = [ctypes.POINTER(helm_grid), dp, dp, ctypes.POINTER(helm_opts), vp, vp,
@@ -252,6 +257,15 @@ def precond_apply_noalloc(dim: int, n: int, theta_beta: float, k: float, r, z, t
     _check(load().helm_precond_apply_noalloc(ctypes.byref(g), float(k), float(theta_beta), ctypes.byref(o),
                                              _ptr(r), _ptr(z), prec, _stream(stream)))
     return z
+
+
+def poly_smoother(k: float, h: float, theta_beta: float, theta_gamma: float, dim: int):
+    """The third-degree polynomial smoother of a level (Sec. 4): (phi, [w1, w2, w3])."""
+    phi = ctypes.c_double()
+    w = (ctypes.c_double * 6)()
+    _check(load().helm_poly_smoother(float(k), float(h), float(theta_beta), float(theta_gamma), int(dim),
+                                     ctypes.byref(phi), w))
+    return phi.value, [complex(w[2 * j], w[2 * j + 1]) for j in range(3)]
 
 
 def launch_count() -> int:
