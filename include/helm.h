@@ -80,7 +80,13 @@ typedef struct {
                      * (Sec. 1, Sec. 2: the complex shifted Laplacian of Erlangga, Oosterlee
                      * and Vuik); 0 = the complex stretched grid alone; with theta_beta = 0
                      * and csl_eps > 0 the preconditioner is M^CSL.  Finite, >= 0.  [0] */
+  int smoother;     /* HELM_SMOOTHER_GMRES: GMRES(s) sweeps (Sec. 3);
+                     * HELM_SMOOTHER_POLY: the third-degree polynomial smoother of Sec. 4
+                     * (three Richardson steps per sweep, weights from helm_poly_smoother per
+                     * level; constant k, csl_eps = 0, s ignored).  [HELM_SMOOTHER_GMRES] */
 } helm_opts;
+#define HELM_SMOOTHER_GMRES 0
+#define HELM_SMOOTHER_POLY 1
 /* The Krylov basis length m = min(restart, maxit) (maxit without restart) is at most
  * HELM_MAX_BASIS; helm_setup returns HELM_EINVAL above it. */
 #define HELM_MAX_BASIS 1536
@@ -236,7 +242,8 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes);
  * stability conditions (Sec. 4.3, 4.4; the midpoint of the longest admissible arc on
  * a 0.05 degree grid, 0 where the first-order condition holds for every phi).
  * Writes phi (radians) and w[0..5] = re, im of the three Richardson weights of
- * p(t) = (1 - w1 t)(1 - w2 t)(1 - w3 t).  Host only (no device work).  HELM_EINVAL if
+ * p(t) = (1 - w1 t)(1 - w2 t)(1 - w3 t), ordered by real, then imaginary part (the
+ * order the V-cycle applies them in).  Host only (no device work).  HELM_EINVAL if
  * no stable polynomial exists (theta_beta too small for this k and h, Sec. 4.5). */
 int helm_poly_smoother(double k, double h, double theta_beta, double theta_gamma, int dim, double* phi,
                        double* w);
@@ -249,7 +256,7 @@ int helm_poly_smoother(double k, double h, double theta_beta, double theta_gamma
  * of helm_precond_apply.
  *   grid, theta_beta, opts: as for helm_setup (constant wavenumber k only; opts may be
  *     NULL; restart and maxit are ignored; precond_prec selects the arithmetic;
- *     csl_eps must be 0: HELM_EINVAL otherwise).
+ *     csl_eps must be 0 and smoother HELM_SMOOTHER_GMRES: HELM_EINVAL otherwise).
  *   r, z: device arrays of n^dim complex numbers in precision `prec`, natural order.
  * All working memory lives in one fixed 4 MiB device array inside the library, which
  * every GPU that loads the library holds until the process exits.  Grids whose

@@ -17,7 +17,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["vcycle_c64.cu", "vcycle_c128.cu", "outer.cu", "convert.cu", "noalloc.cu"]
 CPP = ["engine.cpp", "geometry.cpp", "capi.cpp", "profiler.cpp", "serve.cpp", "tma.cpp"]
-HEADERS = ["helm_internal.h", "device_common.cuh", "vcycle.cuh", "tiles.cuh", "vcycle_launch.cuh", "engine.h", "geometry.h",
+HEADERS = ["poly.h", "helm_internal.h", "device_common.cuh", "vcycle.cuh", "tiles.cuh", "vcycle_launch.cuh", "engine.h", "geometry.h",
            "profiler.h"]
 
 

@@ -14,6 +14,7 @@
 #include <sstream>
 
 #include "geometry.h"
+#include "poly.h"
 #include "profiler.h"
 
 namespace helm {
@@ -122,6 +123,26 @@ static int factor_coarsest(Handle* h, double theta_beta, cudaStream_t st) {
   return HELM_OK;
 }
 
+// Richardson weights of the Sec. 4 polynomial smoother on every smoothed level (all
+// but the coarsest); a level of n interior nodes has real spacing 1 / (n + 1).
+static int compute_poly_weights(Handle* h, const std::vector<int>& sizes) {
+  std::vector<std::array<cplx, 3>> ws(sizes.size() > 0 ? sizes.size() - 1 : 0);
+  for (size_t l = 0; l + 1 < sizes.size(); ++l) {
+    double phi = 0.0;
+    cplx w[3];
+    if (!poly_smoother(h->k, 1.0 / (sizes[l] + 1), h->theta_beta, h->theta_gamma, h->dim, &phi, w)) {
+      std::ostringstream msg;
+      msg << "no stable third-degree polynomial smoother on the level n = " << sizes[l]
+          << " (theta_beta too small for this k, Sec. 4.5)";
+      set_error(msg.str());
+      return HELM_EINVAL;
+    }
+    for (int j = 0; j < 3; ++j) ws[l][j] = w[j];
+  }
+  h->polyw.swap(ws);
+  return HELM_OK;
+}
+
 int setup_handle(const helm_grid* grid, const float* phi, double k, double theta_beta, const helm_opts* opts,
                  cudaStream_t st, Handle** out) {
   if (!grid || !out) { set_error("grid and out must not be NULL"); return HELM_EINVAL; }
@@ -143,6 +164,7 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   h->restart = o.restart > 0 ? o.restart : 0;
   h->maxit = o.maxit > 0 ? o.maxit : 400;
   h->csl_eps = o.csl_eps;
+  h->smoother = o.smoother;
   if (h->dim != 2 && h->dim != 3) { set_error("dim must be 2 or 3"); return HELM_EINVAL; }
   if (h->n < 1 || h->n > (h->dim == 2 ? 32767 : 2047)) { set_error("n out of range"); return HELM_EINVAL; }
   if (!(h->ecs > 0 && h->ecs < 0.5)) { set_error("ecs_frac must be in (0, 0.5)"); return HELM_EINVAL; }
@@ -153,6 +175,16 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   if (h->prec != HELM_C64 && h->prec != HELM_C128) { set_error("precond_prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
   if (!(std::isfinite(h->csl_eps) && h->csl_eps >= 0.0)) { set_error("csl_eps must be finite and >= 0"); return HELM_EINVAL; }
   if (h->csl_eps != 0.0 && phi) { set_error("the complex shift (csl_eps) needs a constant k"); return HELM_EINVAL; }
+  if (h->smoother != HELM_SMOOTHER_GMRES && h->smoother != HELM_SMOOTHER_POLY) {
+    set_error("smoother must be HELM_SMOOTHER_GMRES or HELM_SMOOTHER_POLY");
+    return HELM_EINVAL;
+  }
+  if (h->smoother == HELM_SMOOTHER_POLY && (phi || h->csl_eps != 0.0 || !(theta_beta < h->theta_gamma))) {
+    set_error("the polynomial smoother needs a constant k, csl_eps = 0 and theta_beta < theta_gamma");
+    return HELM_EINVAL;
+  }
+  // the polynomial smoother's steps alternate through p_0 and p_1
+  if (h->smoother == HELM_SMOOTHER_POLY && h->s < 2) h->s = 2;
   if (!phi && !std::isfinite(k)) { set_error("k must be finite"); return HELM_EINVAL; }
   const std::vector<int> sizes = level_sizes(h->n, h->coarsest);
   const int nlev = (int)sizes.size();
@@ -161,6 +193,7 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     set_error("coarsest grid has more than 128 unknowns: n+1 must be divisible by a larger power of two, or lower coarsest_n");
     return HELM_EINVAL;
   }
+  if (h->smoother == HELM_SMOOTHER_POLY) TRY(compute_poly_weights(h.get(), sizes));
   h->m = h->restart > 0 ? std::min(h->restart, h->maxit) : h->maxit;
   if (h->m > HELM_MAX_BASIS) {
     set_error("Krylov basis length min(restart, maxit) exceeds HELM_MAX_BASIS");
@@ -357,6 +390,7 @@ static OuterDev<C> make_outerdev(const Handle& h) {
 template <typename C>
 struct Group {
   int dim = 2, nu1 = 1, nu2 = 1, s = 3, Lmax = 0, tc = 0, nprob = 0;
+  int smoother = HELM_SMOOTHER_GMRES;
   TileCfg cfg{8};
   std::vector<Handle*> hs;
   struct Depth {
@@ -364,6 +398,7 @@ struct Group {
     bool tma = true;  // every problem at this depth has TMA maps
     TileCfg cfg{8};
     LevelDev<C>* d = nullptr;
+    C* pw = nullptr;  // polynomial smoother: three Richardson weights per problem
   };
   std::vector<Depth> depth;      // t < tc
   LevelDev<C>* dcoarse = nullptr;  // [prob][Lmax - tc]
@@ -423,12 +458,13 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   g->nu1 = h0.nu1;
   g->nu2 = h0.nu2;
   g->s = h0.s;
+  g->smoother = h0.smoother;
   g->cfg = h0.cfg;
   for (int p = 0; p < count; ++p) {
     const Handle& h = *hs[p];
     if (h.dim != h0.dim || h.prec != h0.prec || h.nu1 != h0.nu1 || h.nu2 != h0.nu2 || h.s != h0.s ||
-        h.lev.back().n != h0.lev.back().n) {
-      set_error("batched problems must share dim, precision, nu1, nu2, s and the coarsest size");
+        h.smoother != h0.smoother || h.lev.back().n != h0.lev.back().n) {
+      set_error("batched problems must share dim, precision, nu1, nu2, s, the smoother and the coarsest size");
       return HELM_EINVAL;
     }
     g->Lmax = std::max(g->Lmax, (int)h.lev.size());
@@ -451,6 +487,9 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   // the split depends on the level sizes only, never on the other problems: a problem
   // whose finest level is already coarse runs its whole cycle in the coarse kernel
   g->tc = std::min(tthr, g->Lmax - 1);
+  // the polynomial smoother runs every level but the coarsest grid-wide; the coarse
+  // kernel then only solves the coarsest level
+  if (g->smoother == HELM_SMOOTHER_POLY) g->tc = g->Lmax - 1;
   g->nlev_c = g->Lmax - g->tc;
   (void)maxoff;
   {
@@ -466,12 +505,21 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
     if (hs[p]->cfg.rows != g->cfg.rows && off[p] == 0) g->cfg = hs[p]->cfg;
   // host descriptor arrays
   std::vector<std::vector<LevelDev<C>>> dep(g->tc);
+  std::vector<std::vector<C>> pws(g->tc);
   g->depth.resize(g->tc);
   for (int t = 0; t < g->tc; ++t) {
     for (int p = 0; p < count; ++p) {
       if (off[p] > t) continue;
       const int l = t - off[p];
       dep[t].push_back(make_leveldev<C>(*hs[p], l));
+      if (g->smoother == HELM_SMOOTHER_POLY)
+        for (int j = 0; j < 3; ++j) {
+          const cplx wj = hs[p]->polyw[l][j];
+          C v;
+          v.x = (decltype(v.x))wj.real();
+          v.y = (decltype(v.y))wj.imag();
+          pws[t].push_back(v);
+        }
       typename Group<C>::Depth& D = g->depth[t];
       const HostLevel& L = hs[p]->lev[l];
       if (D.cnt > 0 && D.n != L.n) { set_error("batched problems must have n + 1 a power of two"); return HELM_EINVAL; }
@@ -527,7 +575,7 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   }
   // one device allocation for every descriptor array
   size_t bytes = 0;
-  for (int t = 0; t < g->tc; ++t) bytes += dep[t].size() * sizeof(LevelDev<C>);
+  for (int t = 0; t < g->tc; ++t) bytes += dep[t].size() * sizeof(LevelDev<C>) + pws[t].size() * sizeof(C) + 64;
   bytes += coarse.size() * sizeof(LevelDev<C>) + lus.size() * sizeof(CoarseLU) + lev0.size() * sizeof(LevelDev<C>);
   for (auto& v : subs) bytes += v.size() * sizeof(OuterDev<C>);
   bytes += 64 * (g->tc + subs.size() + 4);
@@ -575,6 +623,8 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
     return dst;
   };
   for (int t = 0; t < g->tc; ++t) g->depth[t].d = (LevelDev<C>*)put(dep[t].data(), dep[t].size() * sizeof(LevelDev<C>));
+  for (int t = 0; t < g->tc; ++t)
+    if (!pws[t].empty()) g->depth[t].pw = (C*)put(pws[t].data(), pws[t].size() * sizeof(C));
   g->dcoarse = (LevelDev<C>*)put(coarse.data(), coarse.size() * sizeof(LevelDev<C>));
   g->dlu = (CoarseLU*)put(lus.data(), lus.size() * sizeof(CoarseLU));
   g->lev0 = (LevelDev<C>*)put(lev0.data(), lev0.size() * sizeof(LevelDev<C>));
@@ -587,8 +637,63 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
 // One V(nu1, nu2) cycle from a zero guess on every problem of the group (Sec. 3.1).
 // Algorithmic bytes per launch count every vector the pass must read or write once
 // (E bytes per complex value), plus 4 bytes per point for a phi field.
+// One V(nu1, nu2) cycle with the polynomial smoother of Sec. 4: every level but the
+// coarsest grid-wide.  A sweep is three Richardson steps; the steps of a sweep go
+// through the level's p_0 / p_1 vectors and the last one lands in x_a (pre-smoothing,
+// the prolongation's input) or x_b (post-smoothing, the level's output).
+template <typename C>
+static void run_vcycle_poly(const Group<C>& g, cudaStream_t st) {
+  const int dim = g.dim;
+  const double E = sizeof(C);
+  const double cf = 1.0 / (dim == 3 ? 8.0 : 4.0);
+  auto sweeps = [&](const typename Group<C>::Depth& D, int nsw, int first_src, int last_dst, bool fine) {
+    const double pts = (double)D.cnt * (dim == 3 ? (double)(D.n + 1) * (D.n + 1) * (D.n + 1) : (double)(D.n + 1) * (D.n + 1));
+    const int steps = 3 * nsw;
+    for (int k = 0; k < steps; ++k) {
+      const int src = k == 0 ? first_src : (k % 2 == 1 ? POLY_P0 : POLY_P1);
+      const int dst = k == steps - 1 ? last_dst : (k % 2 == 0 ? POLY_P0 : POLY_P1);
+      Launch L(fine ? "vc.poly.l0" : "vc.poly.lc", st, pts * E * (src == POLY_NONE ? 2.0 : 3.0), 0);
+      launch_poly_step<C>(dim, D.d, D.pw, D.cnt, D.nflat, src, dst, k % 3, st);
+    }
+  };
+  for (int t = 0; t < g.tc; ++t) {
+    const auto& D = g.depth[t];
+    const double pts = (double)D.cnt * (dim == 3 ? (double)(D.n + 1) * (D.n + 1) * (D.n + 1) : (double)(D.n + 1) * (D.n + 1));
+    const bool fine = (t == 0);
+    if (g.nu1 == 0) {
+      Launch L(fine ? "vc.poly.l0" : "vc.poly.lc", st, pts * E, 0);
+      launch_poly_step<C>(dim, D.d, D.pw, D.cnt, D.nflat, POLY_NONE, POLY_XA, -1, st);  // x_a = 0
+    } else {
+      sweeps(D, g.nu1, POLY_NONE, POLY_XA, fine);
+    }
+    Launch L(fine ? "vc.restrict.l0" : "vc.restrict.lc", st, pts * E * (3.0 + cf), 0, 2);
+    launch_poly_restrict<C>(dim, D.d, D.cnt, D.nflat, POLY_XA, st);
+  }
+  {
+    Launch L("vc.coarse", st, 0, 0);
+    if (g.coarse_smem > 0)
+      launch_coarse_smem<C>(dim, g.dcoarse, g.nlev_c, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, g.coarse_smem, st);
+    else
+      launch_coarse_cluster<C>(dim, g.dcoarse, g.nlev_c, g.dlu, g.nprob, g.nu1, g.nu2, st);
+  }
+  for (int t = g.tc - 1; t >= 0; --t) {
+    const auto& D = g.depth[t];
+    const double pts = (double)D.cnt * (dim == 3 ? (double)(D.n + 1) * (D.n + 1) * (D.n + 1) : (double)(D.n + 1) * (D.n + 1));
+    const bool fine = (t == 0);
+    {
+      Launch L(fine ? "vc.prolong.l0" : "vc.prolong.lc", st, pts * E * (2.0 + cf), 0);
+      launch_prolong<C>(dim, false, D.d, D.cnt, D.nflat, D.cfg, st);  // x_b = x_a + P e_c
+    }
+    if (g.nu2 > 0) sweeps(D, g.nu2, POLY_XB, POLY_XB, fine);
+  }
+}
+
 template <typename C>
 static void run_vcycle(const Group<C>& g, cudaStream_t st) {
+  if (g.smoother == HELM_SMOOTHER_POLY) {
+    run_vcycle_poly<C>(g, st);
+    return;
+  }
   const int dim = g.dim;
   const double E = sizeof(C);
   const double cf = 1.0 / (dim == 3 ? 8.0 : 4.0);
@@ -1123,6 +1228,19 @@ int retarget_handle(Handle* h, double k, double theta_beta, cudaStream_t st) {
     return HELM_EINVAL;
   }
   if (h->has_phi) { set_error("a handle built with a phi field cannot be retargeted"); return HELM_EINVAL; }
+  if (h->smoother == HELM_SMOOTHER_POLY) {
+    const double k0 = h->k, tb0 = h->theta_beta;
+    h->k = k;
+    h->theta_beta = theta_beta;
+    std::vector<int> sizes;
+    for (const auto& L : h->lev) sizes.push_back(L.n);
+    const int rc = compute_poly_weights(h, sizes);
+    if (rc != HELM_OK) {
+      h->k = k0;
+      h->theta_beta = tb0;
+      return rc;
+    }
+  }
   h->k = k;
   h->theta_beta = theta_beta;
   for (int l = 0; l < (int)h->lev.size(); ++l) {

@@ -3,6 +3,8 @@
 #include <sstream>
 #include <string>
 #include <utility>
+#include <array>
+#include <complex>
 #include <vector>
 
 #include "../../include/helm.h"
@@ -56,6 +58,8 @@ struct Handle {
   int nu1 = 1, nu2 = 1, s = 3, coarsest = 3, restart = 0, maxit = 400, m = 0;
   double theta_beta = 0, theta_gamma = 0.5, ecs = 0.125, k = 0;
   double csl_eps = 0;             // complex shift of M: L - (1 + i csl_eps) phi
+  int smoother = 0;               // HELM_SMOOTHER_GMRES or HELM_SMOOTHER_POLY
+  std::vector<std::array<std::complex<double>, 3>> polyw;  // Richardson weights per smoothed level
   bool has_phi = false;
   TileCfg cfg{8};
   std::vector<HostLevel> lev;

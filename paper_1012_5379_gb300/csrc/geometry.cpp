@@ -220,6 +220,10 @@ bool poly_smoother(double k, double h, double theta_beta, double theta_gamma, in
     if (moved < 1e-15) break;
   }
   for (int i = 0; i < 3; ++i) w_out[i] = 1.0 / (t0 + s[i]);
+  // a fixed order (real part, then imaginary part): the steps commute in exact arithmetic
+  std::sort(w_out, w_out + 3, [](const cplx& a, const cplx& b) {
+    return a.real() < b.real() || (a.real() == b.real() && a.imag() < b.imag());
+  });
   *phi_out = phi;
   return true;
 }

@@ -290,6 +290,7 @@ int precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, co
   if (s > SMAX || nu1 > 8 || nu2 > 8) { set_error("s must be in 1..4 and nu1, nu2 <= 8"); return HELM_EINVAL; }
   if (iprec != HELM_C64 && iprec != HELM_C128) { set_error("precond_prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
   if (o.csl_eps != 0.0) { set_error("the allocation-free entry point has no complex shift (csl_eps must be 0)"); return HELM_EINVAL; }
+  if (o.smoother != HELM_SMOOTHER_GMRES) { set_error("the allocation-free entry point smooths with GMRES(s) only"); return HELM_EINVAL; }
   return iprec == HELM_C128
              ? run_noalloc<double2>(grid, k, theta_beta, nu1, nu2, s, coarsest, r, z, prec, st)
              : run_noalloc<float2>(grid, k, theta_beta, nu1, nu2, s, coarsest, r, z, prec, st);

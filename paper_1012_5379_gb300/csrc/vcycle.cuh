@@ -666,6 +666,115 @@ __device__ void coarse_cycle(Team& team, const LevelDev<C>* Ls, int nlev, const 
 }
 
 
+// ------------------------------------------------------------------ polynomial smoother (Sec. 4)
+template <typename C>
+__device__ __forceinline__ C* poly_vec(const LevelDev<C>& L, int sel) {
+  switch (sel) {
+    case 1: return L.xa;
+    case 2: return L.xb;
+    case 3: return L.p[0];
+    case 4: return L.p[1];
+    default: return nullptr;
+  }
+}
+
+// Padded coordinates of flat index i (64-bit: the largest levels exceed 2^32 points).
+__device__ __forceinline__ void flat_coords(size_t i, int P, int dim, int& x, int& y, int& z) {
+  const size_t q = i / (size_t)P;
+  x = (int)(i - q * (size_t)P);
+  if (dim == 3) {
+    const size_t zz = q / (size_t)P;
+    y = (int)(q - zz * (size_t)P);
+    z = (int)zz;
+  } else {
+    y = (int)q;
+    z = 0;
+  }
+}
+
+// One Richardson step of the polynomial smoother: dst = src + w (b - M src), zero at
+// the padding; src POLY_NONE is the zero vector (dst = w b); wsel < 0 writes zero.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_poly_step(const LevelDev<C>* __restrict__ levs, const C* __restrict__ pw, int ntiles, int dim, int src, int dst,
+            int wsel) {
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  pdl_wait();
+  const int n = L.n, P = L.P;
+  const C w = wsel >= 0 ? pw[3 * prob + wsel] : czero<C>();
+  const C* xin = poly_vec(L, src);
+  C* xout = poly_vec(L, dst);
+  const C* b = L.b;
+  const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
+  for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < npts; i += (size_t)ntiles * blockDim.x) {
+    int x, y, z;
+    flat_coords(i, P, dim, x, y, z);
+    C v = czero<C>();
+    if (wsel >= 0 && inside(x, y, z, n)) {
+      C mv = czero<C>(), xi = czero<C>();
+      if (xin) {
+        cblock_stencil_apply(L, xin, x, y, z, dim, mv);
+        xi = xin[i];
+      }
+      v = cadd(xi, cmul(w, csub(b[i], mv)));
+    }
+    xout[i] = v;
+  }
+}
+
+// r0 = b - M src on a level (src POLY_NONE: r0 = b), zero at the padding.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_poly_residual(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int src) {
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  pdl_wait();
+  const int n = L.n, P = L.P;
+  const C* xin = poly_vec(L, src);
+  const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
+  for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < npts; i += (size_t)ntiles * blockDim.x) {
+    int x, y, z;
+    flat_coords(i, P, dim, x, y, z);
+    C r = czero<C>();
+    if (inside(x, y, z, n)) {
+      C mv = czero<C>();
+      if (xin) cblock_stencil_apply(L, xin, x, y, z, dim, mv);
+      r = csub(L.b[i], mv);
+    }
+    L.r0[i] = r;
+  }
+}
+
+// b_c = full weighting of r0 ((1/4, 1/2, 1/4) per axis around fine node 2I + 1), zero at
+// the coarse padding.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_poly_fw(const LevelDev<C>* __restrict__ levs, int ntiles, int dim) {
+  typedef typename CT<C>::R R;
+  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const LevelDev<C>& L = levs[prob];
+  pdl_wait();
+  const int n = L.n, P = L.P, nc = L.nc, Pc = L.Pc;
+  const size_t ncpts = dim == 3 ? (size_t)Pc * Pc * Pc : (size_t)Pc * Pc;
+  for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < ncpts; i += (size_t)ntiles * blockDim.x) {
+    int X, Y, Z;
+    flat_coords(i, Pc, dim, X, Y, Z);
+    C out = czero<C>();
+    if (inside(X, Y, Z, nc)) {
+      const int fx = 2 * X + 1, fy = 2 * Y + 1, fz = dim == 3 ? 2 * Z + 1 : 0;
+      const int dz0 = dim == 3 ? -1 : 0, dz1 = dim == 3 ? 1 : 0;
+      for (int dz = dz0; dz <= dz1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const R wgt = (R)((dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25) * (dim == 3 ? (dz == 0 ? 0.5 : 0.25) : 1.0));
+            out = cadd(out, cscale(ldc<C, false>((const C*)L.r0, fx + dx, fy + dy, fz + dz, n, P), wgt));
+          }
+    }
+    L.bc[i] = out;
+  }
+}
+
 // Coarse sub-cycle with the levels in global memory (any size).
 template <typename C>
 __global__ void __launch_bounds__(512)

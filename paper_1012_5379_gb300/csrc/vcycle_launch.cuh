@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <type_traits>
 #include "../../include/helm.h"
+#include "poly.h"
 
 namespace helm {
 
@@ -234,6 +235,18 @@ void launch_store_output(int dim, int n, const LevelDev<C>* levs, void* dst, int
     pdl_launch(k_store_output<C, float2>, dim3(grid), dim3(256), 0, st, levs, dim, (float2*)dst);
 }
 
+template <typename C>
+void launch_poly_step(int dim, const LevelDev<C>* levs, const C* pw, int nprob, int nflat, int src, int dst,
+                      int wsel, cudaStream_t st) {
+  pdl_launch(k_poly_step<C>, dim3(nprob * nflat), dim3(256), 0, st, levs, pw, nflat, dim, src, dst, wsel);
+}
+
+template <typename C>
+void launch_poly_restrict(int dim, const LevelDev<C>* levs, int nprob, int nflat, int src, cudaStream_t st) {
+  pdl_launch(k_poly_residual<C>, dim3(nprob * nflat), dim3(256), 0, st, levs, nflat, dim, src);
+  pdl_launch(k_poly_fw<C>, dim3(nprob * nflat), dim3(256), 0, st, levs, nflat, dim);
+}
+
 #define HELM_VCYCLE_INST(C)                                                                                   \
   template void launch_arnoldi<C>(int, int, const LevelDev<C>*, int, int, TileCfg, bool, bool, bool, cudaStream_t); \
   template void launch_restrict<C>(int, const LevelDev<C>*, int, int, TileCfg, bool, bool, bool,           \
@@ -248,6 +261,8 @@ void launch_store_output(int dim, int n, const LevelDev<C>* levs, void* dst, int
   template void launch_coarse_cluster<C>(int, const LevelDev<C>*, int, const CoarseLU*, int, int, int,       \
                                          cudaStream_t);                                                       \
   template void launch_load_input<C>(int, const LevelDev<C>*, int, const void*, int, cudaStream_t);           \
-  template void launch_store_output<C>(int, int, const LevelDev<C>*, void*, int, cudaStream_t);
+  template void launch_store_output<C>(int, int, const LevelDev<C>*, void*, int, cudaStream_t);              \
+  template void launch_poly_step<C>(int, const LevelDev<C>*, const C*, int, int, int, int, int, cudaStream_t); \
+  template void launch_poly_restrict<C>(int, const LevelDev<C>*, int, int, int, cudaStream_t);
 
 }  // namespace helm

@@ -66,7 +66,7 @@ class helm_grid(ctypes.Structure):
 class helm_opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("s", ctypes.c_int), ("coarsest_n", ctypes.c_int),
                 ("precond_prec", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("csl_eps", ctypes.c_double)]
+                ("csl_eps", ctypes.c_double), ("smoother", ctypes.c_int)]
 
 
 class helm_info(ctypes.Structure):
@@ -176,13 +176,15 @@ class Handle:
     def __init__(self, dim: int, n: int, theta_beta: float, k: Optional[float] = None, phi=None,
                  theta_gamma: float = 0.5, ecs_frac: float = 0.125, nu1: int = 1, nu2: int = 1, s: int = 3,
                  coarsest_n: int = 3, precision: str = "c64", restart: int = 0, maxit: int = 400, stream=None,
-                 csl_eps: float = 0.0):
+                 csl_eps: float = 0.0, smoother: str = "gmres"):
         lib = load()
         self.dim, self.n = dim, n
         self.precision = precision
         g = helm_grid(dim, n, ecs_frac, theta_gamma)
+        if smoother not in ("gmres", "poly"):
+            raise ValueError("smoother must be 'gmres' or 'poly'")
         o = helm_opts(nu1, nu2, s, coarsest_n, HELM_C128 if precision == "c128" else HELM_C64, restart, maxit,
-                      float(csl_eps))
+                      float(csl_eps), 1 if smoother == "poly" else 0)
         h = ctypes.c_void_p()
         phi_ptr = None if phi is None else _ptr(phi)
         self._phi = phi  # keep the caller's field alive during setup
@@ -252,7 +254,7 @@ def precond_apply_noalloc(dim: int, n: int, theta_beta: float, k: float, r, z, t
     allocates no device memory for it (its working memory is a fixed array inside the
     library).  r, z: torch complex64/complex128 CUDA tensors of shape (n,)*dim."""
     g = helm_grid(dim, n, ecs_frac, theta_gamma)
-    o = helm_opts(nu1, nu2, s, 3, HELM_C128 if precision == "c128" else HELM_C64, 0, 0, 0.0)
+    o = helm_opts(nu1, nu2, s, 3, HELM_C128 if precision == "c128" else HELM_C64, 0, 0, 0.0, 0)
     prec = HELM_C128 if str(r.dtype).endswith("complex128") else HELM_C64
     _check(load().helm_precond_apply_noalloc(ctypes.byref(g), float(k), float(theta_beta), ctypes.byref(o),
                                              _ptr(r), _ptr(z), prec, _stream(stream)))

@@ -77,14 +77,14 @@ def test_setup_rejects_a_basis_longer_than_the_limit(lib):
 
     class Opts(ctypes.Structure):
         _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")] + \
-                   [("csl_eps", ctypes.c_double)]
+                   [("csl_eps", ctypes.c_double), ("smoother", ctypes.c_int)]
     hdr = open(os.path.join(ROOT, "include", "helm.h")).read()
     limit = int(re.search(r"#define HELM_MAX_BASIS (\d+)", hdr).group(1))
     lib.helm_setup.restype = ctypes.c_int
     lib.helm_last_error.restype = ctypes.c_char_p
     out = ctypes.c_void_p()
     g = Grid(2, 15, 0.125, 0.5)
-    o = Opts(0, 0, 0, 0, 0, 0, limit + 1, 0.0)
+    o = Opts(0, 0, 0, 0, 0, 0, limit + 1, 0.0, 0)
     rc = lib.helm_setup(ctypes.byref(g), None, ctypes.c_double(1.0), ctypes.c_double(0.3), ctypes.byref(o), None,
                         ctypes.byref(out))
     assert rc == -1 and out.value is None
@@ -99,13 +99,35 @@ def test_setup_rejects_a_negative_complex_shift(lib):
 
     class Opts(ctypes.Structure):
         _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")] + \
-                   [("csl_eps", ctypes.c_double)]
+                   [("csl_eps", ctypes.c_double), ("smoother", ctypes.c_int)]
     lib.helm_setup.restype = ctypes.c_int
     lib.helm_last_error.restype = ctypes.c_char_p
     out = ctypes.c_void_p()
     g = Grid(2, 15, 0.125, 0.5)
-    o = Opts(0, 0, 0, 0, 0, 0, 0, -0.5)
+    o = Opts(0, 0, 0, 0, 0, 0, 0, -0.5, 0)
     rc = lib.helm_setup(ctypes.byref(g), None, ctypes.c_double(1.0), ctypes.c_double(0.0), ctypes.byref(o), None,
                         ctypes.byref(out))
     assert rc == -1 and out.value is None
     assert b"csl_eps" in lib.helm_last_error()
+
+
+def test_setup_rejects_the_polynomial_smoother_with_a_shift(lib):
+    """The polynomial smoother (Sec. 4) is built for the CSG preconditioner alone."""
+    class Grid(ctypes.Structure):
+        _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
+                    ("theta_gamma", ctypes.c_double)]
+
+    class Opts(ctypes.Structure):
+        _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")] + \
+                   [("csl_eps", ctypes.c_double), ("smoother", ctypes.c_int)]
+    lib.helm_setup.restype = ctypes.c_int
+    lib.helm_last_error.restype = ctypes.c_char_p
+    hdr = open(os.path.join(ROOT, "include", "helm.h")).read()
+    poly = int(re.search(r"#define HELM_SMOOTHER_POLY (\d+)", hdr).group(1))
+    out = ctypes.c_void_p()
+    g = Grid(2, 15, 0.125, 0.5)
+    o = Opts(0, 0, 0, 0, 0, 0, 0, 0.5, poly)
+    rc = lib.helm_setup(ctypes.byref(g), None, ctypes.c_double(5.0), ctypes.c_double(0.2), ctypes.byref(o), None,
+                        ctypes.byref(out))
+    assert rc == -1 and out.value is None
+    assert b"polynomial smoother" in lib.helm_last_error()

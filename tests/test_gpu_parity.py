@@ -114,6 +114,71 @@ def test_csl_argument_checks(helm):
         helm.Handle(2, 31, 0.0, phi=phi, csl_eps=0.5)
 
 
+# ------------------------------------------------------------------ polynomial smoother (Sec. 4)
+def poly_weights(helm, levels, k, tb, tg):
+    """The oracle's Richardson weights, for the library's choice of phi on every
+    smoothed level (the two choose it by the same rule; a grid step apart at most), in
+    the library's order (real part, then imaginary part)."""
+    from oracle import polysmoother as PS
+    out = []
+    for lev in levels[:-1]:
+        h = 1.0 / (lev.n + 1)
+        phi, _ = helm.poly_smoother(k, h, tb, tg, lev.dim)
+        t0, t1, t2 = PS.triangle(k, h, tb, tg, lev.dim)
+        e, f = PS.basis_ef(t0, t1, t2)
+        out.append(sorted(PS.omegas(PS.coefficients(e, f, phi), t0), key=lambda c: (c.real, c.imag)))
+    return out
+
+
+@pytest.mark.parametrize("dim,n,prec,nu1,nu2", [(2, 63, "c128", 1, 1), (2, 127, "c128", 2, 1), (3, 15, "c128", 1, 1),
+                                                (2, 255, "c64", 1, 1), (3, 31, "c64", 1, 2)])
+def test_poly_vcycle_matches_oracle(helm, dim, n, prec, nu1, nu2):
+    """One V-cycle with the third-degree polynomial smoother (theta_beta = 10,
+    theta_gamma = 30 degrees) against the oracle's."""
+    from oracle import polysmoother as PS
+    k, tb, tg = 0.1 * (n + 1), np.radians(10.0), np.radians(30.0)
+    levels = O.build_hierarchy(dim, n, tb, tg, WF, k=k)
+    r = I.random_source(dim, n, 40 + n)
+    want = PS.vcycle_poly(levels, poly_weights(helm, levels, k, tb, tg), r, nu1, nu2)
+    h = helm.Handle(dim, n, tb, k=k, theta_gamma=tg, precision=prec, nu1=nu1, nu2=nu2, smoother="poly")
+    rt = dev(r, prec)
+    zt = torch.empty_like(rt)
+    h.precond_apply(rt, zt)
+    assert rel(zt.cpu().numpy(), want) < (1e-11 if prec == "c128" else 1e-4)
+
+
+def test_poly_solve(helm):
+    """FGMRES preconditioned by the polynomial-smoothed V-cycle on 127^2, k = 20,
+    theta_beta = 10 degrees: true residual under the oracle's H, iterations within +10%
+    (+1) of the oracle's."""
+    from oracle import polysmoother as PS
+    n, k, tb, tg, tol = 127, 20.0, np.radians(10.0), TG, 1e-6
+    b = I.random_source(2, n, 33)
+    levels = O.build_hierarchy(2, n, tb, tg, WF, k=k)
+    w = poly_weights(helm, levels, k, tb, tg)
+    _, io = O.fgmres(levels[0].apply_h, lambda v: PS.vcycle_poly(levels, w, v), b, tol=tol, restart=0, maxit=300)
+    h = helm.Handle(2, n, tb, k=k, theta_gamma=tg, precision="c64", smoother="poly")
+    bt = dev(b)
+    xt = torch.zeros_like(bt)
+    info = h.solve(bt, xt, tol)
+    x = xt.cpu().numpy()
+    assert info.status == 0
+    assert np.linalg.norm(b - levels[0].apply_h(x)) / np.linalg.norm(b) <= tol * 1.0001
+    assert info.iters <= int(1.1 * io.iters) + 1
+
+
+def test_poly_argument_checks(helm):
+    """No stable polynomial (theta_beta too small), a k field or a complex shift:
+    refused."""
+    with pytest.raises(helm.HelmError):
+        helm.Handle(2, 127, np.radians(1.0), k=60.0, theta_gamma=np.radians(30.0), smoother="poly")
+    with pytest.raises(helm.HelmError):
+        helm.Handle(2, 31, 0.2, k=5.0, csl_eps=0.5, smoother="poly")
+    phi = torch.full((31, 31), 25.0, dtype=torch.float32, device="cuda")
+    with pytest.raises(helm.HelmError):
+        helm.Handle(2, 31, 0.2, phi=phi, smoother="poly")
+
+
 # ------------------------------------------------------------------ one V-cycle
 VC_CASES = [
     (2, 15, "c128"), (2, 31, "c128"), (2, 63, "c128"), (2, 127, "c128"), (2, 255, "c128"),
