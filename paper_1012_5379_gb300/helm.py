@@ -108,9 +108,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_workspace_bytes.restype = ip
     lib.helm_levels.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
     lib.helm_levels.restype = ip
-    dp = ctypes.POINTER(ctypes.c_double)
-    lib.helm_poly_smoother.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ip, dp,
-                                       dp]
+    dptr = ctypes.POINTER(ctypes.c_double)
+    lib.helm_poly_smoother.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ip, dptr,
+                                       dptr]
     lib.helm_poly_smoother.restype = ip
     lib.helm_last_error.argtypes = []
     lib.helm_last_error.restype = ctypes.c_char_p

@@ -131,3 +131,23 @@ def test_setup_rejects_the_polynomial_smoother_with_a_shift(lib):
                         ctypes.byref(out))
     assert rc == -1 and out.value is None
     assert b"polynomial smoother" in lib.helm_last_error()
+
+
+def test_binding_declares_every_double_parameter_as_double():
+    """The ctypes binding passes a C `double` parameter as c_double (a pointer or an int
+    there makes every call fail), for every prototype of the header."""
+    from paper_1012_5379_gb300 import helm as H
+    lib = H.load()
+    src = open(os.path.join(ROOT, "include", "helm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    checked = 0
+    for m in re.finditer(r"\b(?:int|void|unsigned long long|const char\*)\s+(helm_\w+)\s*\(([^;{]*?)\)\s*;", src):
+        name, params = m.group(1), m.group(2).strip()
+        fn = getattr(lib, name)
+        if not params or params == "void" or fn.argtypes is None:
+            continue
+        for i, p in enumerate(x.strip() for x in params.split(",")):
+            if re.match(r"^double\s+\w+$", p):
+                assert fn.argtypes[i] is ctypes.c_double, (name, i, p)
+                checked += 1
+    assert checked >= 8
