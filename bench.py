@@ -388,8 +388,11 @@ def run_precond(args):
     dev = torch.device("cuda", 0)
     n, dim = args.n, args.dim
     k = 0.156 * (n + 1)
-    # maxit = 1: no FGMRES basis is allocated, the device holds the hierarchy only
-    h = helm.Handle(dim, n, 0.3, k=k, precision="c64", maxit=1)
+    # maxit = 1: no FGMRES basis is allocated, the device holds the hierarchy only.  The
+    # polynomial smoother needs a larger CSG angle than the workload's 0.3 rad on its
+    # coarse levels (Sec. 4.5): it runs at theta_beta = 10 degrees.
+    tb = 0.3 if args.smoother == "gmres" else np.radians(10.0)
+    h = helm.Handle(dim, n, tb, k=k, precision="c64", maxit=1, smoother=args.smoother)
     r = torch.from_numpy(I.random_source(dim, n, 1001)).to(dev).to(torch.complex64)
     z = torch.empty_like(r)
     for _ in range(args.reps):
@@ -404,7 +407,7 @@ def run_precond(args):
     for _ in range(args.reps):
         h.precond_apply(r, z)
     classes = helm.profile_end()
-    print(json.dumps({"mode": "precond", "dim": dim, "n": n, "ms_per_vcycle": 1e3 * dt,
+    print(json.dumps({"mode": "precond", "dim": dim, "n": n, "smoother": args.smoother, "ms_per_vcycle": 1e3 * dt,
                       "mpts_per_s": n ** dim / dt / 1e6,
                       "vcycle_hbm": vcycle_hbm(classes, peaks().get("hbm_gbs", 6800.0)),
                       "classes_us_per_vcycle": {c: round(1e3 * v["ms"] / args.reps, 1) for c, v in classes.items()},
@@ -693,6 +696,8 @@ def main():
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=4095)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--smoother", choices=["gmres", "poly"], default="gmres",
+                    help="precond mode: GMRES(3) sweeps or the Sec. 4 polynomial smoother (theta_beta 10 deg)")
     args = ap.parse_args()
     if args.mode != "solve":
         from paper_1012_5379_gb300 import build
