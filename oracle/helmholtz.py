@@ -18,7 +18,8 @@ import numpy as np
 # Grid (Sec. 2, Eq. csggrid; Remark 2.2 for layers on both sides)
 # ----------------------------------------------------------------------------------
 
-def complex_map(x: float, ecs_frac: float, theta_gamma: float, theta_beta: float) -> complex:
+def complex_map(x: float, ecs_frac: float, theta_gamma: float, theta_beta: float,
+                ecs_sides: str = "both") -> complex:
     """Complex coordinate z(x) = integral_0^x s(t) dt of the stretched grid.
 
     Sec. 2, Eq. csggrid: interior spacing h_beta = h e^{i theta_beta}, ECS layer
@@ -27,10 +28,21 @@ def complex_map(x: float, ecs_frac: float, theta_gamma: float, theta_beta: float
     t > 1 - w (w = ``ecs_frac``), e^{i theta_beta} otherwise.  The printed interior
     grid ends at j h_beta and restarts the layer at 1 (garbled); only spacings enter
     the scheme, so the continuous map is used.
+
+    ``ecs_sides = "high"`` puts the layer at the far end only (Benchmark 3 of Sec. 5:
+    homogeneous Dirichlet on the south and west edges, ECS layers on the north and
+    east edges): s(t) = e^{i theta_gamma} for t > 1 - w, e^{i theta_beta} otherwise,
+    which is Eq. csggrid as printed (n interior intervals followed by m layer ones).
     """
     w = ecs_frac
     eg = np.exp(1j * theta_gamma)
     eb = np.exp(1j * theta_beta)
+    if ecs_sides == "high":
+        if x <= 1.0 - w:
+            return x * eb
+        return (1.0 - w) * eb + (x - (1.0 - w)) * eg
+    if ecs_sides != "both":
+        raise ValueError("ecs_sides is 'both' or 'high'")
     if x <= w:
         return x * eg
     if x <= 1.0 - w:
@@ -38,14 +50,15 @@ def complex_map(x: float, ecs_frac: float, theta_gamma: float, theta_beta: float
     return w * eg + (1.0 - 2.0 * w) * eb + (x - (1.0 - w)) * eg
 
 
-def spacings(n: int, ecs_frac: float, theta_gamma: float, theta_beta: float) -> np.ndarray:
+def spacings(n: int, ecs_frac: float, theta_gamma: float, theta_beta: float,
+             ecs_sides: str = "both") -> np.ndarray:
     """Complex spacings h_i = z(x_{i+1}) - z(x_i), i = 0..n, for nodes x_i = i/(n+1).
 
     The exact integral of the map handles an interval that straddles the
     layer/interior turning point (this happens on coarse levels).  Sec. 2.
     """
     h = 1.0 / (n + 1)
-    z = np.array([complex_map(i * h, ecs_frac, theta_gamma, theta_beta) for i in range(n + 2)])
+    z = np.array([complex_map(i * h, ecs_frac, theta_gamma, theta_beta, ecs_sides) for i in range(n + 2)])
     return np.diff(z)
 
 
@@ -133,7 +146,7 @@ class Level:
 def build_hierarchy(dim: int, n: int, theta_beta: float, theta_gamma: float = 0.5,
                     ecs_frac: float = 0.125, k: Optional[float] = None,
                     phi: Optional[np.ndarray] = None, coarsest: int = 3,
-                    csl_eps: float = 0.0) -> List[Level]:
+                    csl_eps: float = 0.0, ecs_sides: str = "both") -> List[Level]:
     """Rediscretised hierarchy of M^CSG (Sec. 3.1, Prop. 3.1).
 
     Each level uses the same complex map with doubled real spacing; phi is sampled
@@ -146,6 +159,9 @@ def build_hierarchy(dim: int, n: int, theta_beta: float, theta_gamma: float = 0.
     M = L - (1 + i eps) phi on every level; with theta_beta = 0 this is M^CSL on the
     real interior grid (the ECS layers stay), with theta_beta > 0 both devices
     combine.  H is never shifted.
+
+    ``ecs_sides = "high"``: layers at the far end of every axis only, homogeneous
+    Dirichlet at the near end (Benchmark 3 of Sec. 5), see ``complex_map``.
     """
     if (k is None) == (phi is None):
         raise ValueError("give exactly one of k (constant) or phi (field)")
@@ -154,10 +170,10 @@ def build_hierarchy(dim: int, n: int, theta_beta: float, theta_gamma: float = 0.
     for li, nl in enumerate(level_sizes(n, coarsest)):
         if li > 0 and not np.isscalar(cur_phi):
             cur_phi = _inject(cur_phi)
-        sp = spacings(nl, ecs_frac, theta_gamma, theta_beta)
+        sp = spacings(nl, ecs_frac, theta_gamma, theta_beta, ecs_sides)
         lev = Level(n=nl, dim=dim, coef=coefficients_1d(sp), phi=cur_phi, shift=complex(1.0, csl_eps))
         if li == 0:
-            lev.coef_h = coefficients_1d(spacings(nl, ecs_frac, theta_gamma, 0.0))
+            lev.coef_h = coefficients_1d(spacings(nl, ecs_frac, theta_gamma, 0.0, ecs_sides))
         levels.append(lev)
     levels[-1].lu = dense_matrix(levels[-1])
     return levels

@@ -77,6 +77,7 @@ class Workload:
     precision: str = "c64"              # preconditioner precision
     theta_gamma: float = THETA_GAMMA
     ecs_frac: float = ECS_FRAC
+    ecs_sides: str = "both"             # "high": layers at the far end of each axis only
 
 
 def small_2d(seed: int = 1000) -> Workload:
@@ -101,6 +102,48 @@ def cube_3d(n: int = 255, seed: int = 1002) -> Workload:
     point source at the centre, theta_beta = 0.4, restart 40, tolerance 1e-6."""
     return Workload(dim=3, n=n, theta_beta=0.4, phi=bump_field(n, seed), b=point_source(3, n),
                     tol=1e-6, restart=40, precision="c64")
+
+
+GAUSS_DOMAIN = 50.0                       # physical box (0, 50)^2 of the Gaussian model
+GAUSS_THETA_BETA = float(np.radians(10.3132))  # CSG angle of every Sec. 5 benchmark
+GAUSS_THETA_GAMMA = float(np.pi / 6)      # ECS angle of Sec. 4 and 5
+
+
+def gaussian_model(nint: int, k: float, nu: float) -> Workload:
+    """Benchmark 3 of Sec. 5 (the Gaussian model) on the unit box.
+
+    The physical problem lives on (0, 50)^2 with phi = nu (e^{-x^2} + e^{-y^2}) + k^2
+    and the source chi = 1 / (e^{x^2} + e^{y^2}), homogeneous Dirichlet on the south and
+    west edges (x = 0, y = 0) and ECS layers beyond the north and east edges.  Readings
+    (the paper leaves them open): ``nint`` intervals across (0, 50) per axis (the
+    table's "interior grid"), followed by a layer of nint/4 intervals (the layer width
+    of Sec. 4.4), theta_beta = 10.3132 degrees, theta_gamma = pi/6, relative residual
+    1e-7.  So a grid of n = 1.25 nint - 1 unknowns per axis covers a box of length
+    Lam = 50 (n + 1) / nint, the last fifth of it the layer.
+
+    Mapped to the unit box (x = Lam xi) the operator -Delta_x - phi becomes
+    (-Delta_xi - Lam^2 phi) / Lam^2; the returned problem is Lam^2 times the physical one
+    (phi and b both scaled by Lam^2), which has the same solution, the same relative
+    residuals and the same preconditioned iterations.  phi is float32 (the library's
+    field precision); b is complex128 and vanishes to rounding inside the layer.
+    """
+    if nint % 4:
+        raise ValueError("nint must be a multiple of 4 (the layer has nint/4 intervals)")
+    n = nint + nint // 4 - 1
+    lam = GAUSS_DOMAIN * (n + 1) / nint
+    x = np.arange(1, n + 1) * (lam / (n + 1))
+    ex = np.exp(-x * x)
+    phi = lam * lam * (nu * (ex[None, :] + ex[:, None]) + k * k)
+    # 1 / (e^{x^2} + e^{y^2}) without overflow: divide through by the larger exponential
+    sx, sy = (x * x)[None, :], (x * x)[:, None]
+    m = np.maximum(sx, sy)
+    chi = np.exp(-m) / (np.exp(sx - m) + np.exp(sy - m))
+    return Workload(dim=2, n=n, theta_beta=GAUSS_THETA_BETA, phi=phi.astype(np.float32),
+                    b=(lam * lam * chi).astype(np.complex128), tol=1e-7, restart=0, precision="c64",
+                    theta_gamma=GAUSS_THETA_GAMMA, ecs_frac=(nint // 4) / (n + 1), ecs_sides="high")
+
+
+GAUSS_COLUMNS = ((0.5, 64), (1.5, 128), (2.5, 256), (3.5, 512), (4.5, 512))  # (k, nint) of Tables 4-5
 
 
 def batch_2d(count: int = 64, seed: int = 1003, sizes=(255, 511, 1023), theta_beta: float = 0.3
