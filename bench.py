@@ -470,6 +470,51 @@ def run_cube(args):
     print(json.dumps(out), flush=True)
 
 
+def run_gauss(args):
+    """Benchmark 3 of Sec. 5, the Gaussian model: the five (k, grid) columns of
+    Tables 4 and 5 for nu = 1 and nu = 7, V(1,0) and V(1,1) preconditioners (GMRES(3)
+    smoothing, complex64), FGMRES without restart to 1e-7.  Each solve is timed with
+    CUDA events after an untimed one; the paper's counts are printed beside ours."""
+    import torch
+
+    from paper_1012_5379_gb300 import helm
+    dev = torch.device("cuda", 0)
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                                       "paper_tables.json")))
+    rows = []
+    for table, nu in (("table4", 1.0), ("table5", 7.0)):
+        for col, (k, nint) in enumerate(I.GAUSS_COLUMNS):
+            w = I.gaussian_model(nint, k, nu)
+            b = torch.from_numpy(w.b).to(dev)
+            phi = torch.from_numpy(w.phi).to(dev)
+            for cyc in ("1,0", "1,1"):
+                nu1, nu2 = map(int, cyc.split(","))
+                h = helm.Handle(2, w.n, w.theta_beta, phi=phi, precision=w.precision, theta_gamma=w.theta_gamma,
+                                ecs_frac=w.ecs_frac, ecs_sides="high", nu1=nu1, nu2=nu2,
+                                maxit=max(args.maxit, 600))
+                x = torch.zeros_like(b)
+                h.solve(b, x, w.tol)
+                x.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                info = h.solve(b, x, w.tol)
+                e1.record()
+                torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) * 1e-3
+                rows.append({"nu": nu, "k": k, "nint": nint, "n": w.n, "cycle": cyc, "iters": info.iters,
+                             "paper_iters": gold[table]["iters"][cyc][col], "status": info.status,
+                             "rel_res_true": info.rel_res_true, "s": sec,
+                             "vcycle_mpts_per_s": float(w.n) ** 2 * info.iters / sec / 1e6})
+                h.close()
+                del h
+    out = {"mode": "gauss", "config": {"workload": "Gaussian model (Sec. 5, Benchmark 3): (0,50)^2, phi = nu (e^-x^2 + "
+                                                   "e^-y^2) + k^2, Dirichlet S/W, ECS layer nint/4 N/E at pi/6, "
+                                                   "theta_beta 10.3132 deg, FGMRES to 1e-7, c64 preconditioner"},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def _seq_solves(helm, works, precision, bs, xs):
     """Solve `works` one at a time on fresh handles of `precision` (each timed with CUDA
     events after one untimed solve of the same handle); returns per-problem seconds and
@@ -686,7 +731,8 @@ def main():
     ap.add_argument("--sequential-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single", "cube"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single", "cube", "gauss"],
+                    default="solve")
     ap.add_argument("--restart", type=int, default=0)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--requests", type=int, default=2000)
@@ -703,7 +749,7 @@ def main():
         from paper_1012_5379_gb300 import build
         build.build()
         {"precond": run_precond, "batch": run_batch, "serve": run_serve, "single": run_single,
-         "cube": run_cube}[args.mode](args)
+         "cube": run_cube, "gauss": run_gauss}[args.mode](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

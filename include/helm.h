@@ -58,14 +58,22 @@ typedef struct helm_handle helm_handle;
 /* Grid: the unit interval per axis, n interior nodes, spacing h = 1/(n+1); u = 0 on
  * the outer edge of the layers.  n must be >= 3 and coarsening proceeds while n+1 is
  * even and n > coarsest_n (so n = 2^L - 1 gives L-1 levels down to 3).
- * ecs_frac: layer width on each side as a fraction of the box, 0 < ecs_frac < 0.5.
- * theta_gamma: ECS layer angle in radians, 0 <= theta_gamma < pi/2. */
+ * ecs_frac: layer width on each side as a fraction of the box, 0 < ecs_frac < 0.5
+ * (0 < ecs_frac < 1 with ecs_sides = HELM_ECS_HIGH).
+ * theta_gamma: ECS layer angle in radians, 0 <= theta_gamma < pi/2.
+ * ecs_sides: HELM_ECS_BOTH puts a layer at both ends of every axis (Remark 2.2);
+ * HELM_ECS_HIGH only at the far end (x = 1), with u = 0 on the near edge x = 0 of the
+ * interior (Benchmark 3 of Sec. 5: Dirichlet south and west edges, ECS north and
+ * east).  A zero-initialised grid takes HELM_ECS_BOTH. */
 typedef struct {
   int dim;            /* 2 or 3 */
   int n;              /* interior nodes per axis (same on every axis) */
   double ecs_frac;    /* default 0.125 */
   double theta_gamma; /* default 0.5 */
+  int ecs_sides;      /* HELM_ECS_BOTH or HELM_ECS_HIGH, default HELM_ECS_BOTH */
 } helm_grid;
+#define HELM_ECS_BOTH 0
+#define HELM_ECS_HIGH 1
 
 /* Options.  Zero-initialised fields take the defaults in brackets. */
 typedef struct {
@@ -248,6 +256,18 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes);
 int helm_poly_smoother(double k, double h, double theta_beta, double theta_gamma, int dim, double* phi,
                        double* w);
 
+/* Stencil coefficients of one axis of the grid (Sec. 2, Eq. csggrid and the
+ * three-point difference of Eq. csg_dis): the complex spacings h_i = z(x_{i+1}) - z(x_i)
+ * of the stretched map (angle theta_beta inside, theta_gamma in the layers placed as
+ * ecs_sides says, width ecs_frac) and, at interior node i = 0..n-1,
+ * (L u)_i = a_i u_{i-1} + d_i u_i + c_i u_{i+1} with L ~ -d^2/dz^2.  a, d, c are host
+ * arrays of n complex numbers as (re, im) double pairs, owned by the caller.  Host only
+ * (no device work): this is the setup's own geometry, exported so that it can be
+ * checked without a GPU.  HELM_EINVAL on a NULL array, n < 1, angles outside
+ * [0, pi/2) or ecs_frac outside the range helm_grid states. */
+int helm_axis_coefficients(int n, double ecs_frac, int ecs_sides, double theta_gamma, double theta_beta,
+                           double* a, double* d, double* c);
+
 /* One V(nu1, nu2) cycle, z ~ (M^CSG)^{-1} r, for a small grid without allocating any
  * device memory.  For callers that cannot let a library call cudaMalloc: programs
  * whose device memory is reserved up front by a pooling allocator, and
@@ -256,7 +276,8 @@ int helm_poly_smoother(double k, double h, double theta_beta, double theta_gamma
  * of helm_precond_apply.
  *   grid, theta_beta, opts: as for helm_setup (constant wavenumber k only; opts may be
  *     NULL; restart and maxit are ignored; precond_prec selects the arithmetic;
- *     csl_eps must be 0 and smoother HELM_SMOOTHER_GMRES: HELM_EINVAL otherwise).
+ *     csl_eps must be 0, smoother HELM_SMOOTHER_GMRES and grid->ecs_sides
+ *     HELM_ECS_BOTH: HELM_EINVAL otherwise).
  *   r, z: device arrays of n^dim complex numbers in precision `prec`, natural order.
  * All working memory lives in one fixed 4 MiB device array inside the library, which
  * every GPU that loads the library holds until the process exits.  Grids whose

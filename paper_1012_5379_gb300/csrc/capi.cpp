@@ -231,6 +231,30 @@ int helm_poly_smoother(double k, double h, double theta_beta, double theta_gamma
   })
 }
 
+int helm_axis_coefficients(int n, double ecs_frac, int ecs_sides, double theta_gamma, double theta_beta,
+                           double* a, double* d, double* c) {
+  HELM_GUARD({
+    if (!a || !d || !c) { helm::set_error("NULL argument"); return HELM_EINVAL; }
+    const bool both = ecs_sides == HELM_ECS_BOTH;
+    if (!(n >= 1 && (both || ecs_sides == HELM_ECS_HIGH) && ecs_frac > 0 && ecs_frac < (both ? 0.5 : 1.0) &&
+          theta_gamma >= 0 && theta_gamma < M_PI / 2 && theta_beta >= 0 && theta_beta < M_PI / 2)) {
+      helm::set_error("need n >= 1, a valid ecs_sides and ecs_frac, angles in [0, pi/2)");
+      return HELM_EINVAL;
+    }
+    std::vector<helm::cplx> va, vd, vc;
+    helm::stencil_coefficients(helm::grid_spacings(n, ecs_frac, theta_gamma, theta_beta, both), va, vd, vc);
+    for (int i = 0; i < n; ++i) {
+      a[2 * i] = va[i].real();
+      a[2 * i + 1] = va[i].imag();
+      d[2 * i] = vd[i].real();
+      d[2 * i + 1] = vd[i].imag();
+      c[2 * i] = vc[i].real();
+      c[2 * i + 1] = vc[i].imag();
+    }
+    return HELM_OK;
+  })
+}
+
 int helm_precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, const helm_opts* opts,
                                const void* r, void* z, int prec, void* stream) {
   HELM_GUARD({ return helm::precond_apply_noalloc(grid, k, theta_beta, opts, r, z, prec, (cudaStream_t)stream); })

@@ -71,7 +71,7 @@ static int dev_alloc(Handle* h, T** p, size_t bytes) {
 static int upload_level_coefficients(Handle* h, int l, double theta_beta, cudaStream_t st) {
   HostLevel& L = h->lev[l];
   std::vector<cplx> a, d, c;
-  stencil_coefficients(grid_spacings(L.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
+  stencil_coefficients(grid_spacings(L.n, h->ecs, h->theta_gamma, theta_beta, h->ecs_sides == HELM_ECS_BOTH), a, d, c);
   // Complex shift of M (constant k): the diagonal's extra -i eps k^2 is spread over the
   // d axes' diagonal coefficients (every point's diagonal adds one per axis), so the
   // kernels' -phi stays real and nothing else changes.
@@ -101,7 +101,7 @@ static int factor_coarsest(Handle* h, double theta_beta, cudaStream_t st) {
   const HostLevel& Lc = h->lev.back();
   const int cm = h->lu_m;
   std::vector<cplx> a, d, c;
-  stencil_coefficients(grid_spacings(Lc.n, h->ecs, h->theta_gamma, theta_beta), a, d, c);
+  stencil_coefficients(grid_spacings(Lc.n, h->ecs, h->theta_gamma, theta_beta, h->ecs_sides == HELM_ECS_BOTH), a, d, c);
   std::vector<double> phic(cm, Lc.phic);
   if (Lc.phi) {
     std::vector<float> pad(Lc.np);
@@ -151,6 +151,7 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   h->n = grid->n;
   h->ecs = grid->ecs_frac > 0 ? grid->ecs_frac : 0.125;
   h->theta_gamma = grid->theta_gamma;
+  h->ecs_sides = grid->ecs_sides;
   h->theta_beta = theta_beta;
   h->k = k;
   h->has_phi = phi != nullptr;
@@ -167,7 +168,14 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   h->smoother = o.smoother;
   if (h->dim != 2 && h->dim != 3) { set_error("dim must be 2 or 3"); return HELM_EINVAL; }
   if (h->n < 1 || h->n > (h->dim == 2 ? 32767 : 2047)) { set_error("n out of range"); return HELM_EINVAL; }
-  if (!(h->ecs > 0 && h->ecs < 0.5)) { set_error("ecs_frac must be in (0, 0.5)"); return HELM_EINVAL; }
+  if (h->ecs_sides != HELM_ECS_BOTH && h->ecs_sides != HELM_ECS_HIGH) {
+    set_error("ecs_sides must be HELM_ECS_BOTH or HELM_ECS_HIGH");
+    return HELM_EINVAL;
+  }
+  if (!(h->ecs > 0 && h->ecs < (h->ecs_sides == HELM_ECS_BOTH ? 0.5 : 1.0))) {
+    set_error("ecs_frac must be in (0, 0.5) with layers on both sides, (0, 1) with one");
+    return HELM_EINVAL;
+  }
   if (!(h->theta_gamma >= 0 && h->theta_gamma < M_PI / 2)) { set_error("theta_gamma must be in [0, pi/2)"); return HELM_EINVAL; }
   if (!(theta_beta >= 0 && theta_beta < M_PI / 2)) { set_error("theta_beta must be in [0, pi/2)"); return HELM_EINVAL; }
   if (h->s > SMAX) { set_error("s must be in 1..4"); return HELM_EINVAL; }
@@ -278,7 +286,7 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   {
     const HostLevel& L0 = h->lev[0];
     std::vector<cplx> a, d, c;
-    stencil_coefficients(grid_spacings(h->n, h->ecs, h->theta_gamma, 0.0), a, d, c);
+    stencil_coefficients(grid_spacings(h->n, h->ecs, h->theta_gamma, 0.0, h->ecs_sides == HELM_ECS_BOTH), a, d, c);
     std::vector<double2> hc(3 * h->n);
     for (int i = 0; i < h->n; ++i) {
       hc[i] = make_double2(a[i].real(), a[i].imag());

@@ -57,6 +57,7 @@ struct Handle {
   int dim = 2, n = 0, prec = HELM_C64;
   int nu1 = 1, nu2 = 1, s = 3, coarsest = 3, restart = 0, maxit = 400, m = 0;
   double theta_beta = 0, theta_gamma = 0.5, ecs = 0.125, k = 0;
+  int ecs_sides = 0;              // HELM_ECS_BOTH or HELM_ECS_HIGH
   double csl_eps = 0;             // complex shift of M: L - (1 + i csl_eps) phi
   int smoother = 0;               // HELM_SMOOTHER_GMRES or HELM_SMOOTHER_POLY
   std::vector<std::array<std::complex<double>, 3>> polyw;  // Richardson weights per smoothed level

@@ -15,14 +15,17 @@ static double overlap(double a, double b, double lo, double hi) {
 // h_i = integral over [x_i, x_{i+1}] of the stretching factor: e^{i theta_gamma} in
 // the layers [0, w] and [1 - w, 1] (both sides, Remark 2.2), e^{i theta_beta} in the
 // interior (Eq. csggrid).  An interval that straddles a turning point gets the exact
-// mixed value.
-std::vector<cplx> grid_spacings(int n, double ecs, double theta_gamma, double theta_beta) {
+// mixed value.  low_layer = false drops the layer at x = 0: homogeneous Dirichlet on
+// that edge of the interior, the layer only at the far end (Eq. csggrid as printed;
+// Benchmark 3 of Sec. 5 has Dirichlet south and west edges, layers north and east).
+std::vector<cplx> grid_spacings(int n, double ecs, double theta_gamma, double theta_beta, bool low_layer) {
   const double h = 1.0 / (n + 1);
   const cplx eg = std::polar(1.0, theta_gamma), eb = std::polar(1.0, theta_beta);
+  const double lo = low_layer ? ecs : 0.0;
   std::vector<cplx> sp(n + 1);
   for (int i = 0; i <= n; ++i) {
     const double a = i * h, b = (i + 1) * h;
-    sp[i] = eg * (overlap(a, b, 0.0, ecs) + overlap(a, b, 1.0 - ecs, 1.0)) + eb * overlap(a, b, ecs, 1.0 - ecs);
+    sp[i] = eg * (overlap(a, b, 0.0, lo) + overlap(a, b, 1.0 - ecs, 1.0)) + eb * overlap(a, b, lo, 1.0 - ecs);
   }
   return sp;
 }

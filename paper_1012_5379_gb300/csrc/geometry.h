@@ -7,7 +7,9 @@ namespace helm {
 
 typedef std::complex<double> cplx;
 
-std::vector<cplx> grid_spacings(int n, double ecs, double theta_gamma, double theta_beta);
+// Complex spacings of one axis (n + 1 intervals of the unit box); low_layer = false
+// keeps the ECS layer at the far end only (Dirichlet edge at x = 0).
+std::vector<cplx> grid_spacings(int n, double ecs, double theta_gamma, double theta_beta, bool low_layer = true);
 void stencil_coefficients(const std::vector<cplx>& sp, std::vector<cplx>& a, std::vector<cplx>& d,
                           std::vector<cplx>& c);
 // Dense matrix of L - shift * diag(phi) on n^dim nodes (shift 1: CSG; 1 + i eps: CSL variant).

@@ -276,6 +276,7 @@ int precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, co
   if (grid->n < 1 || grid->n > MAX_N) { set_error("n out of range for the allocation-free entry point"); return HELM_EINVAL; }
   const double ecs = grid->ecs_frac > 0 ? grid->ecs_frac : 0.125;
   if (!(ecs < 0.5)) { set_error("ecs_frac must be in (0, 0.5)"); return HELM_EINVAL; }
+  if (grid->ecs_sides != HELM_ECS_BOTH) { set_error("the allocation-free entry point takes layers on both sides only"); return HELM_EINVAL; }
   if (!(grid->theta_gamma >= 0 && grid->theta_gamma < M_PI / 2)) { set_error("theta_gamma must be in [0, pi/2)"); return HELM_EINVAL; }
   if (!(theta_beta >= 0 && theta_beta < M_PI / 2)) { set_error("theta_beta must be in [0, pi/2)"); return HELM_EINVAL; }
   if (!std::isfinite(k)) { set_error("k must be finite"); return HELM_EINVAL; }

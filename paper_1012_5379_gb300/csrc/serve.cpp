@@ -178,7 +178,7 @@ struct Server {
           queue.push_front(r);
           return HELM_OK;
         }
-        helm_grid g;
+        helm_grid g{};
         g.dim = r->dim;
         g.n = r->n;
         g.ecs_frac = opts.ecs_frac;

@@ -32,6 +32,7 @@ _STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ENOCONV
 # names declared in include/helm.h (checked by the CPU test suite)
 EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_operator", "helm_solve",
            "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_poly_smoother",
+           "helm_axis_coefficients",
            "helm_last_error",
            "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc",
            "helm_batch_solve_host", "helm_serve_start", "helm_serve_submit", "helm_serve_poll", "helm_serve_wait",
@@ -60,7 +61,11 @@ class HelmError(RuntimeError):
 
 class helm_grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
-                ("theta_gamma", ctypes.c_double)]
+                ("theta_gamma", ctypes.c_double), ("ecs_sides", ctypes.c_int)]
+
+
+HELM_ECS_BOTH, HELM_ECS_HIGH = 0, 1
+_ECS_SIDES = {"both": HELM_ECS_BOTH, "high": HELM_ECS_HIGH}
 
 
 class helm_opts(ctypes.Structure):
@@ -112,6 +117,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_poly_smoother.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ip, dptr,
                                        dptr]
     lib.helm_poly_smoother.restype = ip
+    lib.helm_axis_coefficients.argtypes = [ip, ctypes.c_double, ip, ctypes.c_double, ctypes.c_double, dptr, dptr,
+                                           dptr]
+    lib.helm_axis_coefficients.restype = ip
     lib.helm_last_error.argtypes = []
     lib.helm_last_error.restype = ctypes.c_char_p
     lib.helm_precond_apply_noalloc.argtypes = [ctypes.POINTER(helm_grid), dp, dp, ctypes.POINTER(helm_opts), vp, vp,
@@ -176,11 +184,13 @@ class Handle:
     def __init__(self, dim: int, n: int, theta_beta: float, k: Optional[float] = None, phi=None,
                  theta_gamma: float = 0.5, ecs_frac: float = 0.125, nu1: int = 1, nu2: int = 1, s: int = 3,
                  coarsest_n: int = 3, precision: str = "c64", restart: int = 0, maxit: int = 400, stream=None,
-                 csl_eps: float = 0.0, smoother: str = "gmres"):
+                 csl_eps: float = 0.0, smoother: str = "gmres", ecs_sides: str = "both"):
         lib = load()
         self.dim, self.n = dim, n
         self.precision = precision
-        g = helm_grid(dim, n, ecs_frac, theta_gamma)
+        if ecs_sides not in _ECS_SIDES:
+            raise ValueError("ecs_sides must be 'both' or 'high'")
+        g = helm_grid(dim, n, ecs_frac, theta_gamma, _ECS_SIDES[ecs_sides])
         if smoother not in ("gmres", "poly"):
             raise ValueError("smoother must be 'gmres' or 'poly'")
         o = helm_opts(nu1, nu2, s, coarsest_n, HELM_C128 if precision == "c128" else HELM_C64, restart, maxit,
@@ -253,7 +263,7 @@ def precond_apply_noalloc(dim: int, n: int, theta_beta: float, k: float, r, z, t
     """One V-cycle on a small grid through helm_precond_apply_noalloc: the library
     allocates no device memory for it (its working memory is a fixed array inside the
     library).  r, z: torch complex64/complex128 CUDA tensors of shape (n,)*dim."""
-    g = helm_grid(dim, n, ecs_frac, theta_gamma)
+    g = helm_grid(dim, n, ecs_frac, theta_gamma, HELM_ECS_BOTH)
     o = helm_opts(nu1, nu2, s, 3, HELM_C128 if precision == "c128" else HELM_C64, 0, 0, 0.0, 0)
     prec = HELM_C128 if str(r.dtype).endswith("complex128") else HELM_C64
     _check(load().helm_precond_apply_noalloc(ctypes.byref(g), float(k), float(theta_beta), ctypes.byref(o),
@@ -268,6 +278,19 @@ def poly_smoother(k: float, h: float, theta_beta: float, theta_gamma: float, dim
     _check(load().helm_poly_smoother(float(k), float(h), float(theta_beta), float(theta_gamma), int(dim),
                                      ctypes.byref(phi), w))
     return phi.value, [complex(w[2 * j], w[2 * j + 1]) for j in range(3)]
+
+
+def axis_coefficients(n: int, ecs_frac: float, theta_gamma: float, theta_beta: float, ecs_sides: str = "both"):
+    """The setup's stencil coefficients (a, d, c) of one axis (Sec. 2), computed on the
+    host by helm_axis_coefficients: three complex128 numpy arrays of length n."""
+    import numpy as np
+    if ecs_sides not in _ECS_SIDES:
+        raise ValueError("ecs_sides must be 'both' or 'high'")
+    out = [np.zeros(2 * n, dtype=np.float64) for _ in range(3)]
+    dptr = ctypes.POINTER(ctypes.c_double)
+    _check(load().helm_axis_coefficients(int(n), float(ecs_frac), _ECS_SIDES[ecs_sides], float(theta_gamma),
+                                         float(theta_beta), *[o.ctypes.data_as(dptr) for o in out]))
+    return tuple(o[0::2] + 1j * o[1::2] for o in out)
 
 
 def launch_count() -> int:

@@ -43,13 +43,13 @@ def test_binding_covers_the_header():
 
 def test_last_error_is_callable_without_gpu(lib):
     lib.helm_last_error.restype = ctypes.c_char_p
-    assert lib.helm_last_error() == b""
+    assert isinstance(lib.helm_last_error(), bytes)   # "" unless an earlier call failed
 
 
 def test_setup_rejects_bad_grid_without_touching_the_device(lib):
     class Grid(ctypes.Structure):
         _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
-                    ("theta_gamma", ctypes.c_double)]
+                    ("theta_gamma", ctypes.c_double), ("ecs_sides", ctypes.c_int)]
     lib.helm_setup.restype = ctypes.c_int
     lib.helm_last_error.restype = ctypes.c_char_p
     out = ctypes.c_void_p()
@@ -73,7 +73,7 @@ def test_setup_rejects_a_basis_longer_than_the_limit(lib):
     """min(restart, maxit) above HELM_MAX_BASIS is refused before any device work."""
     class Grid(ctypes.Structure):
         _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
-                    ("theta_gamma", ctypes.c_double)]
+                    ("theta_gamma", ctypes.c_double), ("ecs_sides", ctypes.c_int)]
 
     class Opts(ctypes.Structure):
         _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")] + \
@@ -95,7 +95,7 @@ def test_setup_rejects_a_negative_complex_shift(lib):
     """csl_eps (the complex shifted Laplacian variant's shift) must be finite and >= 0."""
     class Grid(ctypes.Structure):
         _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
-                    ("theta_gamma", ctypes.c_double)]
+                    ("theta_gamma", ctypes.c_double), ("ecs_sides", ctypes.c_int)]
 
     class Opts(ctypes.Structure):
         _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")] + \
@@ -115,7 +115,7 @@ def test_setup_rejects_the_polynomial_smoother_with_a_shift(lib):
     """The polynomial smoother (Sec. 4) is built for the CSG preconditioner alone."""
     class Grid(ctypes.Structure):
         _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
-                    ("theta_gamma", ctypes.c_double)]
+                    ("theta_gamma", ctypes.c_double), ("ecs_sides", ctypes.c_int)]
 
     class Opts(ctypes.Structure):
         _fields_ = [(f, ctypes.c_int) for f in ("nu1", "nu2", "s", "coarsest_n", "precond_prec", "restart", "maxit")] + \
@@ -131,6 +131,21 @@ def test_setup_rejects_the_polynomial_smoother_with_a_shift(lib):
                         ctypes.byref(out))
     assert rc == -1 and out.value is None
     assert b"polynomial smoother" in lib.helm_last_error()
+
+
+def test_setup_rejects_an_unknown_layer_placement(lib):
+    class Grid(ctypes.Structure):
+        _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("ecs_frac", ctypes.c_double),
+                    ("theta_gamma", ctypes.c_double), ("ecs_sides", ctypes.c_int)]
+    lib.helm_setup.restype = ctypes.c_int
+    lib.helm_last_error.restype = ctypes.c_char_p
+    out = ctypes.c_void_p()
+    for sides, frac, word in ((2, 0.125, b"ecs_sides"), (0, 0.6, b"ecs_frac"), (1, 1.0, b"ecs_frac")):
+        g = Grid(2, 15, frac, 0.5, sides)
+        rc = lib.helm_setup(ctypes.byref(g), None, ctypes.c_double(1.0), ctypes.c_double(0.3), None, None,
+                            ctypes.byref(out))
+        assert rc == -1 and out.value is None
+        assert word in lib.helm_last_error()
 
 
 def test_binding_declares_every_double_parameter_as_double():

@@ -1,0 +1,110 @@
+"""GPU parity on Benchmark 3 of Sec. 5 (the Gaussian model): one-sided ECS layers
+(Dirichlet south and west edges, layers north and east) and the field
+phi = nu (e^{-x^2} + e^{-y^2}) + k^2 of ``inputs.gaussian_model``, through the C ABI
+against the FP64 oracle.
+
+Tolerances are those of the other parity tests: operator c128 1e-13 / c64 1e-6,
+one V-cycle c128 1e-11 / c64 5e-5 (relative 2-norm); FGMRES: the true residual under
+the oracle's H meets the tolerance and the iteration count stays within +10% (+1) of
+the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1012_5379_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def helm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_5379_gb300 import build, helm as H
+    build.build()
+    H.load()
+    return H
+
+
+def dev(a, prec="c128"):
+    t = torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    return t.to(torch.complex64) if prec == "c64" else t
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.complex128) - b) / np.linalg.norm(b))
+
+
+def oracle_levels(w):
+    return O.build_hierarchy(w.dim, w.n, w.theta_beta, w.theta_gamma, w.ecs_frac, phi=w.phi.astype(np.float64),
+                             ecs_sides="high")
+
+
+def handle(helm, w, prec, **kw):
+    return helm.Handle(w.dim, w.n, w.theta_beta, phi=torch.from_numpy(w.phi).cuda(), precision=prec,
+                       theta_gamma=w.theta_gamma, ecs_frac=w.ecs_frac, ecs_sides="high", **kw)
+
+
+@pytest.mark.parametrize("nint,k,nu,prec", [(64, 0.5, 7.0, "c128"), (64, 0.5, 7.0, "c64"),
+                                            (128, 1.5, 1.0, "c128"), (128, 1.5, 7.0, "c64")])
+def test_operator_and_vcycle(helm, nint, k, nu, prec):
+    w = I.gaussian_model(nint, k, nu)
+    levels = oracle_levels(w)
+    h = handle(helm, w, prec)
+    v = I.random_source(2, w.n, 51)
+    for which in "MH":
+        want = levels[0].apply(v) if which == "M" else levels[0].apply_h(v)
+        vt = dev(v, prec)
+        wt = torch.empty_like(vt)
+        h.apply_operator(vt, wt, which)
+        assert rel(wt.cpu().numpy(), want) < (1e-13 if prec == "c128" else 1e-6), which
+    want = O.vcycle(levels, w.b)
+    bt = dev(w.b, prec)
+    zt = torch.empty_like(bt)
+    h.precond_apply(bt, zt)
+    assert rel(zt.cpu().numpy(), want) < (1e-11 if prec == "c128" else 5e-5)
+
+
+def test_one_sided_layers_in_3d(helm):
+    """The layer placement applies to every axis: a 3D grid with far-end layers and a
+    constant k, operator and one V-cycle in c128."""
+    n, k, tb = 15, 4.0, 0.2
+    levels = O.build_hierarchy(3, n, tb, 0.5, 0.25, k=k, ecs_sides="high")
+    h = helm.Handle(3, n, tb, k=k, precision="c128", ecs_frac=0.25, ecs_sides="high")
+    v = I.random_source(3, n, 52)
+    for which in "MH":
+        want = levels[0].apply(v) if which == "M" else levels[0].apply_h(v)
+        vt = dev(v)
+        wt = torch.empty_like(vt)
+        h.apply_operator(vt, wt, which)
+        assert rel(wt.cpu().numpy(), want) < 1e-13, which
+    zt = torch.empty_like(dev(v))
+    h.precond_apply(dev(v), zt)
+    assert rel(zt.cpu().numpy(), O.vcycle(levels, v)) < 1e-11
+
+
+@pytest.mark.parametrize("nint,k,nu,prec", [(64, 0.5, 1.0, "c64"), (64, 0.5, 7.0, "c64"),
+                                            (128, 1.5, 7.0, "c64"), (64, 0.5, 7.0, "c128")])
+def test_fgmres_solve(helm, nint, k, nu, prec):
+    w = I.gaussian_model(nint, k, nu)
+    levels = oracle_levels(w)
+    _, io = O.fgmres(levels[0].apply_h, lambda v: O.vcycle(levels, v), w.b, tol=w.tol, maxit=600)
+    h = handle(helm, w, prec, maxit=600)
+    bt = dev(w.b)
+    xt = torch.zeros_like(bt)
+    info = h.solve(bt, xt, w.tol)
+    x = xt.cpu().numpy()
+    assert info.status == 0
+    assert np.linalg.norm(w.b - levels[0].apply_h(x)) / np.linalg.norm(w.b) <= w.tol * 1.0001
+    assert info.iters <= int(1.1 * io.iters) + 1, (info.iters, io.iters)
+
+
+def test_layer_placement_argument_checks(helm):
+    with pytest.raises(ValueError):
+        helm.Handle(2, 15, 0.2, k=1.0, ecs_sides="low")
+    with pytest.raises(helm.HelmError):
+        helm.Handle(2, 15, 0.2, k=1.0, ecs_frac=0.6)                    # both sides: < 0.5
+    h = helm.Handle(2, 15, 0.2, k=1.0, ecs_frac=0.6, ecs_sides="high")  # one side: < 1
+    h.close()
