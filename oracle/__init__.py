@@ -17,6 +17,10 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
 * ``spacings`` / ``coefficients_1d`` / ``apply_operator``: pinned (quadrature-built
   node coordinates + Lagrange second-difference matrix, closed-form Dirichlet
   eigenpairs, e^{-2i theta} rotation identity, exactness on complex quadratics).
+* ``complex_map(ecs_sides="high")`` (one-sided layers, Benchmark 3 of Sec. 5): pinned by
+  its closed-form end point and end intervals, exactness on a complex quadratic, and
+  the model's bound-state energy at nu = 7 against an ODE shooting solve
+  (``tests/test_oracle_gaussian.py``, which also holds Tables 4-5 as a soft band).
 * ``restrict_fw`` / ``prolong``: pinned (P = 2^d R^T, exactness on linear fields).
 * ``gmres_sweep``: pinned (brute-force Krylov least squares, residual monotonicity).
 * ``coarse_solve``: pinned (independently assembled matrix times solution).
