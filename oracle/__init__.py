@@ -33,7 +33,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
 * ``polysmoother`` (the third-degree polynomial smoother of Sec. 4): pinned by the
   paper's Fig. ex1 (which phi maps the spectrum inside the unit circle), the critical
   angle of Fig. critical_parameters and the stability of Fig. hierarchy_spectrum_smoother;
-  its V-cycle ``vcycle_poly`` has no printed value beyond those and is unpinned as a cycle.
+  its V-cycle ``vcycle_poly`` is linear and pinned as a cycle by its error propagator
+  (the two-grid recursion with p(M) in Taylor form on both sides, dense matrices on
+  tiny grids) and as a stationary iteration converging to the direct solve.
 """
 from .helmholtz import (  # noqa: F401
     Level,

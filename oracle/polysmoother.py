@@ -31,8 +31,8 @@ Readings (the paper's formulas for phi are partly garbled):
   neither applies no stable polynomial exists and ``choose_phi`` returns None.
 * Constant k only (the triangle's vertices assume phi = k^2 everywhere).
 
-Parity status: pinned by the paper's printed values, see
-``tests/test_oracle_polysmoother.py``: Fig. ex1 (k = 100, theta_gamma = pi/6,
+Parity status: pinned by the paper's printed values and, for the cycle, by its error
+propagator in closed form, see ``tests/test_oracle_polysmoother.py``: Fig. ex1 (k = 100, theta_gamma = pi/6,
 theta_beta = 2 pi/45, h = 1/128: phi = 1.2032 degrees maps the 2D spectrum inside the
 unit circle, 0.6303, 0.81212 and 1.0122 degrees do not), the critical angle of
 Fig. critical_parameters (9.45 degrees) and Fig. hierarchy_spectrum_smoother (all six

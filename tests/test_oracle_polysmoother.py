@@ -113,3 +113,61 @@ def test_polynomial_vcycle_converges_as_a_stationary_iteration():
         errs.append(np.linalg.norm(x - exact) / np.linalg.norm(exact))
     assert all(b < a for a, b in zip(errs, errs[1:]))
     assert errs[-1] < 0.05 * errs[0]
+
+
+def _columns(op, m, shape):
+    """Dense matrix of a linear map on arrays of ``shape`` (m entries), column by column."""
+    out = np.zeros((op(np.zeros(shape, dtype=np.complex128)).size, m), dtype=np.complex128)
+    for j in range(m):
+        e = np.zeros(m, dtype=np.complex128)
+        e[j] = 1.0
+        out[:, j] = op(e.reshape(shape)).ravel()
+    return out
+
+
+def _taylor_poly_matrix(A, k, h, tb, tg, dim):
+    """p(A) = c0 I + c1 (A - t0) + c2 (A - t0)^2 + c3 (A - t0)^3 with the level's phi
+    (Eq. polynomial, Taylor form about t0; independent of the factored weights)."""
+    phi, _ = PS.level_polynomial(k, h, tb, tg, dim)
+    t0, t1, t2 = PS.triangle(k, h, tb, tg, dim)
+    e, f = PS.basis_ef(t0, t1, t2)
+    c = PS.coefficients(e, f, phi)
+    m = A.shape[0]
+    S = A - t0 * np.eye(m)
+    return c[0] * np.eye(m) + S @ (c[1] * np.eye(m) + S @ (c[2] * np.eye(m) + c[3] * S))
+
+
+@pytest.mark.parametrize("dim,n", [(2, 7), (2, 15), (3, 7)])
+def test_polynomial_vcycle_equals_its_error_propagator(dim, n):
+    """With fixed weights the polynomial-smoothed V(1,1) cycle is linear, b -> B b, and
+    its error propagator obeys the two-grid recursion of Sec. 3.1 with the smoother's
+    e <- p(M) e of Sec. 4.1 on both sides:
+        I - B_l M_l = p(M_l) (I - P_l B_{l+1} R_l M_l) p(M_l),   B_coarsest = M^{-1}.
+    B is read column by column off ``vcycle_poly``; the right-hand side is built from
+    dense matrices, p(M) in its Taylor form."""
+    k, tb, tg = 0.2 * (n + 1), np.radians(10.0), np.radians(30.0)
+    levels = O.build_hierarchy(dim, n, tb, tg, 0.125, k=k)
+    weights = PS.hierarchy_weights(levels, k, tb, tg)
+    want = None
+    for li in range(len(levels) - 1, -1, -1):
+        lev = levels[li]
+        M = O.helmholtz.dense_matrix(lev)
+        m = M.shape[0]
+        if li == len(levels) - 1:
+            want = np.linalg.inv(M)
+            continue
+        nc = levels[li + 1].n
+        R = _columns(O.restrict_fw, m, (lev.n,) * dim)
+        P = _columns(lambda ec: O.prolong(ec, lev.n), nc ** dim, (nc,) * dim)
+        pM = _taylor_poly_matrix(M, k, 1.0 / (lev.n + 1), tb, tg, dim)
+        E = pM @ (np.eye(m) - P @ want @ R @ M) @ pM
+        want = (np.eye(m) - E) @ np.linalg.inv(M)
+    shape = (n,) * dim
+    got = _columns(lambda b: PS.vcycle_poly(levels, weights, b), n ** dim, shape)
+    assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want)
+    # linearity, the property the closed form rests on
+    rng = np.random.default_rng(9)
+    b1, b2 = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape) for _ in range(2))
+    lhs = PS.vcycle_poly(levels, weights, 2.0 * b1 - 3.0j * b2)
+    rhs = 2.0 * PS.vcycle_poly(levels, weights, b1) - 3.0j * PS.vcycle_poly(levels, weights, b2)
+    assert np.linalg.norm(lhs - rhs) <= 1e-11 * np.linalg.norm(rhs)
