@@ -315,6 +315,37 @@ def test_gmres_breakdown_returns_exact_solution():
     assert np.linalg.norm(got - mode / lam) / np.linalg.norm(mode / lam) < 1e-12
 
 
+@pytest.mark.parametrize("s", [1, 2, 3, 4])
+def test_vcycle_is_exact_on_s_eigenvectors(s):
+    """A source spanned by s eigenvectors of M (sine modes, no stretching) lies in an
+    s-dimensional invariant Krylov space: the pre-smoothing GMRES(s) sweep solves it
+    exactly, the residual it leaves is rounding, and the whole V(1,1) cycle returns
+    M^{-1} b.  With s + 1 modes the sweep is no longer exact and neither is the cycle."""
+    n, k = 31, 9.0
+    levels = O.build_hierarchy(2, n, 0.0, theta_gamma=0.0, ecs_frac=WF, k=k)
+    h = 1 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    modes = [(1, 1), (2, 3), (5, 1), (4, 6), (7, 2)]
+
+    def source(count):
+        b = np.zeros((n, n), dtype=np.complex128)
+        exact = np.zeros_like(b)
+        for i, (jx, jy) in enumerate(modes[:count]):
+            mode = np.outer(np.sin(jy * np.pi * x), np.sin(jx * np.pi * x))
+            lam = -k * k + 4 / h ** 2 * (np.sin(jx * np.pi * h / 2) ** 2 + np.sin(jy * np.pi * h / 2) ** 2)
+            coef = (1.0 + 0.5j) * (i + 1)
+            b += coef * mode
+            exact += coef * mode / lam
+        return b, exact
+
+    b, exact = source(s)
+    got = O.vcycle(levels, b, 1, 1, s)
+    assert np.linalg.norm(got - exact) <= 1e-10 * np.linalg.norm(exact)
+    b, exact = source(s + 1)
+    got = O.vcycle(levels, b, 1, 1, s)
+    assert np.linalg.norm(got - exact) > 1e-6 * np.linalg.norm(exact)
+
+
 def test_zero_rhs_sweep_and_vcycle():
     levels = O.build_hierarchy(2, 15, 0.3, TG, WF, k=5.0)
     z = np.zeros((15, 15), dtype=np.complex128)
