@@ -24,7 +24,7 @@ def paper_levels(k, nint, tb):
     return O.build_hierarchy(2, n, tb, TG, 1.0 / 6.0, k=1.5 * k), I.point_source(2, n)
 
 
-@pytest.mark.parametrize("col", [0, 1])
+@pytest.mark.parametrize("col", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("cyc", ["1,0", "1,1", "2,1"])
 def test_table2_fgmres_iterations(cyc, col):
     t2 = GOLD["table2"]
