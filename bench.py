@@ -470,6 +470,19 @@ def run_cube(args):
     print(json.dumps(out), flush=True)
 
 
+def gauss_key(nu, k, nint, cycle):
+    """Key of one Gaussian-model solve in tests/golden/oracle_iters_gauss.json."""
+    return f"nu={nu:g} k={k:g} nint={nint} V({cycle})"
+
+
+def gauss_oracle_iters(path):
+    """The FP64 oracle's iteration counts of the Gaussian-model solves (a stored file
+    written from the oracle alone), or {} if the file is absent."""
+    if not os.path.exists(path):
+        return {}
+    return {key: v["iters"] for key, v in json.load(open(path))["iters"].items()}
+
+
 def run_gauss(args):
     """Benchmark 3 of Sec. 5, the Gaussian model: the five (k, grid) columns of
     Tables 4 and 5 for nu = 1 and nu = 7, V(1,0) and V(1,1) preconditioners (GMRES(3)
@@ -479,8 +492,9 @@ def run_gauss(args):
 
     from paper_1012_5379_gb300 import helm
     dev = torch.device("cuda", 0)
-    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
-                                       "paper_tables.json")))
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden")
+    gold = json.load(open(os.path.join(golden, "paper_tables.json")))
+    oracle_iters = gauss_oracle_iters(os.path.join(golden, "oracle_iters_gauss.json"))
     rows = []
     for table, nu in (("table4", 1.0), ("table5", 7.0)):
         for col, (k, nint) in enumerate(I.GAUSS_COLUMNS):
@@ -503,6 +517,7 @@ def run_gauss(args):
                 torch.cuda.synchronize()
                 sec = e0.elapsed_time(e1) * 1e-3
                 rows.append({"nu": nu, "k": k, "nint": nint, "n": w.n, "cycle": cyc, "iters": info.iters,
+                             "oracle_iters": oracle_iters.get(gauss_key(nu, k, nint, cyc)),
                              "paper_iters": gold[table]["iters"][cyc][col], "status": info.status,
                              "rel_res_true": info.rel_res_true, "s": sec,
                              "vcycle_mpts_per_s": float(w.n) ** 2 * info.iters / sec / 1e6})

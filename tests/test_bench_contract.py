@@ -29,3 +29,17 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_gaussian_mode_finds_the_oracle_count_of_every_solve():
+    """bench.py --mode gauss prints the FP64 oracle's count beside each GPU solve; every
+    (nu, column, cycle) it runs has one in the stored file."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1012_5379_gb300 import inputs as I
+    counts = bench.gauss_oracle_iters(os.path.join(ROOT, "tests", "golden", "oracle_iters_gauss.json"))
+    for nu in (1.0, 7.0):
+        for k, nint in I.GAUSS_COLUMNS:
+            for cycle in ("1,0", "1,1"):
+                assert isinstance(counts[bench.gauss_key(nu, k, nint, cycle)], int)
+    assert bench.gauss_oracle_iters(os.path.join(ROOT, "tests", "golden", "absent.json")) == {}
