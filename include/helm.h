@@ -116,9 +116,12 @@ typedef struct {
  *   opts may be NULL (all defaults).  opts->csl_eps > 0 (constant k only) adds the
  *         complex shift of the CSL variant: M = L - (1 + i csl_eps) k^2 on every level,
  *         the stretched-grid angle applying as well (theta_beta = 0: pure CSL).
- * Errors: HELM_EINVAL (dim, n, angles, ecs_frac, opts out of range, csl_eps with a
- * phi field), HELM_ENOMEM, HELM_ECUDA.  The call synchronises `stream` before
- * returning. */
+ *   grid->ecs_sides = HELM_ECS_HIGH places the layers at the far end of every axis
+ *         only (Dirichlet near edges, Benchmark 3 of Sec. 5); the hierarchy, the
+ *         kernels and every other call are unchanged.
+ * Errors: HELM_EINVAL (dim, n, angles, ecs_frac, ecs_sides, opts out of range,
+ * csl_eps with a phi field), HELM_ENOMEM, HELM_ECUDA.  The call synchronises `stream`
+ * before returning. */
 int helm_setup(const helm_grid* grid, const float* phi, double k, double theta_beta,
                const helm_opts* opts, void* stream, helm_handle** out);
 
