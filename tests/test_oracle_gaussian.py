@@ -6,7 +6,8 @@ phi = nu (e^{-x^2} + e^{-y^2}) + k^2 on (0, 50)^2 mapped to the unit box.
   z(1) = (1 - w) e^{i theta_beta} + w e^{i theta_gamma}, start at h e^{i theta_beta} and
   end at h e^{i theta_gamma}; the both-sided map keeps its own closed form.
 - The three-point scheme is exact on a quadratic in the complex coordinate that
-  vanishes on both ends of the one-sided map (u = z (Z - z), -u'' = 2).
+  vanishes on both ends of the one-sided map (u = z (Z - z), -u'' = 2), and the
+  spectrum of M stays in the triangle of Lemma 2.1.
 - Bound states (Sec. 5): the 1D operator of the model, -d^2/dx^2 - nu e^{-x^2} with a
   Dirichlet end at 0 and an ECS layer at the far end, has an eigenvalue on the negative
   real axis for nu = 7 equal to the bound-state energy of the continuous problem (found
@@ -56,6 +57,22 @@ def test_one_sided_scheme_is_exact_on_a_complex_quadratic():
     want = 2.0 * (q[None, :] + q[:, None])
     got = lev.apply(u.astype(np.complex128))
     assert np.max(np.abs(got - want)) < 1e-9 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("dim,n,k,w", [(2, 15, 3.0, 0.2), (2, 31, 10.0, 0.3), (3, 7, 2.0, 0.25)])
+def test_one_sided_spectrum_in_lemma_triangle(dim, n, k, w):
+    """Lemma 2.1 with the layers at the far end only: sigma(M) still lies in the
+    triangle t0 = -k^2, t1 = -k^2 + 4d/h_b^2, t2 = -k^2 + 4d/h_g^2 (soft gate, slack
+    1e-8 in barycentric coordinates)."""
+    lev = O.build_hierarchy(dim, n, TB, TG, w, k=k, ecs_sides="high")[0]
+    ev = np.linalg.eigvals(O.helmholtz.dense_matrix(lev))
+    h = 1.0 / (n + 1)
+    t0 = -k * k
+    t1 = t0 + 4 * dim / (h * np.exp(1j * TB)) ** 2
+    t2 = t0 + 4 * dim / (h * np.exp(1j * TG)) ** 2
+    T = np.array([[t0, t1.real, t2.real], [0.0, t1.imag, t2.imag], [1.0, 1.0, 1.0]])
+    for lam in ev:
+        assert np.linalg.solve(T, np.array([lam.real, lam.imag, 1.0])).min() > -1e-8, lam
 
 
 def _operator_1d(nu, n=639, lam=40.0, w=0.2):
