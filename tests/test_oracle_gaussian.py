@@ -13,7 +13,8 @@ phi = nu (e^{-x^2} + e^{-y^2}) + k^2 on (0, 50)^2 mapped to the unit box.
   real axis for nu = 7 equal to the bound-state energy of the continuous problem (found
   here by shooting with an ODE integrator, independent of the oracle) within the
   scheme's O(h^2) error, and none for nu = 2.5; for nu = 3 it has one (the paper puts
-  the threshold at about 2.73).
+  the threshold at about 2.73).  As the paper observes, they hamper the V-cycle: its
+  stationary iteration converges fast for nu = 1 and slowly for nu = 7.
 - Soft pins: the outer FGMRES iteration counts of Tables 4 and 5 (64^2, 128^2 and
   256^2 columns, V(1,0) and V(1,1)) within -30% / +35%: the paper leaves the layer width and
   the tolerance of these runs unstated (readings in ``inputs.gaussian_model``); and,
@@ -144,6 +145,27 @@ def test_tables_4_5_fgmres_iterations(table, col):
         want = t["iters"][cyc][col]
         assert 0.7 * want <= got[cyc] <= 1.35 * want, (table, col, cyc, got[cyc], want)
     assert got["1,1"] < got["1,0"]
+
+
+def test_bound_states_hamper_the_vcycle():
+    """Sec. 5: the isolated bound-state eigenvalues hamper multigrid on the
+    preconditioner.  Iterated as x <- x + V(b - M x) on the 64^2, k = 0.5 model, the
+    V(1,1) cycle with one-sided layers converges at a textbook rate for nu = 1 (down to
+    rounding within 25 cycles) and stalls to a slow asymptotic rate for nu = 7 (still
+    below 1)."""
+    rates = {}
+    for nu in (1.0, 7.0):
+        w = I.gaussian_model(64, 0.5, nu)
+        levels = O.build_hierarchy(2, w.n, w.theta_beta, w.theta_gamma, w.ecs_frac,
+                                   phi=w.phi.astype(np.float64), ecs_sides="high")
+        x = np.zeros_like(w.b)
+        res = [np.linalg.norm(w.b)]
+        for _ in range(25):
+            x = x + O.vcycle(levels, w.b - levels[0].apply(x))
+            res.append(np.linalg.norm(w.b - levels[0].apply(x)))
+        rates[nu] = ((res[10] / res[0]) ** 0.1, (res[25] / res[15]) ** 0.1, res[-1] / res[0])
+    assert rates[1.0][0] < 0.25 and rates[1.0][2] < 1e-13
+    assert 0.5 < rates[7.0][1] < 1.0 and rates[7.0][2] < 1e-3
 
 
 def test_bound_states_make_the_low_wavenumber_solve_harder():
