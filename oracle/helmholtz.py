@@ -2,7 +2,8 @@
 
 Notation follows the paper: H u = -(Laplacian + phi) u = chi (Eq. helm, Sec. 1), with
 phi = k^2.  Grids are the unit interval per axis with N interior nodes, real spacing
-h = 1/(N+1); u = 0 on the outer edge of the absorbing layers.  Arrays are
+h = 1/(N+1); u = 0 on the outer edge of the absorbing layers (and on the near edge of
+the interior where the layers sit at the far end only, Benchmark 3 of Sec. 5).  Arrays are
 ``(N,)*d`` complex128 with the x axis last (C order), i.e. flat index
 ``(iz*N + iy)*N + ix``.
 """
