@@ -170,3 +170,18 @@ def test_bound_states_hamper_the_vcycle():
 
 def test_bound_states_make_the_low_wavenumber_solve_harder():
     assert _fgmres_iters(64, 0.5, 7.0, 1, 1) > 2 * _fgmres_iters(64, 0.5, 1.0, 1, 1)
+
+
+def test_gaussian_model_layout():
+    """The workload's grid and layer (reading in ``inputs.gaussian_model``): n = 1.25 nint
+    - 1 unknowns per axis, a layer of nint/4 intervals (1/5 of the box), the source
+    vanishing to rounding in the layer and phi reaching k^2 (scaled) there."""
+    w = I.gaussian_model(64, 0.5, 7.0)
+    lam = 50.0 * 80 / 64
+    assert w.n == 79 and abs(w.ecs_frac - 0.2) < 1e-15 and w.ecs_sides == "high"
+    layer = slice(63, None)                 # 0-based node i sits at (i + 1) lam / 80: x >= 50
+    assert np.abs(w.b[layer, :]).max() == 0.0 and np.abs(w.b[:, layer]).max() == 0.0
+    assert abs(w.phi[-1, -1] / lam ** 2 - 0.25) < 1e-6
+    assert abs(w.phi[0, 0] / lam ** 2 - (7.0 * 2 * np.exp(-(lam / 80) ** 2) + 0.25)) < 1e-5
+    with pytest.raises(ValueError):
+        I.gaussian_model(66, 0.5, 1.0)
