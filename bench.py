@@ -4,13 +4,16 @@ flexible GMRES solve (arXiv:1012.5379), on GB300.
 
 Metric: V-cycle Mpts/s = fine-grid unknowns x V-cycles / second over whole solves to
 relative residual 1e-6 (one V-cycle per outer iteration).  A step is one pass of the
-whole hot path over one batch of synthetic input: the full FGMRES solve of the
-2D 1023^2, k = 160 problem with a unit-variance complex normal source for each CSG
-angle theta_beta in {0.1, 0.2, 0.3, 0.5} (complex64 V-cycle, FP64 outer).
+whole hot path over one batch of synthetic input: the full FGMRES(40) solve of the 3D
+255^3 heterogeneous problem (unit cube, k(x) = 80 (1 + 0.3 g(x)) with 8 seeded Gaussian
+bumps, point source, theta_beta 0.4, ECS layers 1/8 at 0.5 rad; complex64 V(1,1)
+GMRES(3) V-cycle, FP64 outer), the largest single-GPU workload.  Extra keys of the same
+line: the 2D 1023^2 theta_beta sweep (four solves batched), the 64-problem batch in
+solves/s, and a short Poisson serving run with p50/p99 latency.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU: replicas only (each rank solves its own copy of the sweep; the only
+Multi-GPU: replicas only (each rank solves its own copy of the step; the only
 collectives are a barrier and the max-over-ranks time).  Prints one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -23,6 +26,7 @@ for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
 import argparse  # noqa: E402
 import hashlib  # noqa: E402
 import json  # noqa: E402
+import platform  # noqa: E402
 import statistics  # noqa: E402
 import subprocess  # noqa: E402
 import sys  # noqa: E402
@@ -39,22 +43,37 @@ from paper_1012_5379_gb300 import inputs as I  # noqa: E402
 METRIC = "V-cycle Mpts/s"
 UNIT = "Mpts/s"
 TOL = 1e-6
-N = 1023
+CUBE_N = 255
+N = 1023          # the 2D theta_beta sweep (extra key)
 K = 160.0
 BETAS = I.LARGE_2D_BETAS
 # FP64 peak: ncu's sustained DFMA peak on GB300 is 2 per SM per cycle (304 per cycle on 152
 # SMs), x 2 flop x 2.07 GHz = 1.26 TFLOP/s, the recipe's nominal 1.25 TFLOP/s
 FP64_PEAK_TFLOPS = 1.25
+FP64_CLASSES = ("out.dots", "out.vnew", "out.apply_h")
 
 
 def workload_config():
-    return {"workload": "2D Helmholtz 1023^2 interior, k=160 (kh=0.156), unit-variance complex normal source "
-                        "(seed 1001), ECS layer 1/8 per side at 0.5 rad, CSG theta_beta swept over "
-                        "{0.1,0.2,0.3,0.5}; V(1,1) GMRES(3) multigrid in complex64 down to 3x3, FP64 FGMRES "
-                        "(no restart) to rel. residual 1e-6; one step = the four solves, batched",
-            "n": N, "dim": 2, "k": K, "betas": list(BETAS), "tol": TOL, "levels": 9,
-            "l2": "flushed between steps (256 MiB write) outside the per-step event timing; the FGMRES "
-                  "basis (> 1 GB per solve) exceeds L2 anyway"}
+    return {"workload": "3D Helmholtz 255^3 interior on the unit cube, heterogeneous k(x)=80(1+0.3 g(x)) with g a "
+                        "seeded sum of 8 Gaussian bumps (sigma 0.1, seed 1002) clipped to [-1,1], unit point source "
+                        "at the centre, ECS layers 1/8 per face at 0.5 rad, CSG theta_beta 0.4; V(1,1) GMRES(3) "
+                        "multigrid in complex64 down to 3^3, FP64 FGMRES(40) to rel. residual 1e-6; one step = one "
+                        "full solve",
+            "n": CUBE_N, "dim": 3, "k": "80(1+0.3g(x))", "theta_beta": 0.4, "tol": TOL, "restart": 40, "levels": 7,
+            "l2": "inputs larger than L2: every level-0 vector is 134 MB and the FGMRES(40) basis 10.6 GB, "
+                  "so no step reuses the previous step's data from the 126 MB L2"}
+
+
+def host_info():
+    cpu = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                cpu = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": cpu, "machine": platform.machine()}
 
 
 # ------------------------------------------------------------------ helpers
@@ -169,6 +188,33 @@ def vcycle_hbm(classes, peak_gbs):
 
 
 # ------------------------------------------------------------------ our arm
+def roofline_of(dominant, d, pk):
+    """Roofline object of one kernel class: FP64 classes against the DFMA pipe (their
+    bound on GB300), the rest against the measured HBM copy bandwidth."""
+    nl = max(d["launches"], 1)
+    if dominant in FP64_CLASSES and d["flops"] > 0:
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for(dominant, d["bytes"] / nl),
+                "kernel": dominant,
+                "peak_source": "FP64 DFMA pipe: 2 DFMA/SM/cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz "
+                               "(= recipe nominal 1.25 TFLOP/s; MEASURED_PEAKS.json has no FP64 figure)",
+                "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / nl,
+                "algorithmic_flops_per_launch": d["flops"] / nl, "algorithmic_bytes_per_launch": d["bytes"] / nl}
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    peak = pk.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_for(dominant, d["bytes"] / nl), "kernel": dominant,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "recipe fallback",
+            "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / nl,
+            "algorithmic_bytes_per_launch": d["bytes"] / nl}
+
+
+def class_shares(classes):
+    tot = sum(v["ms"] for v in classes.values()) or 1.0
+    return {c: round(v["ms"] / tot, 4) for c, v in sorted(classes.items(), key=lambda kv: -kv[1]["ms"])}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -178,46 +224,37 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    b_np = I.random_source(2, N, 1001)
-    b = torch.from_numpy(b_np).to(dev)
-    handles = [helm.Handle(2, N, tb, k=K, precision="c64", maxit=args.maxit) for tb in BETAS]
-    xs = [torch.zeros_like(b) for _ in BETAS]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    w = I.cube_3d(CUBE_N)
+    pts = float(w.n) ** 3
+    b = torch.from_numpy(w.b).to(dev)
+    phi = torch.from_numpy(w.phi).to(dev)
+    h = helm.Handle(3, w.n, w.theta_beta, phi=phi, precision="c64", restart=w.restart, maxit=400)
+    x = torch.zeros_like(b)
 
     def step():
-        # the four independent theta_beta solves share every launch (helm_batch_solve)
-        for x in xs:
-            x.zero_()
-        infos = helm.batch_solve(handles, [b] * len(handles), xs, TOL)
-        for info in infos:
-            if info.status != 0:
-                raise RuntimeError(f"solve did not converge: {info}")
-        return [info.iters for info in infos]
-
-    def step_sequential():
-        iters = []
-        for h, x in zip(handles, xs):
-            x.zero_()
-            info = h.solve(b, x, TOL)
-            if info.status != 0:
-                raise RuntimeError(f"solve did not converge: {info}")
-            iters.append(info.iters)
-        return iters
+        x.zero_()
+        info = h.solve(b, x, w.tol)
+        if info.status != 0:
+            raise RuntimeError(f"solve did not converge: {info}")
+        return info.iters
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    # warm-up; the first warm-up step times every kernel class to find the dominant one
+    # warm-up; the first warm-up step times every kernel class with CUDA events around
+    # each launch: one problem on one stream, so the classes' times are serialised
     classes = {}
-    for w in range(args.warmup):
-        if w == 0:
+    for i in range(args.warmup):
+        if i == 0:
             helm.profile_begin("")
         step()
-        if w == 0:
+        if i == 0:
             classes = helm.profile_end()
     dominant = max(classes, key=lambda c: classes[c]["ms"]) if classes else "out.dots"
 
+    # timed region: per-step CUDA events on the solve's stream; events bracket only the
+    # dominant class's launches (a few dozen per solve) for its live roofline
     sampler = ClockSampler(local_rank)
     barrier()
     torch.cuda.synchronize()
@@ -226,11 +263,10 @@ def run_ours(args, rank, world, local_rank):
     helm.profile_begin(dominant)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     all_iters = []
-    for s in range(args.steps):
-        flush.fill_(float(s))
-        ev[s][0].record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
         all_iters.append(step())
-        ev[s][1].record(stream)
+        ev[i][1].record(stream)
     torch.cuda.synchronize()
     barrier()
     prof = helm.profile_end()
@@ -238,144 +274,213 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
     ms_steps = [a.elapsed_time(c) for a, c in ev]
     ms_total = float(sum(ms_steps))
-    pts = float(N * N)
-    work = pts * sum(sum(i) for i in all_iters)
+    work = pts * sum(all_iters)
     if world > 1:
         ms_total, work = reduce_over_ranks(ms_total, work, dev)
     value = work / (ms_total * 1e-3) / 1e6
-
-    # roofline of the dominant kernel class, live from the timed region
     pk = peaks()
-    d = prof.get(dominant, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
-    nl = max(d["launches"], 1)
-    if dominant.startswith("out.dots") or dominant.startswith("out.vnew"):
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for(dominant, d["bytes"] / nl),
-                "kernel": dominant,
-                "peak_source": "FP64 DFMA pipe: 2 DFMA/SM/cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz "
-                               "(= recipe nominal 1.25 TFLOP/s; MEASURED_PEAKS.json has no FP64 figure)",
-                "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / nl,
-                "algorithmic_flops_per_launch": d["flops"] / nl, "algorithmic_bytes_per_launch": d["bytes"] / nl}
-    else:
-        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-        peak = pk.get("hbm_gbs", 6800.0)
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_for(dominant, d["bytes"] / nl), "kernel": dominant,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "recipe fallback",
-                "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / nl,
-                "algorithmic_bytes_per_launch": d["bytes"] / nl}
+    roof = roofline_of(dominant, prof.get(dominant, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0}), pk)
+    roof["selected_by"] = ("largest serialised class time in the first warm-up solve (CUDA events around every "
+                           "launch, one stream); achieved from events around this class's launches in the timed "
+                           "steps")
 
-    # one V-cycle of the workload on its own (no concurrent outer passes): its passes'
-    # algorithmic bandwidth against HBM
-    r64 = b.to(torch.complex64)
-    z64 = torch.empty_like(r64)
-    for _ in range(3):
-        handles[0].precond_apply(r64, z64)
-    torch.cuda.synchronize()
-    helm.profile_begin("")
-    for _ in range(10):
-        handles[0].precond_apply(r64, z64)
-    torch.cuda.synchronize()
-    vc_alone = vcycle_hbm(helm.profile_end(), pk.get("hbm_gbs", 6800.0))
-    if vc_alone:
-        vc_alone["note"] = ("10 V-cycles of the theta_beta 0.1 problem alone; every level of a 1023^2 "
-                            "problem fits in L2 (129 MB), so the passes are latency-bound, not HBM-bound")
-    del r64, z64
-
-    # the same step solved one problem at a time (context: what batching buys)
-    seq = None
-    if args.sequential_steps > 0:
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        swork = 0.0
-        for _ in range(args.sequential_steps):
-            swork += pts * sum(step_sequential())
-        e1.record(stream)
-        torch.cuda.synchronize()
-        seq = {"value": swork / (e0.elapsed_time(e1) * 1e-3) / 1e6, "unit": UNIT,
-               "ms_per_step": e0.elapsed_time(e1) / args.sequential_steps, "api": "helm_solve, one problem at a time"}
-
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers: helm_solve_host copies b to
+    # the device, solves and copies x back (pinned host memory)
     e2e = None
     if args.e2e_steps > 0:
         bh = torch.empty(b.shape, dtype=torch.complex128, pin_memory=True)
-        bh.copy_(torch.from_numpy(b_np))
-        xhs = [torch.empty_like(bh, pin_memory=True) for _ in handles]
-        bh_np, xh_nps = bh.numpy(), [x.numpy() for x in xhs]
+        bh.copy_(torch.from_numpy(w.b))
+        xh = torch.empty_like(bh, pin_memory=True)
+        bh_np, xh_np = bh.numpy(), xh.numpy()
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ework = 0.0
         for _ in range(args.e2e_steps):
-            infos = helm.batch_solve_host(handles, [bh_np] * len(handles), xh_nps, TOL)
-            ework += pts * sum(i.iters for i in infos)
+            info = h.solve_host(bh_np, xh_np, w.tol)
+            ework += pts * info.iters
         torch.cuda.synchronize()
         et = time.perf_counter() - t0
         if world > 1:
             et, ework = reduce_over_ranks(et, ework, dev)
-        e2e = {"value": ework / et / 1e6, "unit": UNIT, "h2d_bytes_per_step": len(BETAS) * N * N * 16,
-               "d2h_bytes_per_step": len(BETAS) * N * N * 16, "steps": args.e2e_steps,
-               "api": "helm_batch_solve_host"}
-
+        e2e = {"value": ework / et / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(pts * 16),
+               "d2h_bytes_per_step": int(pts * 16), "steps": args.e2e_steps, "api": "helm_solve_host"}
+    iters = all_iters[-1]
+    h.close()
+    del h, b, x, phi
+    torch.cuda.empty_cache()
     if rank != 0:
         return None
-    iters = all_iters[-1]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64+c128", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
             "config": workload_config(), "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "iters_per_beta": dict(zip([str(t) for t in BETAS], iters)),
-            "solves_per_s": len(BETAS) * args.steps * world / (ms_total * 1e-3),
-            "ms_steps": ms_steps, "kernel_classes_warmup": classes, "sequential": seq,
-            "vcycle_hbm": vc_alone,
-            "solve_mode": "batched: the four theta_beta solves of a step share every launch (helm_batch_solve)"}
+            "clocks": clocks, "iters": iters, "solves_per_s": args.steps * world / (ms_total * 1e-3),
+            "ms_steps": ms_steps,
+            "kernel_classes_warmup": classes, "kernel_class_shares_warmup": class_shares(classes),
+            "vcycle_hbm": vcycle_hbm(classes, pk.get("hbm_gbs", 6800.0))}
+    if line["vcycle_hbm"]:
+        line["vcycle_hbm"]["note"] = ("V-cycle classes of the first warm-up solve (serialised, one stream), "
+                                      "algorithmic bytes over CUDA-event time")
+    if world == 1 and not args.no_extras:
+        line["sweep_2d"] = sweep_2d(args, dev)
+        line["batch_64"] = batch_extra(args)
+        line["serving"] = serving_extra(args)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+        line["cpu_baseline"] = cpu_baseline()
     else:
         line["cpu_baseline"] = None
     return line
 
 
+def sweep_2d(args, dev):
+    """The 2D 1023^2 workload (k = 160, unit-variance complex normal source, theta_beta
+    0.1 / 0.2 / 0.3 / 0.5 solved together with helm_batch_solve, complex64 V-cycle, FP64
+    FGMRES without restart to 1e-6): V-cycle Mpts/s over whole solves."""
+    import torch
+
+    from paper_1012_5379_gb300 import helm
+    b = torch.from_numpy(I.random_source(2, N, 1001)).to(dev)
+    handles = [helm.Handle(2, N, tb, k=K, precision="c64", maxit=300) for tb in BETAS]
+    xs = [torch.zeros_like(b) for _ in BETAS]
+
+    def step():
+        for x in xs:
+            x.zero_()
+        infos = helm.batch_solve(handles, [b] * len(handles), xs, TOL)
+        if any(i.status != 0 for i in infos):
+            raise RuntimeError("2D sweep solve did not converge")
+        return [i.iters for i in infos]
+
+    for _ in range(2):
+        step()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ms, iters = 0.0, None
+    for i in range(3):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        iters = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    for h in handles:
+        h.close()
+    del handles, xs, b, flush
+    torch.cuda.empty_cache()
+    return {"value": float(N * N) * sum(iters) * 3 / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / 3,
+            "iters_per_beta": dict(zip([str(t) for t in BETAS], iters)), "steps": 3,
+            "workload": "2D 1023^2, k=160, random source (seed 1001), theta_beta {0.1,0.2,0.3,0.5} batched, "
+                        "complex64 V(1,1)-GMRES(3) / FP64 FGMRES to 1e-6; L2 flushed between steps"}
+
+
+def batch_extra(args):
+    """The 64-problem batch (--mode batch) in solves/s, as a sub-object."""
+    return _capture_mode(run_batch, args, batch=args.batch, steps=1, warmup=1)
+
+
+def serving_extra(args):
+    """A short Poisson serving run (--mode serve) with p50/p99 latency, as a sub-object."""
+    return _capture_mode(run_serve, args, requests=args.serve_requests, rate=args.serve_rate, seq_sample=1)
+
+
+def _capture_mode(fn, args, **over):
+    import contextlib
+    import io
+    a = argparse.Namespace(**vars(args))
+    for k, v in over.items():
+        setattr(a, k, v)
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        fn(a)
+    lines = [l for l in buf.getvalue().splitlines() if l.startswith("{")]
+    out = json.loads(lines[-1]) if lines else None
+    if out:
+        out.pop("ms_steps", None)
+    return out
+
+
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_sample(theta_beta, iters):
-    """The oracle's FGMRES on the same problem, stopped after `iters` outer iterations
-    (one V-cycle each); returns (seconds, V-cycles)."""
+_ORACLE = {}
+
+
+def _oracle_setup():
+    """Build the oracle's hierarchy of the 255^3 problem (once per process)."""
+    if "levels" not in _ORACLE:
+        import oracle as O
+        w = I.cube_3d(CUBE_N)
+        _ORACLE["w"] = w
+        _ORACLE["levels"] = O.build_hierarchy(3, w.n, w.theta_beta, I.THETA_GAMMA, I.ECS_FRAC,
+                                              phi=w.phi.astype(np.float64))
+    return _ORACLE["w"], _ORACLE["levels"]
+
+
+def oracle_sample(_=None):
+    """The oracle's FGMRES(40) on the 3D 255^3 problem stopped after one outer iteration
+    (one V-cycle and one H apply; the hierarchy set-up is outside the time).  Returns
+    (wall-clock start, wall-clock end, V-cycles)."""
     import oracle as O
-    levels = O.build_hierarchy(2, N, theta_beta, I.THETA_GAMMA, I.ECS_FRAC, k=K)
-    b = I.random_source(2, N, 1001)
-    t0 = time.perf_counter()
-    _, info = O.fgmres(levels[0].apply_h, lambda v: O.vcycle(levels, v), b, tol=TOL, maxit=iters)
-    return time.perf_counter() - t0, info.iters
+    w, levels = _oracle_setup()
+    t0 = time.time()
+    _, info = O.fgmres(levels[0].apply_h, lambda v: O.vcycle(levels, v), w.b, None, w.tol, w.restart, 1)
+    return t0, time.time(), info.iters
 
 
-def cpu_baseline(iters):
-    sec, its = oracle_sample(0.3, iters)
-    return {"value": N * N * its / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"NumPy FP64 oracle FGMRES on the same 1023^2 problem at theta_beta=0.3, stopped after "
-                      f"{its} outer iterations ({sec:.1f} s), single-threaded"}
+def oracle_pool(samples, workers, warmup=0):
+    """`samples` one-iteration oracle samples on `workers` spawned processes (each
+    process builds the hierarchy once; `warmup` untimed samples first).  Returns
+    (seconds from the first sample's start to the last one's end, V-cycles)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_oracle_setup) as pool:
+        if warmup:
+            pool.map(oracle_sample, range(warmup), chunksize=1)
+        res = pool.map(oracle_sample, range(samples), chunksize=1)
+    return max(r[1] for r in res) - min(r[0] for r in res), sum(r[2] for r in res)
+
+
+def cpu_workers(cap):
+    return max(1, min(os.cpu_count() or 1, 16, cap))
+
+
+def cpu_baseline():
+    """The oracle timed on the host: one core, then every core (one sample per spawned
+    worker process, running together); the reported value is the faster of the two."""
+    pts = float(CUBE_N) ** 3
+    t0, t1, its1 = oracle_sample()
+    sec1 = t1 - t0
+    one = pts * its1 / sec1 / 1e6
+    workers = cpu_workers(16)
+    wall, its = oracle_pool(workers, workers)
+    allc = pts * its / wall / 1e6
+    best_all = allc >= one
+    return {"value": allc if best_all else one, "unit": UNIT, "cores": workers if best_all else 1, "kind": "oracle",
+            "single_core": {"value": one, "seconds": sec1},
+            "all_cores": {"value": allc, "workers": workers, "wall_s": wall},
+            "host": host_info(),
+            "sample": f"NumPy FP64 oracle FGMRES(40) on the same 255^3 problem stopped after one outer iteration "
+                      f"(one V-cycle, one H apply; hierarchy set-up excluded): {sec1:.1f} s on one core; "
+                      f"{workers} such samples on {workers} spawned processes together in {wall:.1f} s"}
 
 
 def run_reference(args, rank):
+    """The oracle as the reference arm: each step is one one-iteration sample of the
+    255^3 solve; the steps run on spawned processes over the host cores (the warm-up
+    steps first, untimed), and the value is fine points x V-cycles over the time from
+    the first timed sample's start to the last one's end."""
     if rank != 0:
         return None
-    its_per_step = max(1, args.cpu_iters // 2)
-    for _ in range(args.warmup):
-        oracle_sample(0.3, 1)
-    secs, work = 0.0, 0.0
-    for s in range(args.steps):
-        sec, its = oracle_sample(BETAS[s % len(BETAS)], its_per_step)
-        secs += sec
-        work += N * N * its
-    value = work / secs / 1e6
+    workers = cpu_workers(max(args.steps, 1))
+    wall, its = oracle_pool(args.steps, workers, warmup=args.warmup) if args.steps > 0 else (1.0, 0)
+    value = float(CUBE_N) ** 3 * its / wall / 1e6
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": workload_config(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the NumPy FP64 oracle FGMRES on the 1023^2 problem for one "
-                                       f"theta_beta, stopped after {its_per_step} outer iterations"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "host": host_info(),
+                             "sample": f"each step: the NumPy FP64 oracle FGMRES(40) on the 255^3 problem stopped "
+                                       f"after one outer iteration (hierarchy set-up excluded); steps on "
+                                       f"{workers} spawned processes"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -743,10 +848,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--maxit", type=int, default=300)
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--sequential-steps", type=int, default=1)
-    ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single", "cube", "gauss"],
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 2D sweep, 64-problem batch and serving keys of the default line")
+    ap.add_argument("--serve-requests", type=int, default=120, help="requests of the default line's serving run")
+    ap.add_argument("--serve-rate", type=float, default=8.0, help="arrivals/s of the default line's serving run")
+    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single", "cube", "gauss", "sweep2d"],
                     default="solve")
     ap.add_argument("--restart", type=int, default=0)
     ap.add_argument("--batch", type=int, default=64)
@@ -763,6 +870,9 @@ def main():
     if args.mode != "solve":
         from paper_1012_5379_gb300 import build
         build.build()
+        if args.mode == "sweep2d":
+            print(json.dumps(sweep_2d(args, "cuda")), flush=True)
+            return
         {"precond": run_precond, "batch": run_batch, "serve": run_serve, "single": run_single,
          "cube": run_cube, "gauss": run_gauss}[args.mode](args)
         return

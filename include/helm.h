@@ -52,6 +52,13 @@ extern "C" {
 /* preconditioner precision */
 #define HELM_C64 1   /* complex FP32 storage and arithmetic (FP32 accumulation) */
 #define HELM_C128 2  /* complex FP64 */
+#define HELM_CAUTO 3 /* helm_setup picks: HELM_C128 when the finest grid has at most
+                        HELM_AUTO_C128_POINTS unknowns (n^dim), else HELM_C64.  Small grids
+                        cost little more in FP64 (their V-cycle is launch-latency bound), and
+                        some small problems are sensitive to the FP32 rounding of the
+                        preconditioner: with bound states (Benchmark 3 of Sec. 5, nu = 7 on
+                        64^2) the complex64 V-cycle costs 40% more outer iterations. */
+#define HELM_AUTO_C128_POINTS 16384
 
 typedef struct helm_handle helm_handle;
 
@@ -81,7 +88,7 @@ typedef struct {
   int nu2;          /* post-smoothing sweeps per level               [1] */
   int s;            /* GMRES steps per sweep, 1..4                   [3] */
   int coarsest_n;   /* stop coarsening at this size or below         [3] */
-  int precond_prec; /* HELM_C64 or HELM_C128                         [HELM_C64] */
+  int precond_prec; /* HELM_C64, HELM_C128 or HELM_CAUTO             [HELM_C64] */
   int restart;      /* outer FGMRES restart length m, 0 = none       [0] */
   int maxit;        /* max preconditioner applications per solve     [400] */
   double csl_eps;   /* complex shift of the preconditioner: M = L - (1 + i csl_eps) phi
@@ -245,6 +252,10 @@ int helm_workspace_bytes(const helm_handle* h, size_t* bytes);
 
 /* Levels of the hierarchy and their sizes (sizes may be NULL). */
 int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes);
+
+/* The handle's preconditioner precision, HELM_C64 or HELM_C128 (what HELM_CAUTO
+ * resolved to).  Batched solves need handles of one precision. */
+int helm_precond_precision(const helm_handle* h, int* prec);
 
 /* The third-degree polynomial smoother (Sec. 4) of one level: real spacing h,
  * constant k, CSG angle theta_beta, layer angle theta_gamma, dimension dim.  p has

@@ -209,6 +209,12 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes) {
   return HELM_OK;
 }
 
+int helm_precond_precision(const helm_handle* h, int* prec) {
+  if (!h || !prec) { helm::set_error("NULL argument"); return HELM_EINVAL; }
+  *prec = h->h->prec;
+  return HELM_OK;
+}
+
 int helm_poly_smoother(double k, double h, double theta_beta, double theta_gamma, int dim, double* phi,
                        double* w) {
   HELM_GUARD({

@@ -162,6 +162,10 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   h->s = o.s > 0 ? o.s : 3;
   h->coarsest = o.coarsest_n > 0 ? o.coarsest_n : 3;
   h->prec = o.precond_prec ? o.precond_prec : HELM_C64;
+  if (h->prec == HELM_CAUTO && (h->dim == 2 || h->dim == 3) && h->n >= 1) {
+    const double pts = h->dim == 3 ? (double)h->n * h->n * h->n : (double)h->n * h->n;
+    h->prec = pts <= HELM_AUTO_C128_POINTS ? HELM_C128 : HELM_C64;
+  }
   h->restart = o.restart > 0 ? o.restart : 0;
   h->maxit = o.maxit > 0 ? o.maxit : 400;
   h->csl_eps = o.csl_eps;
@@ -180,7 +184,7 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   if (!(theta_beta >= 0 && theta_beta < M_PI / 2)) { set_error("theta_beta must be in [0, pi/2)"); return HELM_EINVAL; }
   if (h->s > SMAX) { set_error("s must be in 1..4"); return HELM_EINVAL; }
   if (h->nu1 > 8 || h->nu2 > 8) { set_error("nu1, nu2 must be <= 8"); return HELM_EINVAL; }
-  if (h->prec != HELM_C64 && h->prec != HELM_C128) { set_error("precond_prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
+  if (h->prec != HELM_C64 && h->prec != HELM_C128) { set_error("precond_prec must be HELM_C64, HELM_C128 or HELM_CAUTO"); return HELM_EINVAL; }
   if (!(std::isfinite(h->csl_eps) && h->csl_eps >= 0.0)) { set_error("csl_eps must be finite and >= 0"); return HELM_EINVAL; }
   if (h->csl_eps != 0.0 && phi) { set_error("the complex shift (csl_eps) needs a constant k"); return HELM_EINVAL; }
   if (h->smoother != HELM_SMOOTHER_GMRES && h->smoother != HELM_SMOOTHER_POLY) {

@@ -9,8 +9,10 @@
 // descriptors, the coarsest LU factors) in one file-scope __device__ array of fixed
 // size, and launches the same kernels as the allocating path (the input kernel, the
 // single-CTA coarse-cycle kernel run from the finest level, the output kernel) on
-// descriptors that point into that array.  Host-side set-up uses fixed-size stack
-// arrays only.
+// descriptors that point into that array.  The set-up data (descriptors, stencil
+// coefficients, the coarsest LU factors) is built on the host by the same geometry
+// routines as helm_setup's and reaches the array as the arguments of small staging
+// kernels, so no host buffer outlives the call and nothing waits for the stream.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -18,9 +20,11 @@
 #include <cstring>
 #include <mutex>
 #include <sstream>
+#include <vector>
 
 #include "../../include/helm.h"
 #include "engine.h"
+#include "geometry.h"
 #include "helm_internal.h"
 #include "profiler.h"
 
@@ -35,8 +39,7 @@ namespace {
 constexpr int MAX_DEVICES = 64;
 constexpr int MAX_LEVELS = 12;
 constexpr int MAX_N = 255;        // per-axis interior nodes accepted before the size check
-constexpr int MAX_COARSE = 32;    // unknowns of the coarsest dense solve (stack arrays)
-typedef std::complex<double> cd;
+constexpr int MAX_COARSE = 32;    // unknowns of the coarsest dense solve
 
 void* g_scratch_addr[MAX_DEVICES] = {nullptr};
 std::mutex g_scratch_mu;
@@ -63,27 +66,6 @@ int scratch_address(void** out) {
   return HELM_OK;
 }
 
-// Complex spacings of the stretched grid (per-interval segment integrals of the
-// stretching factor) and the three-point coefficients, written into caller arrays.
-double overlap(double a, double b, double lo, double hi) {
-  return std::fmax(0.0, std::fmin(b, hi) - std::fmax(a, lo));
-}
-void level_coefficients(int n, double ecs, double tg, double tb, cd* a, cd* d, cd* c) {
-  const double h = 1.0 / (n + 1);
-  const cd eg = std::polar(1.0, tg), eb = std::polar(1.0, tb);
-  auto sp = [&](int i) {
-    const double x0 = i * h, x1 = (i + 1) * h;
-    return eg * (overlap(x0, x1, 0.0, ecs) + overlap(x0, x1, 1.0 - ecs, 1.0)) + eb * overlap(x0, x1, ecs, 1.0 - ecs);
-  };
-  for (int i = 0; i < n; ++i) {
-    const cd hl = sp(i), hr = sp(i + 1);
-    const cd t = 2.0 / (hl + hr);
-    a[i] = -t / hl;
-    c[i] = -t / hr;
-    d[i] = t * (1.0 / hl + 1.0 / hr);
-  }
-}
-
 // A bump allocator over the scratch array (offsets only, 256-byte aligned).
 struct Carve {
   size_t off = 0;
@@ -103,40 +85,68 @@ struct Carve {
     }                                                                                   \
   } while (0)
 
+// Set-up bytes reach the scratch array as kernel arguments: a launch copies its
+// arguments when it is enqueued, so the host block may be a stack buffer and the call
+// never waits for the stream (a pageable cudaMemcpyAsync would).  One launch carries
+// STAGE_CHUNK bytes, which keeps the argument block under the classic 4 KB limit.
+constexpr int STAGE_CHUNK = 4032;
+struct StageChunk {
+  unsigned long long off;  // byte offset into the scratch array
+  int nbytes;
+  int pad;
+  unsigned char data[STAGE_CHUNK];
+};
+static_assert(sizeof(StageChunk) <= 4096, "staging argument block above 4 KB");
+
+__global__ void k_noalloc_stage(StageChunk c) {
+  for (int i = threadIdx.x; i < c.nbytes; i += blockDim.x) g_noalloc_scratch[c.off + i] = c.data[i];
+}
+
+// Copy [src, src + bytes) to scratch offset `off` with staging launches on `st`.
+int stage_bytes(const void* src, size_t bytes, size_t off, cudaStream_t st) {
+  const unsigned char* p = static_cast<const unsigned char*>(src);
+  StageChunk c;
+  for (size_t done = 0; done < bytes; done += STAGE_CHUNK) {
+    const size_t nb = bytes - done < (size_t)STAGE_CHUNK ? bytes - done : (size_t)STAGE_CHUNK;
+    c.off = off + done;
+    c.nbytes = (int)nb;
+    c.pad = 0;
+    std::memcpy(c.data, p + done, nb);
+    Launch L("noalloc.stage", st, 0, 0);
+    k_noalloc_stage<<<1, 256, 0, st>>>(c);
+    NA_CUDA(cudaGetLastError());
+  }
+  return HELM_OK;
+}
+
 template <typename C>
 int run_noalloc(const helm_grid* grid, double k, double theta_beta, int nu1, int nu2, int s, int coarsest,
                 const void* r, void* z, int prec, cudaStream_t st) {
   const int dim = grid->dim, n = grid->n;
   const double ecs = grid->ecs_frac > 0 ? grid->ecs_frac : 0.125;
   const double tg = grid->theta_gamma;
-  // level sizes
-  int sizes[MAX_LEVELS];
-  int nlev = 0;
-  sizes[nlev++] = n;
-  while (sizes[nlev - 1] > coarsest && (sizes[nlev - 1] + 1) % 2 == 0) {
-    if (nlev == MAX_LEVELS) { set_error("too many levels"); return HELM_EINVAL; }
-    sizes[nlev] = (sizes[nlev - 1] + 1) / 2 - 1;
-    ++nlev;
-  }
+  const std::vector<int> sizes = level_sizes(n, coarsest);  // helm_setup's hierarchy
+  const int nlev = (int)sizes.size();
+  if (nlev > MAX_LEVELS) { set_error("too many levels"); return HELM_EINVAL; }
   const int nc = sizes[nlev - 1];
   const int m = dim == 3 ? nc * nc * nc : nc * nc;
   if (m > MAX_COARSE) { set_error("coarsest grid has more than 32 unknowns (n+1 needs a larger power of two)"); return HELM_EINVAL; }
-  // carve the scratch: descriptors, scalars, partial slots, LU, then per-level data
+  // carve the scratch: descriptors, LU record, LU factors, pivots and coefficients
+  // (the staged set-up block, contiguous), then scalars, partial slots and vectors
   Carve cv;
   const size_t o_lev = cv.take(sizeof(LevelDev<C>) * nlev);
   const size_t o_lu = cv.take(sizeof(CoarseLU));
+  const size_t o_lum = cv.take(sizeof(double2) * m * m);
+  const size_t o_piv = cv.take(sizeof(int) * m);
+  size_t o_coef[MAX_LEVELS], o_vec[MAX_LEVELS], np[MAX_LEVELS];
+  for (int l = 0; l < nlev; ++l) o_coef[l] = cv.take(3 * sizeof(C) * sizes[l]);
+  const size_t setup_end = cv.off;
   typedef SweepScalarsT<typename RealOf<C>::T> SS;
   const size_t o_sc = cv.take(sizeof(SS) * nlev);
   const size_t o_part = cv.take(sizeof(double) * NPART);
-  const size_t o_lum = cv.take(sizeof(double2) * m * m);
-  const size_t o_piv = cv.take(sizeof(int) * m);
-  const size_t zero_end = cv.off;  // scalars and partial slots start at zero
-  size_t o_coef[MAX_LEVELS], o_vec[MAX_LEVELS];
-  size_t np[MAX_LEVELS];
   for (int l = 0; l < nlev; ++l) {
     const size_t P = sizes[l] + 1;
     np[l] = dim == 3 ? P * P * P : P * P;
-    o_coef[l] = cv.take(3 * sizeof(C) * sizes[l]);
     o_vec[l] = cv.take((4 + s) * sizeof(C) * np[l]);
   }
   if (cv.off > NOALLOC_BYTES) {
@@ -145,19 +155,30 @@ int run_noalloc(const helm_grid* grid, double k, double theta_beta, int nu1, int
     set_error(os.str());
     return HELM_EINVAL;
   }
+  // the set-up block is assembled on the host (bounded by MAX_N and MAX_COARSE)
+  constexpr size_t SETUP_MAX = 64 * 1024;
+  if (setup_end > SETUP_MAX) { set_error("set-up block of the allocation-free entry point too large"); return HELM_EINVAL; }
   void* base_v = nullptr;
   int rc = scratch_address(&base_v);
   if (rc != HELM_OK) return rc;
   char* base = (char*)base_v;
+  alignas(16) static thread_local unsigned char blk[SETUP_MAX];
+  std::memset(blk, 0, setup_end);
 
-  // clear descriptors, scalars, partial slots and every level vector: nothing of the
-  // previous call's contents may leak into this one
-  NA_CUDA(cudaMemsetAsync(base, 0, cv.off, st));
-
-  // descriptors and coefficients (host stack buffers; pageable copies are staged
-  // before cudaMemcpyAsync returns)
-  LevelDev<C> desc[MAX_LEVELS];
-  std::memset(desc, 0, sizeof(desc));
+  // stencil coefficients of every level (helm_setup's geometry)
+  for (int l = 0; l < nlev; ++l) {
+    std::vector<cplx> a, d, c;
+    stencil_coefficients(grid_spacings(sizes[l], ecs, tg, theta_beta, true), a, d, c);
+    C* host = reinterpret_cast<C*>(blk + o_coef[l]);
+    const int nl = sizes[l];
+    for (int i = 0; i < nl; ++i) {
+      host[i].x = a[i].real(); host[i].y = a[i].imag();
+      host[nl + i].x = d[i].real(); host[nl + i].y = d[i].imag();
+      host[2 * nl + i].x = c[i].real(); host[2 * nl + i].y = c[i].imag();
+    }
+  }
+  // descriptors pointing into the scratch array
+  LevelDev<C>* desc = reinterpret_cast<LevelDev<C>*>(blk + o_lev);
   for (int l = 0; l < nlev; ++l) {
     const int nl = sizes[l];
     LevelDev<C>& d = desc[l];
@@ -180,17 +201,6 @@ int run_noalloc(const helm_grid* grid, double k, double theta_beta, int nu1, int
     d.phir = (typename RealOf<C>::T)d.phic;
     d.sc = (SS*)(base + o_sc) + l;
     d.part = (double*)(base + o_part);
-    {
-      cd a[MAX_N], dd[MAX_N], c[MAX_N];
-      level_coefficients(nl, ecs, tg, theta_beta, a, dd, c);
-      C host[3 * MAX_N];
-      for (int i = 0; i < nl; ++i) {
-        host[i].x = a[i].real(); host[i].y = a[i].imag();
-        host[nl + i].x = dd[i].real(); host[nl + i].y = dd[i].imag();
-        host[2 * nl + i].x = c[i].real(); host[2 * nl + i].y = c[i].imag();
-      }
-      NA_CUDA(cudaMemcpyAsync(base + o_coef[l], host, 3 * sizeof(C) * nl, cudaMemcpyHostToDevice, st));
-    }
   }
   for (int l = 0; l + 1 < nlev; ++l) {
     desc[l].nc = desc[l + 1].n;
@@ -199,56 +209,28 @@ int run_noalloc(const helm_grid* grid, double k, double theta_beta, int nu1, int
     desc[l].xcb = desc[l + 1].xb;
     desc[l].scc = desc[l + 1].sc;
   }
-  NA_CUDA(cudaMemcpyAsync(base + o_lev, desc, sizeof(LevelDev<C>) * nlev, cudaMemcpyHostToDevice, st));
-
-  // coarsest dense operator, LU with partial pivoting (FP64, on the stack)
+  // coarsest dense operator and its LU with partial pivoting (helm_setup's routines)
   {
-    cd a[MAX_COARSE], dd[MAX_COARSE], c[MAX_COARSE];
-    level_coefficients(nc, ecs, tg, theta_beta, a, dd, c);
-    cd A[MAX_COARSE * MAX_COARSE];
-    for (int i = 0; i < m * m; ++i) A[i] = 0.0;
-    const int zn = dim == 3 ? nc : 1;
-    for (int zz = 0; zz < zn; ++zz)
-      for (int yy = 0; yy < nc; ++yy)
-        for (int xx = 0; xx < nc; ++xx) {
-          const int row = (zz * nc + yy) * nc + xx;
-          A[row * m + row] = dd[xx] + dd[yy] + (dim == 3 ? dd[zz] : cd(0, 0)) - k * k;
-          if (xx > 0) A[row * m + row - 1] = a[xx];
-          if (xx + 1 < nc) A[row * m + row + 1] = c[xx];
-          if (yy > 0) A[row * m + row - nc] = a[yy];
-          if (yy + 1 < nc) A[row * m + row + nc] = c[yy];
-          if (dim == 3 && zz > 0) A[row * m + row - nc * nc] = a[zz];
-          if (dim == 3 && zz + 1 < nc) A[row * m + row + nc * nc] = c[zz];
-        }
-    int perm[MAX_COARSE];
-    for (int i = 0; i < m; ++i) perm[i] = i;
-    for (int col = 0; col < m; ++col) {
-      int piv = col;
-      for (int i = col + 1; i < m; ++i)
-        if (std::abs(A[i * m + col]) > std::abs(A[piv * m + col])) piv = i;
-      if (std::abs(A[piv * m + col]) == 0.0) { set_error("coarsest operator is singular"); return HELM_ENUMERIC; }
-      if (piv != col) {
-        for (int j = 0; j < m; ++j) std::swap(A[col * m + j], A[piv * m + j]);
-        std::swap(perm[col], perm[piv]);
-      }
-      for (int i = col + 1; i < m; ++i) {
-        const cd l = A[i * m + col] / A[col * m + col];
-        A[i * m + col] = l;
-        for (int j = col + 1; j < m; ++j) A[i * m + j] -= l * A[col * m + j];
-      }
-    }
-    double2 Ad[MAX_COARSE * MAX_COARSE];
+    std::vector<cplx> a, d, c;
+    stencil_coefficients(grid_spacings(nc, ecs, tg, theta_beta, true), a, d, c);
+    std::vector<cplx> A = dense_operator(dim, nc, a, d, c, std::vector<double>(m, k * k));
+    std::vector<int> perm;
+    if (!lu_factor(A, m, perm)) { set_error("coarsest operator is singular"); return HELM_ENUMERIC; }
+    double2* Ad = reinterpret_cast<double2*>(blk + o_lum);
     for (int i = 0; i < m * m; ++i) Ad[i] = make_double2(A[i].real(), A[i].imag());
-    NA_CUDA(cudaMemcpyAsync(base + o_lum, Ad, sizeof(double2) * m * m, cudaMemcpyHostToDevice, st));
-    NA_CUDA(cudaMemcpyAsync(base + o_piv, perm, sizeof(int) * m, cudaMemcpyHostToDevice, st));
-    CoarseLU lu;
-    lu.m = m;
-    lu.nlev = nlev;
-    lu.lu = (const double2*)(base + o_lum);
-    lu.piv = (const int*)(base + o_piv);
-    NA_CUDA(cudaMemcpyAsync(base + o_lu, &lu, sizeof(lu), cudaMemcpyHostToDevice, st));
+    int* pv = reinterpret_cast<int*>(blk + o_piv);
+    for (int i = 0; i < m; ++i) pv[i] = perm[i];
+    CoarseLU* lu = reinterpret_cast<CoarseLU*>(blk + o_lu);
+    lu->m = m;
+    lu->nlev = nlev;
+    lu->lu = (const double2*)(base + o_lum);
+    lu->piv = (const int*)(base + o_piv);
   }
-  (void)zero_end;
+
+  // clear scalars, partial slots and every level vector (nothing of the previous
+  // call's contents may leak into this one), then stage the set-up block
+  NA_CUDA(cudaMemsetAsync(base + setup_end, 0, cv.off - setup_end, st));
+  TRY(stage_bytes(blk, setup_end, 0, st));
 
   const LevelDev<C>* dlev = (const LevelDev<C>*)(base + o_lev);
   {

@@ -25,13 +25,23 @@ HELM_ECUDA = -6
 HELM_EAGAIN = -7
 HELM_C64 = 1
 HELM_C128 = 2
+HELM_CAUTO = 3
+HELM_AUTO_C128_POINTS = 16384   # include/helm.h: HELM_CAUTO picks complex128 up to this many unknowns
+_PRECISIONS = {"c64": HELM_C64, "c128": HELM_C128, "auto": HELM_CAUTO}
+
+
+def _precision_code(precision: str) -> int:
+    if precision not in _PRECISIONS:
+        raise ValueError("precision must be 'c64', 'c128' or 'auto'")
+    return _PRECISIONS[precision]
 
 _STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ENOCONV", -4: "HELM_ENUMERIC",
            -5: "HELM_ETIMEOUT", -6: "HELM_ECUDA", -7: "HELM_EAGAIN"}
 
 # names declared in include/helm.h (checked by the CPU test suite)
 EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_operator", "helm_solve",
-           "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_poly_smoother",
+           "helm_solve_host", "helm_batch_solve", "helm_workspace_bytes", "helm_levels", "helm_precond_precision",
+           "helm_poly_smoother",
            "helm_axis_coefficients",
            "helm_last_error",
            "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc",
@@ -113,6 +123,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_workspace_bytes.restype = ip
     lib.helm_levels.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
     lib.helm_levels.restype = ip
+    lib.helm_precond_precision.argtypes = [vp, ctypes.POINTER(ip)]
+    lib.helm_precond_precision.restype = ip
     dptr = ctypes.POINTER(ctypes.c_double)
     lib.helm_poly_smoother.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ip, dptr,
                                        dptr]
@@ -164,6 +176,60 @@ def _ptr(t) -> int:
     return t if isinstance(t, int) else t.data_ptr()
 
 
+_DTYPES = {"c64": "torch.complex64", "c128": "torch.complex128"}
+
+
+def _require_vec(name: str, t, shape, dtype: Optional[str] = None) -> None:
+    """Reject a tensor the kernels would read or write out of bounds: wrong dtype
+    (complex64 / complex128), shape, strides or device.  Raw integer pointers are
+    passed through unchecked (the caller vouches for them)."""
+    if isinstance(t, int):
+        return
+    if dtype is not None and str(t.dtype) != _DTYPES[dtype]:
+        raise ValueError(f"{name} must be {_DTYPES[dtype]}, got {t.dtype}")
+    if str(t.dtype) not in _DTYPES.values():
+        raise ValueError(f"{name} must be complex64 or complex128, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape) and t.numel() != _numel(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _require_device(name: str, t) -> None:
+    """A tensor must live on the current CUDA device (raw pointers pass unchecked)."""
+    if isinstance(t, int):
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    import torch
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, the current device is cuda:{torch.cuda.current_device()}")
+
+
+def _require_pair(names, a, b, shape, dtype: Optional[str] = None) -> None:
+    """Two vectors of one call: the same complex precision (or `dtype`), `shape` and
+    layout, both on the current device."""
+    _require_vec(names[0], a, shape, dtype)
+    _require_vec(names[1], b, shape, dtype if (dtype or isinstance(a, int)) else _dtype_name(a))
+    _require_device(names[0], a)
+    _require_device(names[1], b)
+
+
+def _numel(shape) -> int:
+    out = 1
+    for s in shape:
+        out *= s
+    return out
+
+
+def _dtype_name(t) -> str:
+    return "c128" if str(t.dtype).endswith("complex128") else "c64"
+
+
+def _prec_of(t) -> int:
+    return HELM_C128 if str(t.dtype).endswith("complex128") else HELM_C64
+
+
 @dataclass
 class Info:
     iters: int
@@ -193,7 +259,7 @@ class Handle:
         g = helm_grid(dim, n, ecs_frac, theta_gamma, _ECS_SIDES[ecs_sides])
         if smoother not in ("gmres", "poly"):
             raise ValueError("smoother must be 'gmres' or 'poly'")
-        o = helm_opts(nu1, nu2, s, coarsest_n, HELM_C128 if precision == "c128" else HELM_C64, restart, maxit,
+        o = helm_opts(nu1, nu2, s, coarsest_n, _precision_code(precision), restart, maxit,
                       float(csl_eps), 1 if smoother == "poly" else 0)
         h = ctypes.c_void_p()
         phi_ptr = None if phi is None else _ptr(phi)
@@ -217,6 +283,13 @@ class Handle:
         except Exception:
             pass
 
+    def resolved_precision(self) -> str:
+        """The preconditioner precision of the handle ('c64' or 'c128'; what 'auto'
+        resolved to)."""
+        p = ctypes.c_int()
+        _check(load().helm_precond_precision(self._h, ctypes.byref(p)))
+        return "c128" if p.value == HELM_C128 else "c64"
+
     def levels(self) -> list:
         n = ctypes.c_int()
         sizes = (ctypes.c_int * 32)()
@@ -228,20 +301,27 @@ class Handle:
         _check(load().helm_workspace_bytes(self._h, ctypes.byref(b)))
         return b.value
 
+    def _vec_shape(self):
+        return (self.n,) * self.dim
+
     def precond_apply(self, r, z, stream=None):
-        """z ~ (M^CSG)^{-1} r by one V-cycle (torch complex64/complex128 CUDA tensors)."""
-        prec = HELM_C128 if str(r.dtype).endswith("complex128") else HELM_C64
+        """z ~ (M^CSG)^{-1} r by one V-cycle (torch complex64/complex128 CUDA tensors of
+        the same dtype, n^dim elements)."""
+        _require_pair(("r", "z"), r, z, self._vec_shape())
+        prec = _prec_of(r)
         _check(load().helm_precond_apply(self._h, _ptr(r), _ptr(z), prec, _stream(stream)))
         return z
 
     def apply_operator(self, v, w, which: str = "M", stream=None):
-        prec = HELM_C128 if str(v.dtype).endswith("complex128") else HELM_C64
+        _require_pair(("v", "w"), v, w, self._vec_shape())
+        prec = _prec_of(v)
         _check(load().helm_apply_operator(self._h, 1 if which == "H" else 0, _ptr(v), _ptr(w), prec,
                                           _stream(stream)))
         return w
 
     def solve(self, b, x, tol: float, stream=None) -> Info:
         """FGMRES solve of H x = b (complex128 CUDA tensors; x holds the initial guess)."""
+        _require_pair(("b", "x"), b, x, self._vec_shape(), "c128")
         ci = helm_info()
         _check(load().helm_solve(self._h, _ptr(b), _ptr(x), float(tol), ctypes.byref(ci), _stream(stream)),
                allow=(HELM_OK, HELM_ENOCONV, HELM_ENUMERIC))
@@ -259,13 +339,20 @@ class Handle:
 
 def precond_apply_noalloc(dim: int, n: int, theta_beta: float, k: float, r, z, theta_gamma: float = 0.5,
                           ecs_frac: float = 0.125, nu1: int = 1, nu2: int = 1, s: int = 3, precision: str = "c64",
-                          stream=None):
+                          coarsest_n: int = 3, stream=None):
     """One V-cycle on a small grid through helm_precond_apply_noalloc: the library
     allocates no device memory for it (its working memory is a fixed array inside the
-    library).  r, z: torch complex64/complex128 CUDA tensors of shape (n,)*dim."""
+    library).  r, z: torch CUDA tensors of shape (n,)*dim, both complex64 or both
+    complex128, contiguous, on the current device (ValueError otherwise: the C entry
+    point takes one precision for both and cannot see a tensor's size)."""
+    if isinstance(r, int) or isinstance(z, int):
+        raise ValueError("r and z must be torch tensors")
+    if tuple(r.shape) != (n,) * dim or tuple(z.shape) != (n,) * dim:
+        raise ValueError(f"r and z must have shape {(n,) * dim}, got {tuple(r.shape)} and {tuple(z.shape)}")
+    _require_pair(("r", "z"), r, z, (n,) * dim)
     g = helm_grid(dim, n, ecs_frac, theta_gamma, HELM_ECS_BOTH)
-    o = helm_opts(nu1, nu2, s, 3, HELM_C128 if precision == "c128" else HELM_C64, 0, 0, 0.0, 0)
-    prec = HELM_C128 if str(r.dtype).endswith("complex128") else HELM_C64
+    o = helm_opts(nu1, nu2, s, coarsest_n, HELM_C128 if precision == "c128" else HELM_C64, 0, 0, 0.0, 0)
+    prec = _prec_of(r)
     _check(load().helm_precond_apply_noalloc(ctypes.byref(g), float(k), float(theta_beta), ctypes.byref(o),
                                              _ptr(r), _ptr(z), prec, _stream(stream)))
     return z

@@ -151,3 +151,20 @@ def test_stop_drains_pending_requests(helm):
     s.stop()   # returns once every admitted and queued request has finished
     assert all(np.isfinite(x).all() for x in xs)
     assert true_rel_residual(reqs[-1], xs[-1]) <= 1.05 * TOL
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_source_is_retired_with_enumeric(helm, bad):
+    """A request whose source holds a NaN or an Inf (injected on the host) is retired
+    with HELM_ENUMERIC; requests served beside it are unaffected (bitwise equal to
+    being served alone)."""
+    good = req(60, 2, 127, 0.2)
+    badr = dict(req(61, 2, 127, 0.2))
+    badr["b"] = badr["b"].copy()
+    badr["b"][17, 40] = bad
+    out, stats = serve(helm, [badr, good])
+    (xb, ib, rcb, _), (xg, ig, rcg, _) = out
+    assert rcb == helm.HELM_ENUMERIC and ib.status == helm.HELM_ENUMERIC
+    assert rcg == helm.HELM_OK and ig.rel_res_true <= TOL
+    (xa, ia, _, _), = serve(helm, [good])[0]
+    assert ia.iters == ig.iters and np.array_equal(xa, xg)
