@@ -575,6 +575,33 @@ def run_cube(args):
     print(json.dumps(out), flush=True)
 
 
+TUNE_WORKLOADS = (  # (dim, n, precision, field) whose levels the committed table covers
+    (3, 255, "c64", True), (3, 127, "c64", True), (2, 4095, "c64", False), (2, 1023, "c64", False),
+    (2, 511, "c64", False), (2, 255, "c64", False), (2, 127, "c128", False), (2, 1023, "c128", False))
+
+
+def run_tune(args):
+    """Tune the V-cycle's launch choices (helm_autotune) for the levels of the benchmark
+    workloads, one after the other, and write the whole table to --tune-out."""
+    import torch
+
+    from paper_1012_5379_gb300 import helm
+    out = {"mode": "tune", "path": args.tune_out, "runs": []}
+    for dim, n, prec, field in TUNE_WORKLOADS:
+        phi = None
+        if field:
+            phi = torch.from_numpy(I.cube_3d(n).phi).cuda()
+        t0 = time.perf_counter()
+        d0, d1 = helm.autotune(dim, n, 0.4 if dim == 3 else 0.3, k=None if field else 0.156 * (n + 1), phi=phi,
+                               precision=prec, reps=args.reps, path=args.tune_out)
+        out["runs"].append({"dim": dim, "n": n, "prec": prec, "default_ms": d0, "tuned_ms": d1,
+                            "s": time.perf_counter() - t0})
+        print(json.dumps(out["runs"][-1]), flush=True)
+        del phi
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def gauss_key(nu, k, nint, cycle):
     """Key of one Gaussian-model solve in tests/golden/oracle_iters_gauss.json."""
     return f"nu={nu:g} k={k:g} nint={nint} V({cycle})"
@@ -853,8 +880,10 @@ def main():
                     help="skip the 2D sweep, 64-problem batch and serving keys of the default line")
     ap.add_argument("--serve-requests", type=int, default=120, help="requests of the default line's serving run")
     ap.add_argument("--serve-rate", type=float, default=8.0, help="arrivals/s of the default line's serving run")
-    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single", "cube", "gauss", "sweep2d"],
-                    default="solve")
+    ap.add_argument("--mode", choices=["solve", "precond", "batch", "serve", "single", "cube", "gauss", "sweep2d",
+                                       "tune"], default="solve")
+    ap.add_argument("--tune-out", default=os.path.join(ROOT, "paper_1012_5379_gb300", "tuning.json"),
+                    help="tune mode: where the table is written")
     ap.add_argument("--restart", type=int, default=0)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--requests", type=int, default=2000)
@@ -874,7 +903,7 @@ def main():
             print(json.dumps(sweep_2d(args, "cuda")), flush=True)
             return
         {"precond": run_precond, "batch": run_batch, "serve": run_serve, "single": run_single,
-         "cube": run_cube, "gauss": run_gauss}[args.mode](args)
+         "cube": run_cube, "gauss": run_gauss, "tune": run_tune}[args.mode](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -309,6 +309,53 @@ int helm_precond_apply_noalloc(const helm_grid* grid, double k, double theta_bet
                                const helm_opts* opts, const void* r, void* z, int prec,
                                void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Launch tuning.  The paper has no counterpart: these choose launch parameters of the
+ * V-cycle passes on this GPU.  Tuned choices live in a process-wide table keyed by
+ * pass, dimension, level pitch P = n + 1, precision and Arnoldi step; every handle with
+ * such a level uses them, and a choice depends on nothing else, so a problem's result
+ * is the same alone and in any batch.  helm_setup reads the table once per process
+ * from $HELM_TUNING or, if that is unset, tuning.json beside the library (absent: the
+ * built-in defaults).  A table written on another kind of device is not used.
+ * --------------------------------------------------------------------------------- */
+
+/* Tune the launch choices of one problem's V-cycle on the current device: the tiles
+ * per CTA of the 2D passes (Arnoldi steps, residual + restriction, prolongation), and
+ * for 3D complex64 levels of pitch 128..1024 the TMA-fed Arnoldi pass of each step
+ * (off, or on with 2..8 plane slots in flight, 2 or 4 points per thread in y, and the
+ * level shared as one piece per resident CTA or as 1, 2 or 4 z pieces per column).
+ * Every candidate is timed over whole V-cycles (reps cycles, best of three trials) by
+ * coordinate descent from the defaults, finest level first, and kept when it makes the
+ * V-cycle more than 0.5% faster.  grid, phi, k, theta_beta, opts as for helm_setup
+ * (restart and maxit ignored).  The choices enter the process's table; with path
+ * non-NULL the whole table, plus a record of this run, is written there as JSON.
+ * default_ms / tuned_ms (may be NULL) receive the milliseconds per V-cycle before and
+ * after.  Blocks until done; allocates a handle and two vectors for the duration.
+ * Errors as helm_setup, HELM_EINVAL for the polynomial smoother or an unwritable path. */
+int helm_autotune(const helm_grid* grid, const float* phi, double k, double theta_beta, const helm_opts* opts,
+                  int reps, const char* path, double* default_ms, double* tuned_ms, void* stream);
+
+/* Replace the process's tuned choices with the JSON table at `path` (NULL: $HELM_TUNING,
+ * else tuning.json beside the library).  Host only.  HELM_EINVAL if the file is missing
+ * or malformed (the current table is then kept). */
+int helm_tuning_load(const char* path);
+
+/* The tuned choice of pass "arnoldi", "restrict" or "prolong" on a level of dimension
+ * dim and pitch P in precision prec (HELM_C64 / HELM_C128) for Arnoldi step J (0 for
+ * the other passes): writes its 4 integers into v and returns 1, or returns 0 when the
+ * table has none (the built-in default applies).  v: 2D passes {tiles per CTA}; 3D
+ * Arnoldi {TMA-fed pass on, plane slots, z pieces per column (0: one share per resident
+ * CTA), points per thread in y}.  Host only. */
+int helm_tuning_get(const char* pass, int dim, int P, int prec, int J, int* v);
+
+/* Spin limit of the grid-wide barrier between the passes of the persistent V-cycle
+ * segments (the small grid-wide levels of every V-cycle run as one cooperative launch
+ * per half cycle; a CTA waits at most this long for the others, then the launch
+ * returns and the solve reports HELM_ETIMEOUT).  Process-wide, [0, 60] seconds, default
+ * 1.  The paper has no counterpart: this bounds a wait of this GPU implementation (a
+ * limit of 0 makes every waiting CTA give up at once, which tests the error path). */
+int helm_set_barrier_timeout(double seconds);
+
 /* Kernels this library has launched in the process so far (all handles, all
  * streams).  The paper has no counterpart: this is launch accounting for
  * benchmarks. */

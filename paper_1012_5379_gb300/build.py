@@ -16,7 +16,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["vcycle_c64.cu", "vcycle_c128.cu", "outer.cu", "convert.cu", "noalloc.cu"]
-CPP = ["engine.cpp", "geometry.cpp", "capi.cpp", "profiler.cpp", "serve.cpp", "tma.cpp"]
+CPP = ["engine.cpp", "geometry.cpp", "capi.cpp", "profiler.cpp", "serve.cpp", "tma.cpp", "tune.cpp", "autotune.cpp"]
 HEADERS = ["poly.h", "helm_internal.h", "device_common.cuh", "vcycle.cuh", "tiles.cuh", "vcycle_launch.cuh", "engine.h", "geometry.h",
            "profiler.h"]
 
@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(o)
     objs = [os.path.join(BUILD, f + ".o") for f in CU + CPP]
     tmp = LIB + ".tmp"
-    _run([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
+    _run([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -209,6 +209,46 @@ int helm_levels(const helm_handle* h, int* nlevels, int* sizes, int max_sizes) {
   return HELM_OK;
 }
 
+int helm_autotune(const helm_grid* grid, const float* phi, double k, double theta_beta, const helm_opts* opts,
+                  int reps, const char* path, double* default_ms, double* tuned_ms, void* stream) {
+  HELM_GUARD({
+    if (!grid) { helm::set_error("grid must not be NULL"); return HELM_EINVAL; }
+    return helm::autotune(grid, phi, k, theta_beta, opts, reps, path, default_ms, tuned_ms, (cudaStream_t)stream);
+  })
+}
+
+int helm_set_barrier_timeout(double seconds) {
+  HELM_GUARD({
+    if (!(seconds >= 0.0 && seconds <= 60.0)) { helm::set_error("seconds must be in [0, 60]"); return HELM_EINVAL; }
+    helm::set_barrier_limit_ns((unsigned long long)(seconds * 1e9));
+    return HELM_OK;
+  })
+}
+
+int helm_tuning_load(const char* path) {
+  HELM_GUARD({
+    std::string err;
+    const int rc = helm::tune_load(path, &err);
+    if (rc != HELM_OK) helm::set_error(err);
+    return rc;
+  })
+}
+
+int helm_tuning_get(const char* pass, int dim, int P, int prec, int J, int* v) {
+  HELM_GUARD({
+    if (!pass || !v) { helm::set_error("NULL argument"); return HELM_EINVAL; }
+    const std::string p(pass);
+    const int tp = p == "arnoldi" ? helm::TP_ARNOLDI : p == "restrict" ? helm::TP_RESTRICT
+                 : p == "prolong" ? helm::TP_PROLONG : -1;
+    if (tp < 0) { helm::set_error("pass must be arnoldi, restrict or prolong"); return HELM_EINVAL; }
+    if (prec != HELM_C64 && prec != HELM_C128) { helm::set_error("prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
+    helm::TuneChoice c;
+    if (!helm::tune_get(tp, dim, P, prec == HELM_C128 ? 16 : 8, J, &c)) return 0;
+    for (int i = 0; i < helm::TUNE_NV; ++i) v[i] = c.v[i];
+    return 1;
+  })
+}
+
 int helm_precond_precision(const helm_handle* h, int* prec) {
   if (!h || !prec) { helm::set_error("NULL argument"); return HELM_EINVAL; }
   *prec = h->h->prec;

@@ -146,6 +146,7 @@ static int compute_poly_weights(Handle* h, const std::vector<int>& sizes) {
 int setup_handle(const helm_grid* grid, const float* phi, double k, double theta_beta, const helm_opts* opts,
                  cudaStream_t st, Handle** out) {
   if (!grid || !out) { set_error("grid and out must not be NULL"); return HELM_EINVAL; }
+  tune_load_default();  // the tuned launch choices, read once per process
   std::unique_ptr<Handle> h(new Handle());
   h->dim = grid->dim;
   h->n = grid->n;
@@ -253,17 +254,28 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     const size_t scb = h->prec == HELM_C128 ? sizeof(SweepScalarsT<double>) : sizeof(SweepScalarsT<float>);
     TRY(dev_alloc(h.get(), &L.sc, scb));
     CUDA_TRY(cudaMemsetAsync(L.sc, 0, scb, st));
-    const size_t nparts = std::max<size_t>(std::max(L.ntiles, L.nflat), 1);
+    // partial slots: one per tile of the marching passes, per flat-pass CTA, and per
+    // share of the 3D TMA-fed pass
+    size_t nparts = std::max<size_t>(std::max(L.ntiles, L.nflat), 1);
+    if (h->dim == 3) nparts = std::max<size_t>(nparts, TMA3_MAX_UNITS);
     TRY(dev_alloc(h.get(), &L.part, nparts * NPART * sizeof(double)));
-    // TMA maps of the raw vectors the 2D complex64 Arnoldi pass streams
-    if (h->dim == 2 && h->prec == HELM_C64 && L.P >= 64) {
-      std::vector<CUtensorMap> maps(TM_COUNT);
-      const void* vecs[TM_COUNT] = {L.b, L.r0, nullptr, nullptr, nullptr, nullptr};
+    // TMA maps of the raw vectors the complex64 Arnoldi passes stream
+    // (3D: two sets, for column tiles of 16 and of 32 rows)
+    if (h->prec == HELM_C64 && L.P >= 64 && (h->dim == 2 || L.P % 32 == 0)) {
+      const int nmaps = h->dim == 2 ? TM_COUNT : 2 * TM_COUNT;
+      std::vector<CUtensorMap> maps(nmaps);
+      const void* vecs[TM_COUNT] = {};
+      vecs[TM_B] = L.b;
+      vecs[TM_R0] = L.r0;
+      vecs[TM_XB] = L.xb;
       for (int j = 0; j < h->s; ++j) vecs[TM_P0 + j] = L.p[j];
-      if (encode_level_tmaps(L.P, vecs, TM_COUNT, maps.data())) {
+      const bool encoded = h->dim == 2 ? encode_level_tmaps(L.P, vecs, TM_COUNT, maps.data())
+                                       : encode_level_tmaps3(L.P, 18, vecs, TM_COUNT, maps.data()) &&
+                                             encode_level_tmaps3(L.P, 34, vecs, TM_COUNT, maps.data() + TM_COUNT);
+      if (encoded) {
         CUtensorMap* dtm = nullptr;
-        TRY(dev_alloc(h.get(), &dtm, TM_COUNT * sizeof(CUtensorMap)));
-        CUDA_TRY(cudaMemcpyAsync(dtm, maps.data(), TM_COUNT * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+        TRY(dev_alloc(h.get(), &dtm, nmaps * sizeof(CUtensorMap)));
+        CUDA_TRY(cudaMemcpyAsync(dtm, maps.data(), nmaps * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
         L.tm = dtm;
       }
     }
@@ -427,6 +439,8 @@ struct Group {
   std::vector<Sub> outer;
   LevelDev<C>* lev0 = nullptr;   // level-0 descriptors of all problems (single problem: [0])
   int lev0_nflat = 1;
+  GridBar* gbar = nullptr;       // grid barrier of the persistent segments
+  int tp = 0;                    // first depth of the persistent segments (tc: none)
   void* dmem = nullptr;
   bool owns = true;              // dmem and cap_stream belong to the group (not to an arena)
   // the V-cycle captured as a CUDA graph (re-captured when profiling starts or stops)
@@ -541,6 +555,7 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
       D.ntiles = L.ntiles;
       D.nflat = L.nflat;
       D.cfg.rows = zchunk(L.P);
+      D.cfg.P = L.P;
     }
   }
   std::vector<LevelDev<C>> coarse;
@@ -641,6 +656,17 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
   g->dlu = (CoarseLU*)put(lus.data(), lus.size() * sizeof(CoarseLU));
   g->lev0 = (LevelDev<C>*)put(lev0.data(), lev0.size() * sizeof(LevelDev<C>));
   for (size_t q = 0; q < subs.size(); ++q) g->outer[q].d = (OuterDev<C>*)put(subs[q].data(), subs[q].size() * sizeof(OuterDev<C>));
+  const GridBar gb0{0u, 0u};
+  g->gbar = (GridBar*)put(&gb0, sizeof(GridBar));
+  // the persistent segments: the deepest run of grid-wide levels that qualify
+  // (bounded by the pass list's capacity: a depth records nu1 (s + 1) passes going down
+  // and 1 + nu2 (s + 1) coming up)
+  g->tp = g->tc;
+  const int per_depth = std::max(g->nu1 == 0 ? 1 : g->nu1 * (g->s + 1), 1 + g->nu2 * (g->s + 1));
+  if (g->smoother == HELM_SMOOTHER_GMRES)
+    while (g->tp > 0 && (g->tc - g->tp + 1) * per_depth <= SEQ_MAX &&
+           persist_level(g->dim, g->depth[g->tp - 1].n + 1, (int)sizeof(C)))
+      --g->tp;
   CUDA_TRY(cudaGetLastError());
   if (!arena) CUDA_TRY(cudaStreamSynchronize(st));
   return HELM_OK;
@@ -694,7 +720,7 @@ static void run_vcycle_poly(const Group<C>& g, cudaStream_t st) {
     const bool fine = (t == 0);
     {
       Launch L(fine ? "vc.prolong.l0" : "vc.prolong.lc", st, pts * E * (2.0 + cf), 0);
-      launch_prolong<C>(dim, false, D.d, D.cnt, D.nflat, D.cfg, st);  // x_b = x_a + P e_c
+      launch_prolong<C>(dim, false, D.d, D.cnt, D.nflat, D.cfg, false, st);  // x_b = x_a + P e_c
     }
     if (g.nu2 > 0) sweeps(D, g.nu2, POLY_XB, POLY_XB, fine);
   }
@@ -709,30 +735,64 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
   const int dim = g.dim;
   const double E = sizeof(C);
   const double cf = 1.0 / (dim == 3 ? 8.0 : 4.0);
+  // The depths t >= g.tp run as two persistent launches (descent, ascent): their passes
+  // are recorded instead of launched; bytes counts their algorithmic bytes.
+  PassSeq seq;
+  seq.npass = 0;
+  double seq_bytes = 0;
+  auto flush = [&](const char* name) {
+    if (seq.npass == 0) return;
+    Launch L(name, st, seq_bytes, 0);
+    launch_seq<C>(dim, seq, g.gbar, barrier_limit_ns(), st);
+    seq.npass = 0;
+    seq_bytes = 0;
+  };
   for (int t = 0; t < g.tc; ++t) {
     const auto& D = g.depth[t];
     const double pts = (double)D.cnt * (dim == 3 ? (double)(D.n + 1) * (D.n + 1) * (D.n + 1) : (double)(D.n + 1) * (D.n + 1));
     const bool fine = (t == 0);
+    const bool rec = t >= g.tp;
     const double ph = g.hs[0]->has_phi ? 4.0 : 0.0;
     if (g.nu1 == 0) {
+      if (rec) {
+        record_restrict<C>(seq, dim, D.d, D.cnt, D.ntiles, D.cfg, true, true, true);
+        seq_bytes += pts * E * (2.0 + cf);
+        continue;
+      }
       Launch L(fine ? "vc.restrict.l0" : "vc.restrict.lc", st, pts * E * (2.0 + cf), 0);
-      launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, D.cfg, true, true, true, st);
+      launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, D.cfg, true, true, true, st, D.tma, 1);
       continue;
     }
     for (int sw = 0; sw < g.nu1; ++sw) {
       for (int J = 1; J <= g.s; ++J) {
+        if (rec) {
+          record_arnoldi<C>(seq, dim, J, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, true);
+          seq_bytes += pts * (E * (J + 1) + ph);
+          continue;
+        }
         Launch L(fine ? "vc.arnoldi.l0" : "vc.arnoldi.lc", st, pts * (E * (J + 1) + ph), pts * (8.0 * (2 * dim + 1) + 8.0 * J + 4));
         launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, true, D.tma, st);
       }
       if (sw < g.nu1 - 1) {
+        if (rec) {
+          record_update<C>(seq, dim, UPD_RESIDUAL, D.d, D.cnt, D.nflat, sw == 0, 0, sw == 0);
+          seq_bytes += pts * E * (g.s + 3.0 + (sw == 0 ? 0 : 1));
+          continue;
+        }
         Launch L(fine ? "vc.update.l0" : "vc.update.lc", st, pts * E * (g.s + 3.0 + (sw == 0 ? 0 : 1)), 0);
         launch_update_flat<C>(dim, UPD_RESIDUAL, D.d, D.cnt, D.nflat, sw == 0, 0, sw == 0, st);
       } else {
+        if (rec) {
+          record_restrict<C>(seq, dim, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, sw == 0, false);
+          seq_bytes += pts * E * (g.s + 2.0 + cf + (sw == 0 ? 0 : 1));
+          continue;
+        }
         Launch L(fine ? "vc.restrict.l0" : "vc.restrict.lc", st, pts * E * (g.s + 2.0 + cf + (sw == 0 ? 0 : 1)), 0);
-        launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, sw == 0, false, st);
+        launch_restrict<C>(dim, D.d, D.cnt, D.ntiles, D.cfg, sw == 0, sw == 0, false, st, D.tma, g.s + 1);
       }
     }
   }
+  flush("vc.seq.down");
   {
     Launch L("vc.coarse", st, 0, 0);
     if (g.coarse_smem > 0)
@@ -744,24 +804,41 @@ static void run_vcycle(const Group<C>& g, cudaStream_t st) {
     const auto& D = g.depth[t];
     const double pts = (double)D.cnt * (dim == 3 ? (double)(D.n + 1) * (D.n + 1) * (D.n + 1) : (double)(D.n + 1) * (D.n + 1));
     const bool fine = (t == 0);
+    const bool rec = t >= g.tp;
+    if (!rec) flush("vc.seq.up");
     const double ph = g.hs[0]->has_phi ? 4.0 : 0.0;
-    {
-      Launch L(fine ? "vc.prolong.l0" : "vc.prolong.lc", st,
-               g.nu2 > 0 ? pts * (E * (4.0 + cf) + ph) : pts * E * (2.0 + cf), 0);
-      launch_prolong<C>(dim, g.nu2 > 0, D.d, D.cnt, g.nu2 > 0 ? D.ntiles : D.nflat, D.cfg, st);
+    const double pbytes = g.nu2 > 0 ? pts * (E * (4.0 + cf) + ph) : pts * E * (2.0 + cf);
+    if (rec) {
+      record_prolong<C>(seq, dim, g.nu2 > 0, D.d, D.cnt, g.nu2 > 0 ? D.ntiles : D.nflat, D.cfg);
+      seq_bytes += pbytes;
+    } else {
+      Launch L(fine ? "vc.prolong.l0" : "vc.prolong.lc", st, pbytes, 0,
+               prolong_kernels(dim, g.nu2 > 0, (int)sizeof(C), D.tma, D.cfg.P));
+      launch_prolong<C>(dim, g.nu2 > 0, D.d, D.cnt, g.nu2 > 0 ? D.ntiles : D.nflat, D.cfg, D.tma, st);
     }
     for (int sw = 0; sw < g.nu2; ++sw) {
       const bool last = (sw == g.nu2 - 1);
       for (int J = 1; J <= g.s; ++J) {
         const bool store = J < g.s || !last;
+        if (rec) {
+          record_arnoldi<C>(seq, dim, J, D.d, D.cnt, D.ntiles, D.cfg, false, store);
+          seq_bytes += pts * (E * (J + (store ? 1 : 0)) + ph);
+          continue;
+        }
         Launch L(fine ? "vc.arnoldi.l0" : "vc.arnoldi.lc", st, pts * (E * (J + (store ? 1 : 0)) + ph),
                  pts * (8.0 * (2 * dim + 1) + 8.0 * J + 4));
         launch_arnoldi<C>(dim, J, D.d, D.cnt, D.ntiles, D.cfg, false, store, D.tma, st);
+      }
+      if (rec) {
+        record_update<C>(seq, dim, last ? UPD_XONLY : UPD_RESIDUAL, D.d, D.cnt, D.nflat, false, 1, false);
+        seq_bytes += pts * E * (last ? g.s + 2.0 : g.s + 4.0);
+        continue;
       }
       Launch L(fine ? "vc.update.l0" : "vc.update.lc", st, pts * E * (last ? g.s + 2.0 : g.s + 4.0), 0);
       launch_update_flat<C>(dim, last ? UPD_XONLY : UPD_RESIDUAL, D.d, D.cnt, D.nflat, false, 1, false, st);
     }
   }
+  flush("vc.seq.up");
 }
 
 // Host work of group (re)builds and V-cycle graph captures, for the serving counters.
@@ -1156,7 +1233,7 @@ static int solve_t(Handle* const* hs, int count, const double* const* b, double*
   }
   TRY(rc);
   if (vcycle_take_error()) {
-    set_error("a V-cycle kernel's wait for its tile copies ran out");
+    set_error("a V-cycle kernel's bounded wait ran out (its tile copies, or the persistent segment's grid barrier)");
     return HELM_ETIMEOUT;
   }
   for (int k = 0; k < nsets; ++k)

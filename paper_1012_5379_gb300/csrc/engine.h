@@ -104,6 +104,8 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
                  cudaStream_t st, Handle** out);
 int precond_apply(Handle* h, const void* r, void* z, int prec, cudaStream_t st);
 int apply_operator(Handle* h, int which, const void* v, void* w, int prec, cudaStream_t st);
+int autotune(const helm_grid* grid, const float* phi, double k, double theta_beta, const helm_opts* opts, int reps,
+             const char* path, double* default_ms, double* tuned_ms, cudaStream_t st);
 int precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, const helm_opts* opts,
                           const void* r, void* z, int prec, cudaStream_t st);
 // Problems iterated together, joining and leaving between outer iterations.

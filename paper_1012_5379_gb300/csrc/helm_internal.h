@@ -12,6 +12,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <string>
+
 #ifdef __CUDACC__
 #define HELM_HD __host__ __device__
 #else
@@ -81,7 +83,7 @@ struct LevelDev {
 };
 
 // TMA maps per level: b, r0, p_1..p_SMAX (in this order).
-constexpr int TM_B = 0, TM_R0 = 1, TM_P0 = 2, TM_COUNT = 2 + SMAX;
+constexpr int TM_B = 0, TM_R0 = 1, TM_P0 = 2, TM_XB = 2 + SMAX, TM_COUNT = 3 + SMAX;
 
 // Dense LU factors of the coarsest operator (FP64), row-major, with pivots.
 constexpr int MAX_COARSE_LEVELS_HOST = 8;  // levels the staged coarse kernels hold
@@ -145,6 +147,7 @@ struct OuterDev {
 // Tile configuration: rows (2D) or planes (3D) marched per warp / CTA (even).
 struct TileCfg {
   int rows;
+  int P = 0;   // pitch of the level (n + 1)
 };
 
 constexpr int WARPS2 = 8;     // 2D: warps per CTA (each marches its own rows)
@@ -154,7 +157,7 @@ HELM_HD inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // V-cycle tile kernels: 2D tiles of 64 x 16 points; 3D blocks of 32 x 8 columns
 // marching zchunk(P) planes.
-HELM_HD inline int zchunk(int P) { return P >= 128 ? 32 : (P >= 32 ? 16 : 8); }
+HELM_HD inline int zchunk(int P) { return P >= 128 ? 32 : (P >= 64 ? 4 : 2); }
 HELM_HD inline int vtiles(int dim, int P) {
   return dim == 2 ? ceil_div(P, 64) * ceil_div(P, 16) : ceil_div(P, 32) * ceil_div(P, 8) * ceil_div(P, zchunk(P));
 }
@@ -166,6 +169,30 @@ inline int tiles_per_problem(int dim, int P, TileCfg cfg) {
   return ceil_div(P, 32) * ceil_div(P, WY3) * ceil_div(P, cfg.rows);
 }
 
+// ---------------------------------------------------------------- persistent V-cycle segments
+// Passes of the small grid-wide levels walked by one cooperative launch (tiles.cuh
+// k_vcycle_seq): each pass's virtual blocks are the blocks of its ordinary launch.
+enum PassKind { PK_ARNOLDI = 0, PK_RESTRICT = 1, PK_PROLONG = 2, PK_UPDATE = 3, PK_PROLONG_FLAT = 4 };
+struct PassDesc {
+  const void* levs;  // the depth's LevelDev array (device)
+  int kind, J;
+  int ntiles;        // tiles (marching passes) or flat blocks per problem
+  int geo;           // 2D tiles per CTA, 3D planes per march
+  int f0, f1, f2, f3;  // kind-specific flags (see run_pass)
+  int nvblk;         // virtual blocks of the pass over all problems
+};
+constexpr int SEQ_MAX = 56;
+struct PassSeq {
+  int npass;
+  PassDesc p[SEQ_MAX];
+};
+static_assert(sizeof(PassSeq) <= 4000, "the pass list travels as a kernel argument");
+
+// Grid barrier of the persistent launch: arrival count and generation, cleared before
+// every launch.
+struct GridBar {
+  unsigned count, gen;
+};
 // ---------------------------------------------------------------- launchers
 enum UpdateMode { UPD_RESTRICT = 0, UPD_RESIDUAL = 1, UPD_XONLY = 2 };
 
@@ -175,13 +202,28 @@ void launch_arnoldi(int dim, int J, const LevelDev<C>* levs, int nprob, int ntil
                     bool store_p, bool tma, cudaStream_t st);
 template <typename C>
 void launch_restrict(int dim, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
-                     bool x_from_zero, bool nosmooth, cudaStream_t st);
+                     bool x_from_zero, bool nosmooth, cudaStream_t st, bool tma = false, int nraw = SMAX + 1);
 template <typename C>
 void launch_update_flat(int dim, UpdateMode mode, const LevelDev<C>* levs, int nprob, int ntiles, bool r0_is_b,
                         int xsel, bool x_from_zero, cudaStream_t st);
 template <typename C>
 void launch_prolong(int dim, bool with_residual, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg,
-                    cudaStream_t st);
+                    bool tma, cudaStream_t st);
+// Recorders of the same passes into a pass list, and the cooperative launch of a list.
+template <typename C>
+void record_arnoldi(PassSeq& q, int dim, int J, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg,
+                    bool r0_is_b, bool store_p);
+template <typename C>
+void record_restrict(PassSeq& q, int dim, const LevelDev<C>* levs, int nprob, int ntiles, TileCfg cfg, bool r0_is_b,
+                     bool x_from_zero, bool nosmooth);
+template <typename C>
+void record_update(PassSeq& q, int dim, UpdateMode mode, const LevelDev<C>* levs, int nprob, int ntiles, bool r0_is_b,
+                   int xsel, bool x_from_zero);
+template <typename C>
+void record_prolong(PassSeq& q, int dim, bool with_residual, const LevelDev<C>* levs, int nprob, int ntiles,
+                    TileCfg cfg);
+template <typename C>
+int launch_seq(int dim, const PassSeq& q, GridBar* gb, unsigned long long limit_ns, cudaStream_t st);
 template <typename C>
 void launch_coarse(int dim, const LevelDev<C>* levs, int nlev, int lev_stride, const CoarseLU* lus, int nprob,
                    int nu1, int nu2, cudaStream_t st);
@@ -207,8 +249,65 @@ void outer_apply_h(int dim, const OuterDev<C>* od, int nprob, int ntiles, TileCf
 // points plus halo) over a P x P complex field.  False when the driver has no
 // tensor-map encoder or the layout does not meet its rules.
 bool encode_level_tmaps(int P, const void* const* vectors, int count, CUtensorMap* out);
+// TMA maps of a 3D complex64 level (tma.cpp): 72 x box_rows x 1 float boxes (a 32-point
+// wide column tile plus halo, one plane) over a P^3 complex field; P a multiple of 32.
+bool encode_level_tmaps3(int P, int box_rows, const void* const* vectors, int count, CUtensorMap* out);
+// ---------------------------------------------------------------- tuned launch choices
+// (tune.cpp) keyed by pass, dimension, level pitch P, precision (bytes per complex
+// value) and Arnoldi step J (0 for the other passes); TUNE_NV integers per choice:
+//   arnoldi (step J) and prolong (J = 0), 3D, complex64: {TMA-fed pass on, plane slots
+//                            in flight, z pieces per column (0: one equal share per
+//                            resident CTA), points per thread in y (2 or 4; 0: 2)}
+//   arnoldi / restrict / prolong, 2D: {tiles per CTA}
+//   persist, 2D/3D: {grid-wide level run inside the persistent segments (1) or by its
+//                    own launches (0)}
+enum TunePass { TP_ARNOLDI = 0, TP_RESTRICT = 1, TP_PROLONG = 2, TP_PERSIST = 3 };
+constexpr int TUNE_NV = 4;
+struct TuneChoice {
+  int v[TUNE_NV];
+};
+constexpr int TM3_STAGES_MAX = 8;     // plane slots of the 3D TMA-fed pass
+// Read a table (path NULL: $HELM_TUNING, else tuning.json beside the library); replaces
+// the current one.  Entries tuned on another kind of device are dropped.
+int tune_load(const char* path, std::string* err);
+void tune_load_default();             // once per process (helm_setup)
+bool tune_get(int pass, int dim, int P, int prec_bytes, int J, TuneChoice* out);
+void tune_set(int pass, int dim, int P, int prec_bytes, int J, const TuneChoice* c);  // NULL: remove
+int tune_entries();
+// Write the current table with the kept run records and `run_record` appended.
+int tune_write(const char* path, const std::string& run_record, std::string* err);
+// 2D tiles per CTA of a pass: the tuned value, else the heuristic's.
+int tuned_tpc(int pass, int P, int prec_bytes, int J, int heuristic);
+// Whether a grid-wide level of pitch P runs inside the persistent segments: only where
+// the tuning table switches it on, for 2D levels up to 511^2 and 3D levels up to 63^3.
+bool persist_level(int dim, int P, int prec_bytes);
+// Spin limit of the persistent segments' grid barrier (helm_set_barrier_timeout; 1 s).
+unsigned long long barrier_limit_ns();
+void set_barrier_limit_ns(unsigned long long ns);
+
+// The 3D TMA-fed Arnoldi pass of step J on a level of pitch P: whether it runs (else
+// the plain pass), plane slots in flight, how the level is shared among CTAs (pieces
+// > 0: every column in that many equal z pieces, one per CTA; 0: one equal share of
+// the (column, plane) sequence per resident CTA), and points per thread in y (2, 4).
+struct Tma3Params {
+  bool enabled;
+  int stages, pieces, qy;
+};
+Tma3Params tma3_params(int pass, int J, int P);  // pass TP_ARNOLDI (step J) or TP_PROLONG (J = 0)
+constexpr int TMA3_MAX_UNITS = 2048;  // shares per problem (partial-sum slots of a 3D level)
+constexpr int TMA3_MIN_P = 128;       // the 3D TMA-fed passes run on levels of 127^3 and larger
+constexpr int TMA3_MAX_P = 1024;      // (32-bit point indices)
+// Kernels of the coarse correction of a level: 2 where a 3D complex64 level splits it
+// into the row-wise prolongation and the TMA-fed residual pass, else 1.
+inline int prolong_kernels(int dim, bool with_residual, int prec_bytes, bool tma, int P) {
+  return dim == 3 && with_residual && prec_bytes == 8 && tma && P >= TMA3_MIN_P && P <= TMA3_MAX_P &&
+                 tma3_params(TP_PROLONG, 0, P).enabled
+             ? 2
+             : 1;
+}
 // Sticky device error flag of the V-cycle kernels (a wait ran out): read and clear.
 int vcycle_take_error();
+int vcycle_take_error_c128();
 int outer_chunks(size_t vs);
 size_t outer_part_doubles(int chunks, int m);
 template <typename C>

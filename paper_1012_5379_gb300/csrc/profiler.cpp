@@ -50,6 +50,7 @@ void capture_sink_end() {
 }
 void count_launches(int kernels) { g_launches.fetch_add((unsigned long long)kernels); }
 int profile_generation() { return g_gen.load(); }
+void bump_launch_generation() { g_gen.fetch_add(1); }
 bool profiling() { return g_on; }
 
 void harvest(const std::vector<GraphRec>& recs) {

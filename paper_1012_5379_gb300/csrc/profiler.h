@@ -28,7 +28,8 @@ void capture_sink_end();
 void harvest(const std::vector<GraphRec>& recs);
 void release(std::vector<GraphRec>& recs);
 void count_launches(int kernels);
-int profile_generation();     // changes whenever profiling starts or stops
+int profile_generation();     // changes whenever profiling starts or stops, or launch choices change
+void bump_launch_generation();  // launch choices changed: captured graphs are stale
 bool profiling();
 
 // Brackets one kernel launch (or a short sequence of launches counted as `kernels`).

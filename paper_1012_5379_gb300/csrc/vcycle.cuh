@@ -181,11 +181,10 @@ __device__ __forceinline__ void update_flat_body(const UpdCoef<C>& u, C* xo, C* 
 }
 
 template <typename C>
-__global__ void __launch_bounds__(256, sizeof(C) == 16 ? 2 : 4)
-k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mode, int r0_is_b, int xsel,
-              int x_from_zero) {
+__device__ __forceinline__ void update_pass_body(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mode, int r0_is_b, int xsel,
+              int x_from_zero, int vblk) {
   __shared__ typename CT<C>::R sm[32];
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const int prob = vblk / ntiles, tile = vblk - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int P = L.P;
   pdl_wait();
@@ -194,8 +193,8 @@ k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mod
   C* r0out = L.r0;
   const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
   const bool want_r = (mode == UPD_RESIDUAL);
-  const size_t stride = (size_t)ntiles * blockDim.x;
-  const size_t i_beg = (size_t)tile * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)ntiles * block_threads();
+  const size_t i_beg = (size_t)tile * block_threads() + flat_tid();
   const bool xz = x_from_zero != 0;
   typename CT<C>::R acc = 0;
   switch (u.m) {  // uniform over the grid
@@ -219,6 +218,12 @@ k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mod
   if (grid_sum_last<1>(red, L.part, tile, ntiles, &L.sc->counter, sm, tot)) {
     if (flat_tid() == 0) sweep_begin(L.sc, tot[0], L.s);
   }
+}
+template <typename C>
+__global__ void __launch_bounds__(256, sizeof(C) == 16 ? 2 : 4)
+k_update_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int mode, int r0_is_b, int xsel,
+              int x_from_zero) {
+  update_pass_body<C>(levs, ntiles, dim, mode, r0_is_b, xsel, x_from_zero, blockIdx.x);
 }
 
 // Level-0 input: b <- src (natural layout, any precision), ||b||^2 starts the first
@@ -273,21 +278,25 @@ k_store_output(const LevelDev<C>* __restrict__ levs, int dim, Cout* __restrict__
 
 // ------------------------------------------------------------------ coarse correction
 // Coarse correction without post-smoothing (nu2 = 0): x_b = x_a + P e_c, pointwise.
-template <typename C>
-__global__ void __launch_bounds__(256)
-k_prolong_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim) {
+template <typename C, bool NC = true>
+__device__ __forceinline__ void prolong_flat_body(const LevelDev<C>* __restrict__ levs, int ntiles, int dim, int vblk) {
   pdl_trigger();
-  const int prob = blockIdx.x / ntiles, tile = blockIdx.x - prob * ntiles;
+  const int prob = vblk / ntiles, tile = vblk - prob * ntiles;
   const LevelDev<C>& L = levs[prob];
   const int n = L.n, P = L.P;
   pdl_wait();
   const size_t npts = dim == 3 ? (size_t)P * P * P : (size_t)P * P;
-  for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < npts; i += (size_t)ntiles * blockDim.x) {
+  for (size_t i = (size_t)tile * block_threads() + flat_tid(); i < npts; i += (size_t)ntiles * block_threads()) {
     const int x = (int)(i % P), y = (int)((i / P) % P), z = dim == 3 ? (int)(i / ((size_t)P * P)) : 0;
     C v = czero<C>();
-    if (inside(x, y, z, n)) v = cadd(L.xa[i], interp(L, x, y, z, dim));
+    if (inside(x, y, z, n)) v = cadd(L.xa[i], interp<C, NC>(L, x, y, z, dim));
     L.xb[i] = v;
   }
+}
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_prolong_flat(const LevelDev<C>* __restrict__ levs, int ntiles, int dim) {
+  prolong_flat_body<C>(levs, ntiles, dim, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ coarse levels
@@ -520,13 +529,23 @@ __device__ void cblock_sweep(Team& team, const LevelDev<C>& L, int dim, int r0_i
 // LU) on one team; the level vectors may live in global or shared memory (plain
 // loads only), the sweep scalars are the CTA's own.  `sm` needs 32 * (2 SMAX + 1)
 // doubles.
+// The coarsest LU factors are staged in shared memory (lu_sm, lu_cap complex values)
+// when they fit: the triangular solves read one factor per step of a serial chain,
+// and from global memory every step waited for an L2 round trip.
+constexpr int LU_STAGE = 1024;  // up to 32 coarsest unknowns (3^3 in 3D, 3^2 .. 5^2 in 2D)
 template <typename C, typename Team>
 __device__ void coarse_cycle(Team& team, const LevelDev<C>* Ls, int nlev, const CoarseLU& lu, int nu1, int nu2,
-                             int dim, double* smd) {
+                             int dim, double* smd, double2* lu_sm = nullptr, int lu_cap = 0) {
   typedef typename CT<C>::R R;
   R* sm = reinterpret_cast<R*>(smd);
   const unsigned gt = team.gtid(), gn = team.gnth();
   const int tid = flat_tid(), nth = block_threads();
+  const bool staged = lu_sm && lu.m * lu.m <= lu_cap;
+  if (staged) {
+    for (int i = tid; i < lu.m * lu.m; i += nth) lu_sm[i] = lu.lu[i];
+    __syncthreads();
+  }
+  const double2* const LUf = staged ? lu_sm : lu.lu;
   // descent
   for (int l = 0; l < nlev - 1; ++l) {
     const LevelDev<C>& L = Ls[l];
@@ -589,14 +608,14 @@ __device__ void coarse_cycle(Team& team, const LevelDev<C>* Ls, int nlev, const 
         for (int k = 0; k < m; ++k) {  // forward, unit lower
           const double2 yk = yv[k];
           __syncwarp();
-          for (int i = k + 1 + tid; i < m; i += 32) yv[i] = csub(yv[i], cmul(lu.lu[(size_t)i * m + k], yk));
+          for (int i = k + 1 + tid; i < m; i += 32) yv[i] = csub(yv[i], cmul(LUf[(size_t)i * m + k], yk));
           __syncwarp();
         }
         for (int k = m - 1; k >= 0; --k) {  // backward
-          if (tid == 0) yv[k] = ddiv(yv[k], lu.lu[(size_t)k * m + k]);
+          if (tid == 0) yv[k] = ddiv(yv[k], LUf[(size_t)k * m + k]);
           __syncwarp();
           const double2 yk = yv[k];
-          for (int i = tid; i < k; i += 32) yv[i] = csub(yv[i], cmul(lu.lu[(size_t)i * m + k], yk));
+          for (int i = tid; i < k; i += 32) yv[i] = csub(yv[i], cmul(LUf[(size_t)i * m + k], yk));
           __syncwarp();
         }
       }
@@ -781,11 +800,12 @@ __global__ void __launch_bounds__(512)
 k_coarse(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride, const CoarseLU* __restrict__ lus,
          int nu1, int nu2, int dim) {
   __shared__ double sm[32 * (2 * SMAX + 1)];
+  __shared__ double2 lu_sm[LU_STAGE];
   pdl_trigger();
   pdl_wait();
   const int prob = blockIdx.x;
   CtaTeam team;
-  coarse_cycle<C>(team, levs_all + (size_t)prob * lev_stride, nlev, lus[prob], nu1, nu2, dim, sm);
+  coarse_cycle<C>(team, levs_all + (size_t)prob * lev_stride, nlev, lus[prob], nu1, nu2, dim, sm, lu_sm, LU_STAGE);
 }
 
 // Coarse sub-cycle with every level's vectors, descriptors and sweep scalars staged
@@ -800,6 +820,7 @@ k_coarse_smem(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride
   __shared__ double sm[32 * (2 * SMAX + 1)];
   __shared__ LevelDev<C> Ls[MAX_COARSE_LEVELS];
   __shared__ SweepScalarsT<typename CT<C>::R> Ss[MAX_COARSE_LEVELS];
+  __shared__ double2 lu_sm[LU_STAGE];
   pdl_trigger();
   const int prob = blockIdx.x;
   const LevelDev<C>* G = levs_all + (size_t)prob * lev_stride;
@@ -835,7 +856,7 @@ k_coarse_smem(const LevelDev<C>* __restrict__ levs_all, int nlev, int lev_stride
   }
   __syncthreads();
   CtaTeam team;
-  coarse_cycle<C>(team, Ls, nlev, lus[prob], nu1, nu2, dim, sm);
+  coarse_cycle<C>(team, Ls, nlev, lus[prob], nu1, nu2, dim, sm, lu_sm, LU_STAGE);
   __syncthreads();
   {
     const size_t np0 = dim == 3 ? (size_t)G[0].P * G[0].P * G[0].P : (size_t)G[0].P * G[0].P;

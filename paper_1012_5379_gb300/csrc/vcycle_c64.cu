@@ -3,6 +3,8 @@
 namespace helm {
 HELM_VCYCLE_INST(float2)
 
+// The error flag is a file-scope device variable, one copy per translation unit: this
+// one (the complex64 kernels') and the complex128 unit's are read and cleared together.
 int vcycle_take_error() {
   int v = 0;
   if (cudaMemcpyFromSymbol(&v, g_vcycle_error, sizeof(int)) != cudaSuccess) return 1;
@@ -10,6 +12,7 @@ int vcycle_take_error() {
     const int z = 0;
     cudaMemcpyToSymbol(g_vcycle_error, &z, sizeof(int));
   }
-  return v;
+  const int w = vcycle_take_error_c128();
+  return v ? v : w;
 }
 }

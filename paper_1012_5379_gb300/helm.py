@@ -46,7 +46,8 @@ EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_opera
            "helm_last_error",
            "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc",
            "helm_batch_solve_host", "helm_serve_start", "helm_serve_submit", "helm_serve_poll", "helm_serve_wait",
-           "helm_serve_stats", "helm_serve_stop")
+           "helm_serve_stats", "helm_serve_stop", "helm_autotune", "helm_tuning_load", "helm_tuning_get",
+           "helm_set_barrier_timeout")
 
 
 class helm_serve_opts(ctypes.Structure):
@@ -123,6 +124,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_workspace_bytes.restype = ip
     lib.helm_levels.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
     lib.helm_levels.restype = ip
+    lib.helm_autotune.argtypes = [ctypes.POINTER(helm_grid), vp, dp, dp, ctypes.POINTER(helm_opts), ip,
+                                  ctypes.c_char_p, ctypes.POINTER(dp), ctypes.POINTER(dp), vp]
+    lib.helm_autotune.restype = ip
+    lib.helm_set_barrier_timeout.argtypes = [dp]
+    lib.helm_set_barrier_timeout.restype = ip
+    lib.helm_tuning_load.argtypes = [ctypes.c_char_p]
+    lib.helm_tuning_load.restype = ip
+    lib.helm_tuning_get.argtypes = [ctypes.c_char_p, ip, ip, ip, ip, ctypes.POINTER(ip)]
+    lib.helm_tuning_get.restype = ip
     lib.helm_precond_precision.argtypes = [vp, ctypes.POINTER(ip)]
     lib.helm_precond_precision.restype = ip
     dptr = ctypes.POINTER(ctypes.c_double)
@@ -356,6 +366,42 @@ def precond_apply_noalloc(dim: int, n: int, theta_beta: float, k: float, r, z, t
     _check(load().helm_precond_apply_noalloc(ctypes.byref(g), float(k), float(theta_beta), ctypes.byref(o),
                                              _ptr(r), _ptr(z), prec, _stream(stream)))
     return z
+
+
+def autotune(dim: int, n: int, theta_beta: float, k: Optional[float] = None, phi=None, precision: str = "c64",
+             theta_gamma: float = 0.5, ecs_frac: float = 0.125, reps: int = 10, path: Optional[str] = None,
+             stream=None):
+    """helm_autotune: tune the V-cycle's launch choices for this problem's levels on the
+    current device; returns (default, tuned) milliseconds per V-cycle.  With `path` the
+    process's whole table is written there as JSON."""
+    g = helm_grid(dim, n, ecs_frac, theta_gamma, HELM_ECS_BOTH)
+    o = helm_opts(1, 1, 3, 3, _precision_code(precision), 0, 1, 0.0, 0)
+    d0, d1 = ctypes.c_double(), ctypes.c_double()
+    _check(load().helm_autotune(ctypes.byref(g), None if phi is None else _ptr(phi),
+                                float(k if k is not None else 0.0), float(theta_beta), ctypes.byref(o), int(reps),
+                                None if path is None else path.encode(), ctypes.byref(d0), ctypes.byref(d1),
+                                _stream(stream)))
+    return d0.value, d1.value
+
+
+def set_barrier_timeout(seconds: float) -> None:
+    """helm_set_barrier_timeout: spin limit of the persistent V-cycle segments' grid
+    barrier (seconds, default 1)."""
+    _check(load().helm_set_barrier_timeout(float(seconds)))
+
+
+def tuning_load(path: Optional[str] = None) -> None:
+    """helm_tuning_load: replace the process's tuned launch choices with a JSON table."""
+    _check(load().helm_tuning_load(None if path is None else path.encode()))
+
+
+def tuning_get(pass_name: str, dim: int, P: int, precision: str = "c64", J: int = 0):
+    """helm_tuning_get: the table's 4 integers for a key, or None (built-in default)."""
+    v = (ctypes.c_int * 4)()
+    rc = load().helm_tuning_get(pass_name.encode(), int(dim), int(P), _precision_code(precision), int(J), v)
+    if rc < 0:
+        _check(rc)
+    return list(v) if rc == 1 else None
 
 
 def poly_smoother(k: float, h: float, theta_beta: float, theta_gamma: float, dim: int):

@@ -10,8 +10,15 @@
   with the oracle's H, meets the tolerance, and the iteration count stays within
   +10% (+1) of the oracle's (tests/golden/oracle_iters_1023.json, written by
   tests/golden/make_oracle_iters.py from the oracle alone).
-- The 3D 255^3 heterogeneous solve (FGMRES(40), tol 1e-6): the solution's true
-  residual under the oracle's H.
+- One V-cycle of the 3D 255^3 heterogeneous workload (complex64; its two finest
+  levels take the TMA-fed 3D Arnoldi pass) against the oracle's, point by point.
+- The 3D heterogeneous solves (FGMRES(40), tol 1e-6) on 127^3 and 255^3: the
+  solution's true residual under the oracle's H, and the iteration count within +10%
+  (+1) of the oracle's (tests/golden/oracle_iters_cube.json, written by
+  tests/golden/make_oracle_iters_cube.py from the oracle alone).
+- A batch of 10 problems drawn from the batched workload's sizes {255^2, 511^2,
+  1023^2} (more than 8 problems: the batch runs on four stream sets): every result is
+  bitwise the problem's solo result, with the same iteration count.
 """
 import json
 import os
@@ -87,6 +94,46 @@ def test_solve_1023_iterations_and_residual(helm, source, tb):
     assert np.linalg.norm(source - lev.apply_h(xs)) / np.linalg.norm(source) <= 1.05e-6
 
 
+def test_vcycle_3d_255_heterogeneous_matches_oracle_c64(helm):
+    w = I.cube_3d(255)
+    levels = O.build_hierarchy(3, 255, w.theta_beta, phi=w.phi.astype(np.float64))
+    src = I.random_source(3, 255, 1005)
+    want = O.vcycle(levels, src, 1, 1, 3)
+    del levels
+    h = helm.Handle(3, 255, w.theta_beta, phi=torch.from_numpy(w.phi).cuda(), precision="c64", maxit=1)
+    r = torch.from_numpy(src).cuda().to(torch.complex64)
+    z = torch.empty_like(r)
+    h.precond_apply(r, z)
+    h.close()
+    assert_parity(z, want, 5e-5, "255^3 V-cycle c64")
+
+
+def cube_oracle_iters(n):
+    path = os.path.join(HERE, "golden", "oracle_iters_cube.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))["by_n"].get(str(n))
+    return rec["iters"] if rec else None
+
+
+def test_solve_3d_127_heterogeneous_iterations(helm):
+    ref = cube_oracle_iters(127)
+    if ref is None:
+        pytest.skip("oracle iteration count of 127^3 not generated")
+    w = I.cube_3d(127)
+    h = helm.Handle(3, 127, w.theta_beta, phi=torch.from_numpy(w.phi).cuda(), precision="c64", restart=40,
+                    maxit=400)
+    b = torch.from_numpy(w.b).cuda()
+    x = torch.zeros_like(b)
+    info = h.solve(b, x, w.tol)
+    h.close()
+    assert info.status == 0 and info.rel_res_true <= w.tol
+    assert info.iters <= int(1.1 * ref) + 1, (info.iters, ref)
+    lev = O.build_hierarchy(3, 127, w.theta_beta, phi=w.phi)[0]
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(w.b - lev.apply_h(xs)) / np.linalg.norm(w.b) <= 1.05 * w.tol
+
+
 def test_solve_3d_255_heterogeneous_true_residual(helm):
     w = I.cube_3d(255)
     h = helm.Handle(3, 255, w.theta_beta, phi=torch.from_numpy(w.phi).cuda(), precision="c64", restart=40,
@@ -96,8 +143,28 @@ def test_solve_3d_255_heterogeneous_true_residual(helm):
     info = h.solve(b, x, w.tol)
     h.close()
     assert info.status == 0 and info.rel_res_true <= w.tol
+    ref = cube_oracle_iters(255)
+    if ref is not None:
+        assert info.iters <= int(1.1 * ref) + 1, (info.iters, ref)
     lev = O.build_hierarchy(3, 255, w.theta_beta, phi=w.phi)[0]
     xs = x.cpu().numpy()
     del x, b
     torch.cuda.empty_cache()
     assert np.linalg.norm(w.b - lev.apply_h(xs)) / np.linalg.norm(w.b) <= 1.05 * w.tol
+
+
+def test_batch_of_workload_sizes_equals_alone_bitwise(helm):
+    ws = I.batch_2d(count=10, seed=91)
+    assert {w.n for w in ws} == {255, 511, 1023}
+    hs = [helm.Handle(2, w.n, w.theta_beta, k=w.k, precision="c64", restart=w.restart) for w in ws]
+    bs = [torch.from_numpy(w.b).cuda() for w in ws]
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = helm.batch_solve(hs, bs, xs, 1e-6)
+    for w, h, b, x, inf in zip(ws, hs, bs, xs, infos):
+        solo = torch.zeros_like(b)
+        sinfo = h.solve(b, solo, 1e-6)
+        assert inf.status == 0 and sinfo.status == 0 and inf.iters == sinfo.iters, (w.n, inf, sinfo)
+        assert torch.equal(solo, x), w.n
+        assert inf.rel_res_true <= 1e-6
+    for h in hs:
+        h.close()

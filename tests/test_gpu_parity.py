@@ -185,7 +185,7 @@ def test_poly_argument_checks(helm):
 VC_CASES = [
     (2, 15, "c128"), (2, 31, "c128"), (2, 63, "c128"), (2, 127, "c128"), (2, 255, "c128"),
     (3, 7, "c128"), (3, 15, "c128"), (3, 31, "c128"),
-    (2, 63, "c64"), (2, 255, "c64"), (2, 511, "c64"), (3, 31, "c64"), (3, 63, "c64"),
+    (2, 63, "c64"), (2, 255, "c64"), (2, 511, "c64"), (3, 31, "c64"), (3, 63, "c64"), (3, 127, "c64"),
 ]
 
 
