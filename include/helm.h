@@ -99,9 +99,33 @@ typedef struct {
                      * HELM_SMOOTHER_POLY: the third-degree polynomial smoother of Sec. 4
                      * (three Richardson steps per sweep, weights from helm_poly_smoother per
                      * level; constant k, csl_eps = 0, s ignored).  [HELM_SMOOTHER_GMRES] */
+  int outer_basis;  /* arithmetic of the outer FGMRES Krylov basis v_i, of w = H z_j and of the
+                     * orthogonalisation h_ij = <v_i, w>, u = w - sum h_ij v_i (Sec. 5):
+                     * HELM_BASIS_F64: binary64 throughout;
+                     * HELM_BASIS_DF: double-float, each real a pair of binary32 (hi + lo, 47
+                     *   significant bits) multiplied and summed with error-free transformations
+                     *   on the FP32 pipe; an inner product of n points errs by at most about
+                     *   (4 + K) 2^-45 sum |v_i||w_i|, K the points one thread sums
+                     *   (ceil(n / 77,824) on 152 SMs), which is inside binary64's
+                     *   recursive-summation bound n u sum |v_i||w_i| (u = 2^-53) for n >= 2048;
+                     *   with a complex64 preconditioner w = H z_j is formed in double-float too;
+                     * HELM_BASIS_AUTO: double-float for grids of more than HELM_AUTO_C128_POINTS
+                     *   unknowns solved to tol >= HELM_BASIS_DF_MIN_TOL, binary64 otherwise.  On
+                     *   small grids the orthogonalisation costs little either way, and problems
+                     *   with bound states are sensitive to any rounding there (Benchmark 3 of
+                     *   Sec. 5, nu = 7 on 64^2: 79 outer iterations with binary64, 80 with
+                     *   double-float); on the larger grids the two take the same counts.
+                     * The Hessenberg matrix, the Givens rotations, the least-squares solution, the
+                     * stored z_j, the solution x (updated in double-float with a double-float
+                     * basis and a complex64 preconditioner) and the true residual b - H x that
+                     * decides convergence are held in binary64 in every mode.  [HELM_BASIS_AUTO] */
 } helm_opts;
 #define HELM_SMOOTHER_GMRES 0
 #define HELM_SMOOTHER_POLY 1
+#define HELM_BASIS_AUTO 0
+#define HELM_BASIS_F64 1
+#define HELM_BASIS_DF 2
+#define HELM_BASIS_DF_MIN_TOL 1e-9
 /* The Krylov basis length m = min(restart, maxit) (maxit without restart) is at most
  * HELM_MAX_BASIS; helm_setup returns HELM_EINVAL above it. */
 #define HELM_MAX_BASIS 1536
@@ -112,6 +136,8 @@ typedef struct {
   double rel_res_est;  /* Arnoldi estimate |g_{j+1}| / ||b|| at exit */
   double rel_res_true; /* ||b - H x|| / ||b|| recomputed in FP64 at exit */
   int status;          /* HELM_OK, HELM_ENOCONV or HELM_ENUMERIC */
+  int basis;           /* the arithmetic the solve's Krylov basis ran in: HELM_BASIS_F64 or
+                        * HELM_BASIS_DF (what HELM_BASIS_AUTO resolved to) */
 } helm_info;
 
 /* Build the CSG hierarchy (Sec. 3.1, Prop. 3.1) and the ECS operator H for one
@@ -355,6 +381,19 @@ int helm_tuning_get(const char* pass, int dim, int P, int prec, int J, int* v);
  * 1.  The paper has no counterpart: this bounds a wait of this GPU implementation (a
  * limit of 0 makes every waiting CTA give up at once, which tests the error path). */
 int helm_set_barrier_timeout(double seconds);
+
+/* The outer multi-dot of FGMRES (Sec. 5: the inner products h_ij = <v_i, w> of the
+ * Arnoldi step) on caller data: h[i] = sum_p conj(V_i[p]) w[p], i = 0..nvec-1, through
+ * the same pass a solve runs, with V and w first stored in the basis arithmetic `basis`
+ * (HELM_BASIS_F64 or HELM_BASIS_DF, see helm_opts.outer_basis).  For checking the
+ * orthogonalisation's accuracy apart from a solve.
+ *   V:  device array of nvec vectors of npts complex128 (interleaved re, im), vector i at
+ *       V + 2 i npts; w: device array of npts complex128.  Both are read only.
+ *   h:  HOST array of 2 nvec doubles (complex128 results).
+ *   1 <= nvec <= HELM_MAX_BASIS + 1, 1 <= npts <= 2^34.  The call allocates a
+ *   workspace of about (nvec + 1) npts 16 bytes, runs on `stream` and synchronises it.
+ * Errors: HELM_EINVAL (arguments), HELM_ENOMEM, HELM_ECUDA. */
+int helm_multidot(int basis, const double* V, int nvec, size_t npts, const double* w, double* h, void* stream);
 
 /* Kernels this library has launched in the process so far (all handles, all
  * streams).  The paper has no counterpart: this is launch accounting for

@@ -217,6 +217,13 @@ int helm_autotune(const helm_grid* grid, const float* phi, double k, double thet
   })
 }
 
+int helm_multidot(int basis, const double* V, int nvec, size_t npts, const double* w, double* h, void* stream) {
+  HELM_GUARD({
+    return helm::multidot(basis, (const double2*)V, nvec, npts, (const double2*)w, (double2*)h,
+                          (cudaStream_t)stream);
+  })
+}
+
 int helm_set_barrier_timeout(double seconds) {
   HELM_GUARD({
     if (!(seconds >= 0.0 && seconds <= 60.0)) { helm::set_error("seconds must be in [0, 60]"); return HELM_EINVAL; }

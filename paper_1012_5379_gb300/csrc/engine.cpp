@@ -171,6 +171,11 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
   h->maxit = o.maxit > 0 ? o.maxit : 400;
   h->csl_eps = o.csl_eps;
   h->smoother = o.smoother;
+  h->basis = o.outer_basis;
+  if (h->basis != HELM_BASIS_AUTO && h->basis != HELM_BASIS_F64 && h->basis != HELM_BASIS_DF) {
+    set_error("outer_basis must be HELM_BASIS_AUTO, HELM_BASIS_F64 or HELM_BASIS_DF");
+    return HELM_EINVAL;
+  }
   if (h->dim != 2 && h->dim != 3) { set_error("dim must be 2 or 3"); return HELM_EINVAL; }
   if (h->n < 1 || h->n > (h->dim == 2 ? 32767 : 2047)) { set_error("n out of range"); return HELM_EINVAL; }
   if (h->ecs_sides != HELM_ECS_BOTH && h->ecs_sides != HELM_ECS_HIGH) {
@@ -311,6 +316,18 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     }
     TRY(dev_alloc(h.get(), &h->hcoef, hc.size() * sizeof(double2)));
     CUDA_TRY(cudaMemcpyAsync(h->hcoef, hc.data(), hc.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    std::vector<float4> hcf(hc.size());
+    auto split = [](double v, float* hi, float* lo) {
+      *hi = (float)v;
+      *lo = (float)(v - (double)*hi);
+    };
+    for (size_t i = 0; i < hc.size(); ++i) {
+      split(hc[i].x, &hcf[i].x, &hcf[i].y);
+      split(hc[i].y, &hcf[i].z, &hcf[i].w);
+    }
+    TRY(dev_alloc(h.get(), &h->hcoef_df, hcf.size() * sizeof(float4)));
+    CUDA_TRY(cudaMemcpyAsync(h->hcoef_df, hcf.data(), hcf.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));  // hc and hcf are host staging of this frame
     h->vs = L0.np;
     h->ntiles0 = L0.ntiles;
     h->chunks = outer_chunks(h->vs);
@@ -387,6 +404,7 @@ static OuterDev<C> make_outerdev(const Handle& h) {
   o.ca = h.hcoef;
   o.cd = h.hcoef + h.n;
   o.cc = h.hcoef + 2 * h.n;
+  o.cdf = h.hcoef_df;
   o.phi = h.lev[0].phi;
   o.phic = h.lev[0].phic;
   o.bpad = h.bpad;
@@ -940,6 +958,76 @@ int apply_operator(Handle* h, int which, const void* v, void* w, int prec, cudaS
   return HELM_OK;
 }
 
+// h_i = <v_i, w>, i < nvec, on caller data through the outer multi-dot pass (k_dots)
+// with the basis held in the arithmetic `basis` selects: the accuracy of the FGMRES
+// orthogonalisation checked apart from a solve.
+int multidot(int basis, const double2* V, int nvec, size_t npts, const double2* w, double2* h_host,
+             cudaStream_t st) {
+  if (!V || !w || !h_host) { set_error("NULL argument"); return HELM_EINVAL; }
+  if (basis != HELM_BASIS_F64 && basis != HELM_BASIS_DF) { set_error("basis must be HELM_BASIS_F64 or HELM_BASIS_DF"); return HELM_EINVAL; }
+  if (nvec < 1 || nvec > HELM_MAX_BASIS + 1) { set_error("nvec must be in 1..HELM_MAX_BASIS + 1"); return HELM_EINVAL; }
+  if (npts < 1 || npts > ((size_t)1 << 34)) { set_error("npts must be in 1..2^34"); return HELM_EINVAL; }
+  const int m = nvec;  // column j = nvec - 1 of an (m + 1) x m Hessenberg matrix
+  const int chunks = outer_chunks(npts);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t bV = al((size_t)nvec * npts * sizeof(double2)), bw = al(npts * sizeof(double2));
+  const size_t bst = al(sizeof(OuterState)), bpart = al(outer_part_doubles(chunks, m) * sizeof(double));
+  const size_t bH = al((size_t)(m + 1) * m * sizeof(double2)), bcol = al((size_t)(m + 1) * sizeof(double2));
+  const size_t bsc = al((size_t)(m + 1) * sizeof(double)), bod = al(sizeof(OuterDev<float2>));
+  char* base = nullptr;
+  if (cudaMalloc(&base, bV + bw + bst + bpart + bH + bcol + bsc + bod) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("multidot: cannot allocate the workspace");
+    return HELM_ENOMEM;
+  }
+  struct Free {
+    void* p;
+    ~Free() { cudaFree(p); }
+  } fr{base};
+  char* q = base;
+  auto take = [&](size_t b) { char* r = q; q += b; return r; };
+  double2* Vb = (double2*)take(bV);
+  double2* wb = (double2*)take(bw);
+  OuterState* dst = (OuterState*)take(bst);
+  double* part = (double*)take(bpart);
+  double2* Hm = (double2*)take(bH);
+  double2* hcol = (double2*)take(bcol);
+  double* vscale = (double*)take(bsc);
+  OuterDev<float2>* od = (OuterDev<float2>*)take(bod);
+  const int df = basis == HELM_BASIS_DF;
+  basis_store(V, Vb, (size_t)nvec * npts, df, st);
+  basis_store(w, wb, npts, df, st);
+  CUDA_TRY(cudaMemsetAsync(part, 0, bpart, st));
+  OuterState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.j = nvec - 1;
+  s0.m = m;
+  s0.df = df;
+  std::vector<double> ones((size_t)m + 1, 1.0);
+  OuterDev<float2> o;
+  std::memset(&o, 0, sizeof(o));
+  o.vs = npts;
+  o.V = Vb;
+  o.w = wb;
+  o.Hm = Hm;
+  o.hcol = hcol;
+  o.vscale = vscale;
+  o.part = part;
+  o.st = dst;
+  // host staging lives on this frame: the stream is synchronised before it returns
+  CUDA_TRY(cudaMemcpyAsync(dst, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(vscale, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(od, &o, sizeof(o), cudaMemcpyHostToDevice, st));
+  {
+    Launch L("out.dots", st, 0, 0);
+    outer_dots<float2>(od, 1, chunks, m, st);
+  }
+  CUDA_TRY(cudaMemcpyAsync(h_host, hcol, (size_t)nvec * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
 // ------------------------------------------------------------------ FGMRES driver
 // Outer FP64 kernels: bytes and flops per point of each pass (j+1 basis vectors).
 template <typename C>
@@ -1007,6 +1095,9 @@ static int begin_problem(Handle* h, const double2* b_dense, const double2* x_den
   s0.m = h->m;
   s0.maxit = h->maxit;
   s0.tol = tol;
+  const double pts = h->dim == 3 ? (double)h->n * h->n * h->n : (double)h->n * h->n;
+  s0.df = h->basis == HELM_BASIS_DF ||
+          (h->basis == HELM_BASIS_AUTO && tol >= HELM_BASIS_DF_MIN_TOL && pts > HELM_AUTO_C128_POINTS);
   s0.bnorm = -1.0;
   s0.need_residual = 1;
   CUDA_TRY(cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
@@ -1031,6 +1122,7 @@ static int finish_problem(Handle* h, const OuterState& s, double2* x_dense, cuda
     info->rel_res_est = s.rel_est;
     info->rel_res_true = s.rel_true;
     info->status = status;
+    info->basis = s.df ? HELM_BASIS_DF : HELM_BASIS_F64;
   }
   CUDA_TRY(cudaGetLastError());
   return status;

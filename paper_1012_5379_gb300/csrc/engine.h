@@ -60,6 +60,7 @@ struct Handle {
   int ecs_sides = 0;              // HELM_ECS_BOTH or HELM_ECS_HIGH
   double csl_eps = 0;             // complex shift of M: L - (1 + i csl_eps) phi
   int smoother = 0;               // HELM_SMOOTHER_GMRES or HELM_SMOOTHER_POLY
+  int basis = 0;                  // HELM_BASIS_AUTO, HELM_BASIS_F64 or HELM_BASIS_DF (outer Krylov basis)
   std::vector<std::array<std::complex<double>, 3>> polyw;  // Richardson weights per smoothed level
   bool has_phi = false;
   TileCfg cfg{8};
@@ -68,6 +69,7 @@ struct Handle {
   int* piv = nullptr;
   int lu_m = 0;
   double2* hcoef = nullptr;   // 3n FP64 coefficients of H
+  float4* hcoef_df = nullptr; // the same as double-floats (hi + lo, rounded to nearest)
   // outer FGMRES storage
   size_t vs = 0;
   double2* bpad = nullptr;
@@ -108,6 +110,8 @@ int autotune(const helm_grid* grid, const float* phi, double k, double theta_bet
              const char* path, double* default_ms, double* tuned_ms, cudaStream_t st);
 int precond_apply_noalloc(const helm_grid* grid, double k, double theta_beta, const helm_opts* opts,
                           const void* r, void* z, int prec, cudaStream_t st);
+int multidot(int basis, const double2* V, int nvec, size_t npts, const double2* w, double2* h_host,
+             cudaStream_t st);
 // Problems iterated together, joining and leaving between outer iterations.
 struct BatchRunner;
 BatchRunner* runner_create(int prec);

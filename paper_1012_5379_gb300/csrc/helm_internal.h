@@ -115,7 +115,7 @@ struct OuterState {
   unsigned int counter;   // last-block counter
   int need_residual;      // 1: the true residual must be recomputed (start or cycle end)
   int fresh;              // 1: a new cycle starts, v_0 must be formed
-  int pad;
+  int df;                 // 1: the Krylov basis and H z_j are held and reduced in double-float
 };
 
 // Per-problem pointers of the outer solve (device memory).
@@ -123,6 +123,7 @@ template <typename C>
 struct OuterDev {
   int n, P, ntiles;
   const double2* ca; const double2* cd; const double2* cc;  // H coefficients
+  const float4* cdf;      // the same as double-floats: a, d, c blocks of n
   const float* phi; double phic;
   double2* bpad;          // b in padded layout
   double2* xpad;          // x in padded layout
@@ -310,6 +311,7 @@ int vcycle_take_error();
 int vcycle_take_error_c128();
 int outer_chunks(size_t vs);
 size_t outer_part_doubles(int chunks, int m);
+void basis_store(const double2* src, double2* dst, size_t n, int df, cudaStream_t st);
 template <typename C>
 void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t st);
 template <typename C>

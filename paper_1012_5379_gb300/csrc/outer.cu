@@ -12,9 +12,20 @@
 // sqrt(||w||^2 - sum |h|^2), whose cancellation made the basis lose orthogonality
 // once the preconditioned operator is close to the identity.
 // At a cycle end: y = R^{-1} g, x += Z y, true residual b - H x recomputed in FP64.
+//
+// Basis arithmetic (OuterState::df): binary64, or double-float (dfloat.cuh) for the
+// basis V, for w = H z_j as the multi-dot and the update read it, and for their
+// products and sums.  The double-float passes run on the FP32 pipe, which issues 64
+// instructions where the FP64 pipe issues one; in binary64 the multi-dot and the update
+// are bound by the FP64 pipe (4 FMA per point and vector against 16 bytes), in
+// double-float by HBM.  With a complex64 preconditioner the stencil forms H z_j in
+// double-float from the exact complex64 z_j, and x += Z y accumulates in double-float
+// too; the Hessenberg column, the rotations, y, the stored x and Z and the true residual
+// stay binary64.
 #include <algorithm>
 
 #include "device_common.cuh"
+#include "dfloat.cuh"
 #include "vcycle.cuh"
 
 namespace helm {
@@ -69,6 +80,121 @@ __device__ __forceinline__ void outer_stencil_epilogue(const OuterDev<C>& O, Out
   }
 }
 
+// ---- w = H z_j in double-float (complex64 z_j, FP32 pipe)
+// H's coefficients as double-floats (a, d, c blocks of n), zero outside 0..n-1.
+__device__ __forceinline__ float4 ldh_df(const float4* cdf, int which, int i, int n) {
+  return (unsigned)i < (unsigned)n ? __ldg(cdf + (size_t)which * n + i) : make_float4(0, 0, 0, 0);
+}
+__device__ __forceinline__ float2 ldz(const float2* p, int x, int y, int z, int n, int P) {
+  return inside(x, y, z, n) ? __ldg(p + pidx(x, y, z, P)) : make_float2(0, 0);
+}
+__device__ __forceinline__ float2 shfl_f2(float2 v, int d, bool up) {
+  return up ? make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d))
+            : make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+// One point: diag = d_x + d_y (+ d_z) - phi assembled in double-float, then the five or
+// seven products summed with TwoSum; returns the double-float result and adds |w_p|^2
+// to (ns, nc).  dxy holds d_x + d_y; the z terms enter only in 3D.
+__device__ __forceinline__ float4 hpoint_df(float4 dxy, float4 dz, float phih, float phil, float4 ax, float4 cxr,
+                                            float4 ay, float4 cyr, float4 az, float4 czr, float2 v0, float2 vl,
+                                            float2 vr, float2 vs, float2 vn, float2 vm, float2 vp, bool three,
+                                            float& ns, float& nc) {
+  float4 dg = three ? df_cadd(dxy, dz) : dxy;
+  const float2 dre = df_add(dg.x, dg.y, -phih, -phil);
+  dg.x = dre.x;
+  dg.y = dre.y;
+  DfAcc a{0.0f, 0.0f, 0.0f, 0.0f};
+  df_cmac(a, dg, v0);
+  df_cmac(a, ax, vl);
+  df_cmac(a, cxr, vr);
+  df_cmac(a, ay, vs);
+  df_cmac(a, cyr, vn);
+  if (three) {
+    df_cmac(a, az, vm);
+    df_cmac(a, czr, vp);
+  }
+  float hr, lr, hi, li;
+  df_two_sum(a.sr, a.cr, hr, lr);
+  df_two_sum(a.si, a.ci, hi, li);
+  df_mac(ns, nc, hr, lr, hr, lr);
+  df_mac(ns, nc, hi, li, hi, li);
+  df_renorm(ns, nc);
+  return make_float4(hr, lr, hi, li);
+}
+
+// 2D rows ybeg..yend-1 of one warp column; returns this thread's share of ||w||^2.
+__device__ double hstencil2_df(const OuterDev<float2>& O, const float2* u1, float2* zarch, int x, int ybeg,
+                               int yend, int lane) {
+  const int n = O.n, P = O.P;
+  const float4 ax = ldh_df(O.cdf, 0, x, n), dx = ldh_df(O.cdf, 1, x, n), cxr = ldh_df(O.cdf, 2, x, n);
+  const float2 pc = df_split(O.phic);
+  const float4 zero = make_float4(0, 0, 0, 0);
+  float ns = 0.0f, nc = 0.0f;
+  if (ybeg < P) {
+    float2 vm = ldz(u1, x, ybeg - 1, 0, n, P), v0 = ldz(u1, x, ybeg, 0, n, P);
+    for (int y = ybeg; y < yend; ++y) {
+      const float2 vp = ldz(u1, x, y + 1, 0, n, P);
+      float2 vl = shfl_f2(v0, 1, true), vr = shfl_f2(v0, 1, false);
+      if (lane == 0) vl = ldz(u1, x - 1, y, 0, n, P);
+      if (lane == 31) vr = ldz(u1, x + 1, y, 0, n, P);
+      if (x < P) {
+        float4 o = zero;
+        if (x < n && y < n) {
+          const float4 ay = ldh_df(O.cdf, 0, y, n), dy = ldh_df(O.cdf, 1, y, n), cyr = ldh_df(O.cdf, 2, y, n);
+          const float ph = O.phi ? __ldg(O.phi + pidx(x, y, 0, P)) : pc.x, pl = O.phi ? 0.0f : pc.y;
+          o = hpoint_df(df_cadd(dx, dy), zero, ph, pl, ax, cxr, ay, cyr, zero, zero, v0, vl, vr, vm, vp, vm, vp,
+                        false, ns, nc);
+        }
+        reinterpret_cast<float4*>(O.w)[pidx(x, y, 0, P)] = o;
+        zarch[pidx(x, y, 0, P)] = u1[pidx(x, y, 0, P)];
+      }
+      vm = v0;
+      v0 = vp;
+    }
+  }
+  return df_value(ns, nc);
+}
+
+// 3D: the block's 32 x (WY3 + 2) columns marching planes zbeg..zend-1 (y neighbours
+// through a two-plane shared ring, as the binary64 pass does).
+__device__ double hstencil3_df(const OuterDev<float2>& O, const float2* u1, float2* zarch, int x, int y, int zbeg,
+                               int zend, int w, int lane, bool owned) {
+  __shared__ float2 svf[2][WY3 + 2][32];
+  const int n = O.n, P = O.P;
+  const float4 ax = ldh_df(O.cdf, 0, x, n), cxr = ldh_df(O.cdf, 2, x, n);
+  const float4 ay = ldh_df(O.cdf, 0, y, n), cyr = ldh_df(O.cdf, 2, y, n);
+  const float4 dxy = df_cadd(ldh_df(O.cdf, 1, x, n), ldh_df(O.cdf, 1, y, n));
+  const float2 pc = df_split(O.phic);
+  float ns = 0.0f, nc = 0.0f;
+  if (zbeg < P) {
+    float2 vm = ldz(u1, x, y, zbeg - 1, n, P), v0 = ldz(u1, x, y, zbeg, n, P);
+    for (int z = zbeg; z < zend; ++z) {
+      const float2 vp = ldz(u1, x, y, z + 1, n, P);
+      svf[z & 1][w][lane] = v0;
+      __syncthreads();
+      if (owned) {
+        const float2 vs = svf[z & 1][w - 1][lane], vn = svf[z & 1][w + 1][lane];
+        float2 vl = shfl_f2(v0, 1, true), vr = shfl_f2(v0, 1, false);
+        if (lane == 0) vl = ldz(u1, x - 1, y, z, n, P);
+        if (lane == 31) vr = ldz(u1, x + 1, y, z, n, P);
+        if (x < P && y < P) {
+          float4 o = make_float4(0, 0, 0, 0);
+          if (inside(x, y, z, n)) {
+            const float4 az = ldh_df(O.cdf, 0, z, n), dz = ldh_df(O.cdf, 1, z, n), czr = ldh_df(O.cdf, 2, z, n);
+            const float ph = O.phi ? __ldg(O.phi + pidx(x, y, z, P)) : pc.x, pl = O.phi ? 0.0f : pc.y;
+            o = hpoint_df(dxy, dz, ph, pl, ax, cxr, ay, cyr, az, czr, v0, vl, vr, vs, vn, vm, vp, true, ns, nc);
+          }
+          reinterpret_cast<float4*>(O.w)[pidx(x, y, z, P)] = o;
+          zarch[pidx(x, y, z, P)] = u1[pidx(x, y, z, P)];
+        }
+      }
+      vm = v0;
+      v0 = vp;
+    }
+  }
+  return df_value(ns, nc);
+}
+
 template <typename C, int MODE>
 __global__ void __launch_bounds__(32 * WARPS2)
 k_hstencil2(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
@@ -88,12 +214,20 @@ k_hstencil2(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
   const C* u1 = stencil_src<C, MODE>(O, st);
   C* zarch = O.Z + (size_t)st->j * O.vs;
   const double2* u0 = O.xpad;
+  const bool df = MODE == 1 && st->df;  // H z_j stored as a double-float
   auto form = [&](int xx, int yy) -> double2 {
     return MODE == 0 ? ldd(u0, xx, yy, 0, n, P) : ldd(u1, xx, yy, 0, n, P);
   };
   const HCoef cx = ldh(O.ca, O.cd, O.cc, x, n);
   double accw = 0.0, accb = 0.0;
-  if (ybeg < P) {
+  bool dfdone = false;
+  if constexpr (MODE == 1 && sizeof(C) == 8) {
+    if (df) {
+      accw = hstencil2_df(O, u1, zarch, x, ybeg, yend, lane);
+      dfdone = true;
+    }
+  }
+  if (!dfdone && ybeg < P) {
     double2 vm = form(x, ybeg - 1), v0 = form(x, ybeg);
     for (int y = ybeg; y < yend; ++y) {
       double2 vp = form(x, y + 1);
@@ -120,7 +254,8 @@ k_hstencil2(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
           }
           accw += dabs2(out);
         }
-        O.w[pidx(x, y, 0, P)] = out;
+        if (df) reinterpret_cast<float4*>(O.w)[pidx(x, y, 0, P)] = df_split(out);
+        else O.w[pidx(x, y, 0, P)] = out;
         if (MODE == 1) zarch[pidx(x, y, 0, P)] = u1[pidx(x, y, 0, P)];
       }
       vm = v0;
@@ -155,12 +290,20 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
   const C* u1 = stencil_src<C, MODE>(O, st);
   C* zarch = O.Z + (size_t)st->j * O.vs;
   const double2* u0 = O.xpad;
+  const bool df = MODE == 1 && st->df;  // H z_j stored as a double-float
   auto form = [&](int xx, int yy, int zz) -> double2 {
     return MODE == 0 ? ldd(u0, xx, yy, zz, n, P) : ldd(u1, xx, yy, zz, n, P);
   };
   const HCoef cx = ldh(O.ca, O.cd, O.cc, x, n), cy = ldh(O.ca, O.cd, O.cc, y, n);
   double accw = 0.0, accb = 0.0;
-  if (zbeg < P) {
+  bool dfdone = false;
+  if constexpr (MODE == 1 && sizeof(C) == 8) {
+    if (df) {
+      accw = hstencil3_df(O, u1, zarch, x, y, zbeg, zend, w, lane, owned);
+      dfdone = true;
+    }
+  }
+  if (!dfdone && zbeg < P) {
     double2 vm = form(x, y, zbeg - 1), v0 = form(x, y, zbeg);
     for (int z = zbeg; z < zend; ++z) {
       double2 vp = form(x, y, z + 1);
@@ -193,7 +336,8 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
             }
             accw += dabs2(out);
           }
-          O.w[pidx(x, y, z, P)] = out;
+          if (df) reinterpret_cast<float4*>(O.w)[pidx(x, y, z, P)] = df_split(out);
+          else O.w[pidx(x, y, z, P)] = out;
           if (MODE == 1) zarch[pidx(x, y, z, P)] = u1[pidx(x, y, z, P)];
         }
       }
@@ -261,6 +405,59 @@ __device__ __forceinline__ double warp_transpose_sum16(double (&v)[16], int lane
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// One thread's sums over its points of the DOT_VB vectors vb .. vb + nv - 1: acc[2 t]
+// and acc[2 t + 1] the real and imaginary parts of <v_{vb+t}, w>.
+__device__ __forceinline__ void dots_block_f64(const double2* V, const double2* W, size_t npts, int vb, int nv,
+                                               size_t beg, size_t end, double (&acc)[2 * DOT_VB]) {
+  const double2* vbase = V + (size_t)vb * npts;
+#pragma unroll
+  for (int k = 0; k < 2 * DOT_VB; ++k) acc[k] = 0.0;
+#pragma unroll 2
+  for (size_t idx = beg; idx < end; idx += DOT_THREADS) {
+    const double2 w = __ldcg(W + idx);
+#pragma unroll
+    for (int t = 0; t < DOT_VB; ++t) {
+      if (t < nv) {
+        const double2 v = __ldcs(vbase + (size_t)t * npts + idx);
+        acc[2 * t] = fma(v.x, w.x, acc[2 * t]);
+        acc[2 * t] = fma(v.y, w.y, acc[2 * t]);
+        acc[2 * t + 1] = fma(v.x, w.y, acc[2 * t + 1]);
+        acc[2 * t + 1] = fma(-v.y, w.x, acc[2 * t + 1]);
+      }
+    }
+  }
+}
+// The same sums with the basis and w in double-float (FP32 pipe), widened to binary64
+// at the end: conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr), four multiply-adds.
+__device__ __forceinline__ void dots_block_df(const double2* V, const double2* W, size_t npts, int vb, int nv,
+                                              size_t beg, size_t end, double (&acc)[2 * DOT_VB]) {
+  const float4* vbase = reinterpret_cast<const float4*>(V) + (size_t)vb * npts;
+  const float4* w4 = reinterpret_cast<const float4*>(W);
+  float s[2 * DOT_VB], c[2 * DOT_VB];
+#pragma unroll
+  for (int k = 0; k < 2 * DOT_VB; ++k) s[k] = c[k] = 0.0f;
+  for (size_t idx = beg; idx < end; idx += DOT_THREADS) {
+    const float4 w = __ldcg(w4 + idx);
+    float4 v[DOT_VB];
+#pragma unroll
+    for (int t = 0; t < DOT_VB; ++t)
+      if (t < nv) v[t] = __ldcs(vbase + (size_t)t * npts + idx);
+#pragma unroll
+    for (int t = 0; t < DOT_VB; ++t) {
+      if (t < nv) {
+        df_mac(s[2 * t], c[2 * t], v[t].x, v[t].y, w.x, w.y);
+        df_mac(s[2 * t], c[2 * t], v[t].z, v[t].w, w.z, w.w);
+        df_mac(s[2 * t + 1], c[2 * t + 1], v[t].x, v[t].y, w.z, w.w);
+        df_mac(s[2 * t + 1], c[2 * t + 1], -v[t].z, -v[t].w, w.x, w.y);
+        df_renorm(s[2 * t], c[2 * t]);
+        df_renorm(s[2 * t + 1], c[2 * t + 1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * DOT_VB; ++k) acc[k] = df_value(s[k], c[k]);
+}
+
 template <typename C>
 __global__ void __launch_bounds__(DOT_THREADS, 2)
 k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
@@ -281,26 +478,12 @@ k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
     unsigned* gcnt = reinterpret_cast<unsigned*>(gpart + (size_t)ngroups * M1 * 2);  // [ngroups]
     double* wsum = sred + (size_t)warp * 2 * M1;
     __syncthreads();  // the previous unit's readers of sred are done
+    const bool df = st->df;
     for (int vb = 0; vb <= j; vb += DOT_VB) {
       const int nv = min(DOT_VB, j + 1 - vb);
-      const double2* vbase = O.V + (size_t)vb * npts;
       double acc[2 * DOT_VB];
-#pragma unroll
-      for (int k = 0; k < 2 * DOT_VB; ++k) acc[k] = 0.0;
-#pragma unroll 2
-      for (size_t idx = ubeg + tid; idx < uend; idx += DOT_THREADS) {
-        const double2 w = __ldcg(O.w + idx);
-#pragma unroll
-        for (int t = 0; t < DOT_VB; ++t) {
-          if (t < nv) {
-            const double2 v = __ldcs(vbase + (size_t)t * npts + idx);
-            acc[2 * t] = fma(v.x, w.x, acc[2 * t]);
-            acc[2 * t] = fma(v.y, w.y, acc[2 * t]);
-            acc[2 * t + 1] = fma(v.x, w.y, acc[2 * t + 1]);
-            acc[2 * t + 1] = fma(-v.y, w.x, acc[2 * t + 1]);
-          }
-        }
-      }
+      if (df) dots_block_df(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
+      else dots_block_f64(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
       const double r = warp_transpose_sum16(acc, lane);
       if ((lane & 1) == 0 && (lane >> 1) < 2 * nv) wsum[2 * vb + (lane >> 1)] = r;
     }
@@ -349,15 +532,15 @@ k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
   }
 }
 
-// Units of the multi-dot and new-vector passes for a problem of vs points: two per
-// SM (so the persistent grids, one or two CTAs per SM, get equal shares), at most one
+// Units of the multi-dot and new-vector passes for a problem of vs points: four per
+// SM (so the persistent grids, two or four CTAs per SM, get equal shares), at most one
 // per 256 points.
 int outer_chunks(size_t vs) {
   static const int units = [] {  // thread-safe initialisation
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
-    return 2 * std::max(1, sms);
+    return 4 * std::max(1, sms);
   }();
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)units, (vs + DOT_THREADS - 1) / DOT_THREADS));
 }
@@ -439,10 +622,10 @@ __device__ void givens_step_warp(const OuterDev<C>& O, OuterState* st, int j, do
   O.g[j + 1] = cmul(make_double2(-sn.x, sn.y), g0);
 }
 
-// Shared memory of k_vnew: the scaled column h (m+1), then the staging of the Givens
-// update: column j (m+1), sines (m), cosines (m).
+// Shared memory of k_vnew: the scaled column h (m+1) in binary64 and in double-float,
+// then the staging of the Givens update: column j (m+1), sines (m), cosines (m).
 HELM_HD constexpr size_t vnew_smem_bytes(int m) {
-  return (size_t)(m + 1) * 16 + (size_t)(m + 1) * 16 + (size_t)m * 16 + (size_t)m * 8;
+  return 2 * (size_t)(m + 1) * 16 + (size_t)(m + 1) * 16 + (size_t)m * 16 + (size_t)m * 8;
 }
 
 // start = 1: v_0 = w / beta (w holds the true residual).
@@ -451,7 +634,7 @@ HELM_HD constexpr size_t vnew_smem_bytes(int m) {
 // update and decides whether the cycle ends.  Both write the next V-cycle input b0
 // (precision C) and start level 0's first sweep from its norm.
 template <typename C>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
   extern __shared__ double2 sh[];  // m+1
   __shared__ double sm[64];
@@ -462,10 +645,13 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
     OuterState* st = O.st;
     if (st->done || (!start && st->cycle_end) || (start && !st->fresh)) continue;  // uniform
     const int j = start ? -1 : st->j;
+    const bool df = st->df;
+    float4* shf = reinterpret_cast<float4*>(sh + (st->m + 1));  // the same column as double-floats
     __syncthreads();  // the previous unit's readers of sh are done
     for (int i = tid; i <= j; i += blockDim.x) {
       const double sc = O.vscale[i];
       sh[i] = make_double2(O.hcol[i].x * sc, O.hcol[i].y * sc);
+      shf[i] = df_split(sh[i]);
     }
     __syncthreads();
     const double inv = start ? 1.0 / st->beta : 1.0;
@@ -480,6 +666,72 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
     double accu = 0.0;
     typename CT<C>::R accb = 0;
     const size_t end = unit_begin(O.vs, unit + 1, chunks);
+    if (df && !start) {
+      // u = w - sum h_i v_i in double-float: four multiply-adds per vector on the FP32
+      // pipe, eight vectors' loads in flight per step (the pass is bound by HBM: the
+      // loads in flight per SM must cover its latency)
+      const float4* w4 = reinterpret_cast<const float4*>(O.w);
+      float4* vout4 = reinterpret_cast<float4*>(vout);
+      const float bscf = (float)bsc;
+      const bool bf = sizeof(C) == 8 && bscf > 1e-30f && bscf < 1e30f;  // complex64 input formed in FP32
+      float ns = 0.0f, nc = 0.0f;
+      for (size_t idx = unit_begin(O.vs, unit, chunks) + tid; idx < end; idx += blockDim.x) {
+        const float4 w = __ldcg(w4 + idx);
+        float sr = w.x, cr = w.y, si = w.z, ci = w.w;
+        const float4* vp = reinterpret_cast<const float4*>(O.V) + idx;
+        int i = 0;
+        for (; i + 7 <= j; i += 8) {
+          float4 v[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] = __ldcs(vp + (size_t)(i + q) * O.vs);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 h = shf[i + q];
+            df_mac(sr, cr, -h.x, -h.y, v[q].x, v[q].y);
+            df_mac(sr, cr, h.z, h.w, v[q].z, v[q].w);
+            df_mac(si, ci, -h.x, -h.y, v[q].z, v[q].w);
+            df_mac(si, ci, -h.z, -h.w, v[q].x, v[q].y);
+          }
+          df_renorm(sr, cr);
+          df_renorm(si, ci);
+        }
+        if (i + 3 <= j) {
+          float4 v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = __ldcs(vp + (size_t)(i + q) * O.vs);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 h = shf[i + q];
+            df_mac(sr, cr, -h.x, -h.y, v[q].x, v[q].y);
+            df_mac(sr, cr, h.z, h.w, v[q].z, v[q].w);
+            df_mac(si, ci, -h.x, -h.y, v[q].z, v[q].w);
+            df_mac(si, ci, -h.z, -h.w, v[q].x, v[q].y);
+          }
+          i += 4;
+        }
+        for (; i <= j; ++i) {
+          const float4 v = __ldcs(vp + (size_t)i * O.vs), h = shf[i];
+          df_mac(sr, cr, -h.x, -h.y, v.x, v.y);
+          df_mac(sr, cr, h.z, h.w, v.z, v.w);
+          df_mac(si, ci, -h.x, -h.y, v.z, v.w);
+          df_mac(si, ci, -h.z, -h.w, v.x, v.y);
+        }
+        float ur, lr, ui, li;
+        df_two_sum(sr, cr, ur, lr);
+        df_two_sum(si, ci, ui, li);
+        vout4[idx] = make_float4(ur, lr, ui, li);
+        df_mac(ns, nc, ur, lr, ur, lr);
+        df_mac(ns, nc, ui, li, ui, li);
+        df_renorm(ns, nc);
+        C c;
+        if (bf) c = CT<C>::make((typename CT<C>::R)__fmul_rn(__fadd_rn(ur, lr), bscf),
+                                (typename CT<C>::R)__fmul_rn(__fadd_rn(ui, li), bscf));
+        else c = from_d<C>(make_double2(df_value(ur, lr) * bsc, df_value(ui, li) * bsc));
+        O.b0[idx] = c;
+        accb += cabs2(c);
+      }
+      accu = df_value(ns, nc);
+    } else
     for (size_t idx = unit_begin(O.vs, unit, chunks) + tid; idx < end; idx += blockDim.x) {
       // two independent accumulation chains keep the FP64 pipe busy
       double2 wa = __ldcg(O.w + idx), wb = make_double2(0, 0);
@@ -493,7 +745,8 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
       if (i <= j) wa = cfms(sh[i], __ldcs(vp + (size_t)i * O.vs), wa);
       double2 wv = cadd(wa, wb);
       wv = make_double2(wv.x * inv, wv.y * inv);
-      vout[idx] = wv;
+      if (df) reinterpret_cast<float4*>(vout)[idx] = df_split(wv);  // v_0 of a double-float basis
+      else vout[idx] = wv;
       accu += dabs2(wv);
       C c = from_d<C>(make_double2(wv.x * bsc, wv.y * bsc));
       O.b0[idx] = c;
@@ -502,7 +755,7 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
     double red[2] = {accu, (double)accb}, tot[2];
     if (grid_sum_last<2>(red, O.part, unit, chunks, &st->counter, sm, tot)) {
       const int mm = st->m;
-      double2* hc = sh + (mm + 1);
+      double2* hc = sh + 2 * (mm + 1);
       double2* sn_prev = hc + (mm + 1);
       double* cs = reinterpret_cast<double*>(sn_prev + mm);
       if (!start) {
@@ -527,8 +780,9 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
           O.vscale[jn] = hn > 0.0 ? 1.0 / hn : 0.0;
           st->iters += 1;
           st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
-          // lucky breakdown: the new direction vanishes against H z_j
-          const bool breakdown = !(hn > 1e-14 * sqrt(st->wnorm2));
+          // lucky breakdown: the new direction vanishes against H z_j (below the
+          // rounding level of the basis arithmetic: about 2^-46 j relative in double-float)
+          const bool breakdown = !(hn > (df ? 1e-12 : 1e-14) * sqrt(st->wnorm2));
           if (!isfinite(st->rel_est)) { st->done = 3; st->status = -4; st->cycle_end = 1; }
           else if (st->rel_est <= st->tol || st->iters >= st->maxit || j + 1 >= st->m || breakdown) st->cycle_end = 1;
           else st->j = jn;
@@ -562,18 +816,61 @@ __global__ void k_backsolve(const OuterDev<C>* __restrict__ ods) {
   }
 }
 
-// x += sum_i y_i z_i (FP64 accumulation of the stored preconditioned vectors).
+// x += sum_i y_i z_i over the stored preconditioned vectors: binary64 accumulation, or
+// (double-float basis with complex64 z_i) double-float accumulation on the FP32 pipe of
+// the exact complex64 z_i against y split into double-floats, x read and written in
+// binary64.
 template <typename C>
 __global__ void __launch_bounds__(256)
 k_solution(const OuterDev<C>* __restrict__ ods, int chunks) {
-  extern __shared__ double2 sh[];
+  extern __shared__ double2 sh[];  // y (m+1), then y as double-floats (m+1)
   const int prob = blockIdx.x / chunks, cta = blockIdx.x - prob * chunks;
   const OuterDev<C>& O = ods[prob];
   OuterState* st = O.st;
   if (!st->cycle_end) return;
   const int k = st->j + 1;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = O.y[i];
+  float4* shf = reinterpret_cast<float4*>(sh + (st->m + 1));
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    sh[i] = O.y[i];
+    shf[i] = df_split(sh[i]);
+  }
   __syncthreads();
+  if constexpr (sizeof(C) == 8) {
+    if (st->df) {
+      for (size_t idx = (size_t)cta * blockDim.x + threadIdx.x; idx < O.vs; idx += (size_t)chunks * blockDim.x) {
+        const double2 x0 = O.xpad[idx];
+        const float2 xr = df_split(x0.x), xi = df_split(x0.y);
+        float sr = xr.x, cr = xr.y, si = xi.x, ci = xi.y;
+        const C* zp = O.Z + idx;
+        int i = 0;
+        for (; i + 7 < k; i += 8) {
+          C z[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) z[q] = __ldcs(zp + (size_t)(i + q) * O.vs);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 y = shf[i + q];
+            df_mac1(sr, cr, y.x, y.y, z[q].x);
+            df_mac1(sr, cr, -y.z, -y.w, z[q].y);
+            df_mac1(si, ci, y.x, y.y, z[q].y);
+            df_mac1(si, ci, y.z, y.w, z[q].x);
+          }
+          df_renorm(sr, cr);
+          df_renorm(si, ci);
+        }
+        for (; i < k; ++i) {
+          const C z = __ldcs(zp + (size_t)i * O.vs);
+          const float4 y = shf[i];
+          df_mac1(sr, cr, y.x, y.y, z.x);
+          df_mac1(sr, cr, -y.z, -y.w, z.y);
+          df_mac1(si, ci, y.x, y.y, z.y);
+          df_mac1(si, ci, y.z, y.w, z.x);
+        }
+        O.xpad[idx] = make_double2(df_value(sr, cr), df_value(si, ci));
+      }
+      return;
+    }
+  }
   for (size_t idx = (size_t)cta * blockDim.x + threadIdx.x; idx < O.vs; idx += (size_t)chunks * blockDim.x) {
     double2 xv = O.xpad[idx];
     for (int i = 0; i < k; ++i) xv = cfma(sh[i], to_d(__ldcg(O.Z + (size_t)i * O.vs + idx)), xv);
@@ -624,15 +921,17 @@ void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_
 }
 template <typename C>
 void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start, cudaStream_t s) {
-  // Shared memory is padded so that at most two CTAs fit on an SM: the persistent
-  // grid of two CTAs per SM then places exactly two on every SM, and the FP64 work
-  // (the bound of this pass) is spread evenly.
+  // Shared memory is padded so that at most four CTAs fit on an SM: the persistent
+  // grid of four CTAs per SM then places exactly four on every SM, one unit each, so
+  // the work (FP64 in binary64, HBM in double-float) is spread evenly.  Four CTAs
+  // (1024 threads) keep enough loads in flight for the double-float pass: at two per SM
+  // the pass reached 2.9 TB/s, at four 5.0 TB/s (255^3, 19 basis vectors).
   thread_local size_t pad = 0;
   if (pad == 0) {
     int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    pad = (size_t)per_sm / 3 + 1024;
+    pad = (size_t)per_sm / 5 + 1024;
     cudaFuncSetAttribute(k_vnew<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(pad, 160 * 1024));
   }
   const size_t need = vnew_smem_bytes(m);
@@ -653,7 +952,28 @@ void outer_backsolve(const OuterDev<C>* od, int nprob, cudaStream_t s) {
 }
 template <typename C>
 void outer_solution(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t s) {
-  k_solution<C><<<nprob * chunks, 256, (size_t)(m + 1) * sizeof(double2), s>>>(od, chunks);
+  const size_t smem = 2 * (size_t)(m + 1) * sizeof(double2);
+  thread_local size_t configured = 0;  // per host thread; setting the attribute again is harmless
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(k_solution<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  k_solution<C><<<nprob * chunks, 256, smem, s>>>(od, chunks);
+}
+
+// Binary64 complex values stored in the basis arithmetic: as double-floats (df) or
+// copied unchanged.
+__global__ void __launch_bounds__(256) k_basis_store(const double2* __restrict__ src, double2* __restrict__ dst,
+                                                     size_t n, int df) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    if (df) reinterpret_cast<float4*>(dst)[i] = df_split(v);
+    else dst[i] = v;
+  }
+}
+void basis_store(const double2* src, double2* dst, size_t n, int df, cudaStream_t s) {
+  const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
+  k_basis_store<<<(unsigned)std::max<size_t>(blocks, 1), 256, 0, s>>>(src, dst, n, df);
 }
 
 // The outer states of a set's problems gathered into one array (one copy to the host

@@ -47,7 +47,7 @@ EXPORTS = ("helm_setup", "helm_destroy", "helm_precond_apply", "helm_apply_opera
            "helm_launch_count", "helm_profile_begin", "helm_profile_end", "helm_precond_apply_noalloc",
            "helm_batch_solve_host", "helm_serve_start", "helm_serve_submit", "helm_serve_poll", "helm_serve_wait",
            "helm_serve_stats", "helm_serve_stop", "helm_autotune", "helm_tuning_load", "helm_tuning_get",
-           "helm_set_barrier_timeout")
+           "helm_set_barrier_timeout", "helm_multidot")
 
 
 class helm_serve_opts(ctypes.Structure):
@@ -82,12 +82,23 @@ _ECS_SIDES = {"both": HELM_ECS_BOTH, "high": HELM_ECS_HIGH}
 class helm_opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("s", ctypes.c_int), ("coarsest_n", ctypes.c_int),
                 ("precond_prec", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("csl_eps", ctypes.c_double), ("smoother", ctypes.c_int)]
+                ("csl_eps", ctypes.c_double), ("smoother", ctypes.c_int), ("outer_basis", ctypes.c_int)]
+
+
+HELM_BASIS_AUTO, HELM_BASIS_F64, HELM_BASIS_DF = 0, 1, 2
+HELM_BASIS_DF_MIN_TOL = 1e-9
+_BASES = {"auto": HELM_BASIS_AUTO, "f64": HELM_BASIS_F64, "df": HELM_BASIS_DF}
+
+
+def _basis_code(basis: str) -> int:
+    if basis not in _BASES:
+        raise ValueError("basis must be 'auto', 'f64' or 'df'")
+    return _BASES[basis]
 
 
 class helm_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_res_est", ctypes.c_double),
-                ("rel_res_true", ctypes.c_double), ("status", ctypes.c_int)]
+                ("rel_res_true", ctypes.c_double), ("status", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
 _lib = None
@@ -127,6 +138,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_autotune.argtypes = [ctypes.POINTER(helm_grid), vp, dp, dp, ctypes.POINTER(helm_opts), ip,
                                   ctypes.c_char_p, ctypes.POINTER(dp), ctypes.POINTER(dp), vp]
     lib.helm_autotune.restype = ip
+    lib.helm_multidot.argtypes = [ip, vp, ip, ctypes.c_size_t, vp, ctypes.POINTER(dp), vp]
+    lib.helm_multidot.restype = ip
     lib.helm_set_barrier_timeout.argtypes = [dp]
     lib.helm_set_barrier_timeout.restype = ip
     lib.helm_tuning_load.argtypes = [ctypes.c_char_p]
@@ -247,10 +260,12 @@ class Info:
     rel_res_est: float
     rel_res_true: float
     status: int
+    basis: str = "f64"  # the Krylov basis arithmetic the solve ran in ('f64' or 'df')
 
     @staticmethod
     def of(ci: helm_info) -> "Info":
-        return Info(ci.iters, ci.restarts, ci.rel_res_est, ci.rel_res_true, ci.status)
+        return Info(ci.iters, ci.restarts, ci.rel_res_est, ci.rel_res_true, ci.status,
+                    "df" if ci.basis == HELM_BASIS_DF else "f64")
 
 
 class Handle:
@@ -260,7 +275,7 @@ class Handle:
     def __init__(self, dim: int, n: int, theta_beta: float, k: Optional[float] = None, phi=None,
                  theta_gamma: float = 0.5, ecs_frac: float = 0.125, nu1: int = 1, nu2: int = 1, s: int = 3,
                  coarsest_n: int = 3, precision: str = "c64", restart: int = 0, maxit: int = 400, stream=None,
-                 csl_eps: float = 0.0, smoother: str = "gmres", ecs_sides: str = "both"):
+                 csl_eps: float = 0.0, smoother: str = "gmres", ecs_sides: str = "both", basis: str = "auto"):
         lib = load()
         self.dim, self.n = dim, n
         self.precision = precision
@@ -270,7 +285,7 @@ class Handle:
         if smoother not in ("gmres", "poly"):
             raise ValueError("smoother must be 'gmres' or 'poly'")
         o = helm_opts(nu1, nu2, s, coarsest_n, _precision_code(precision), restart, maxit,
-                      float(csl_eps), 1 if smoother == "poly" else 0)
+                      float(csl_eps), 1 if smoother == "poly" else 0, _basis_code(basis))
         h = ctypes.c_void_p()
         phi_ptr = None if phi is None else _ptr(phi)
         self._phi = phi  # keep the caller's field alive during setup
@@ -402,6 +417,26 @@ def tuning_get(pass_name: str, dim: int, P: int, precision: str = "c64", J: int 
     if rc < 0:
         _check(rc)
     return list(v) if rc == 1 else None
+
+
+def multidot(V, w, basis: str = "df", stream=None):
+    """h_i = <V[i], w> through the outer multi-dot pass (helm_multidot): V a contiguous
+    complex128 CUDA tensor of shape (nvec, npts), w one of shape (npts,).  Returns a
+    complex128 numpy array of nvec values."""
+    import numpy as np
+    if basis not in ("f64", "df"):
+        raise ValueError("basis must be 'f64' or 'df'")
+    if V.dim() != 2 or w.dim() != 1 or V.shape[1] != w.shape[0]:
+        raise ValueError("V must be (nvec, npts) and w (npts,)")
+    nvec, npts = int(V.shape[0]), int(V.shape[1])
+    _require_vec("V", V, (nvec, npts), "c128")
+    _require_vec("w", w, (npts,), "c128")
+    _require_device("V", V)
+    _require_device("w", w)
+    out = (ctypes.c_double * (2 * max(nvec, 1)))()
+    _check(load().helm_multidot(_basis_code(basis), _ptr(V), nvec, npts, _ptr(w), out, _stream(stream)))
+    a = np.frombuffer(out, dtype=np.float64)[:2 * nvec]
+    return a[0::2] + 1j * a[1::2]
 
 
 def poly_smoother(k: float, h: float, theta_beta: float, theta_gamma: float, dim: int):
