@@ -85,12 +85,17 @@ __device__ __forceinline__ void df_mac1(float& s, float& c, float ah, float al, 
 struct DfAcc {
   float sr, cr, si, ci;
 };
-// a += k v for a double-float complex k = {re.hi, re.lo, im.hi, im.lo} and a complex64 v
+// a += k v for a double-float complex k = {re.hi, re.lo, im.hi, im.lo} and a complex64 v.
+// A real k (zero imaginary part: stencil coefficients outside the absorbing layers)
+// takes two multiply-adds instead of four; the skipped products are exact zeros, whose
+// TwoSum leaves (s, c) unchanged (up to the sign of a zero sum).
 __device__ __forceinline__ void df_cmac(DfAcc& a, float4 k, float2 v) {
   df_mac1(a.sr, a.cr, k.x, k.y, v.x);
-  df_mac1(a.sr, a.cr, -k.z, -k.w, v.y);
   df_mac1(a.si, a.ci, k.x, k.y, v.y);
-  df_mac1(a.si, a.ci, k.z, k.w, v.x);
+  if (k.z != 0.0f || k.w != 0.0f) {
+    df_mac1(a.sr, a.cr, -k.z, -k.w, v.y);
+    df_mac1(a.si, a.ci, k.z, k.w, v.x);
+  }
 }
 // (ah + al) + (bh + bl), renormalised
 __device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl) {
