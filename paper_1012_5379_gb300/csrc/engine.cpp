@@ -350,7 +350,10 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
                                                         (size_t)h->chunks * NPART),
                                        outer_part_doubles(h->chunks, m));
     TRY(dev_alloc(h.get(), &h->opart, op * sizeof(double)));
-    CUDA_TRY(cudaMemsetAsync(h->opart, 0, op * sizeof(double), st));  // multi-dot group counters
+    CUDA_TRY(cudaMemsetAsync(h->opart, 0, op * sizeof(double), st));
+    const int nct = outer_dot_counters(h->chunks);
+    TRY(dev_alloc(h.get(), &h->dcnt, (size_t)nct * sizeof(unsigned)));
+    CUDA_TRY(cudaMemsetAsync(h->dcnt, 0, (size_t)nct * sizeof(unsigned), st));
     TRY(dev_alloc(h.get(), &h->st, sizeof(OuterState)));
     CUDA_TRY(cudaMemsetAsync(h->w, 0, h->vs * sizeof(double2), st));
     CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(OuterState), st));
@@ -426,6 +429,7 @@ static OuterDev<C> make_outerdev(const Handle& h) {
   o.hcol = h.hcol;
   o.vscale = h.vscale;
   o.part = h.opart;
+  o.gcnt = h.dcnt;
   o.st = h.st;
   o.sc0 = (SweepScalarsT<typename RealOf<C>::T>*)h.lev[0].sc;
   return o;
@@ -976,8 +980,9 @@ int multidot(int basis, const double2* V, int nvec, size_t npts, const double2* 
   const size_t bst = al(sizeof(OuterState)), bpart = al(outer_part_doubles(chunks, m) * sizeof(double));
   const size_t bH = al((size_t)(m + 1) * m * sizeof(double2)), bcol = al((size_t)(m + 1) * sizeof(double2));
   const size_t bsc = al((size_t)(m + 1) * sizeof(double)), bod = al(sizeof(OuterDev<float2>));
+  const size_t bct = al((size_t)outer_dot_counters(chunks) * sizeof(unsigned));
   char* base = nullptr;
-  if (cudaMalloc(&base, bV + bw + bst + bpart + bH + bcol + bsc + bod) != cudaSuccess) {
+  if (cudaMalloc(&base, bV + bw + bst + bpart + bH + bcol + bsc + bod + bct) != cudaSuccess) {
     cudaGetLastError();
     set_error("multidot: cannot allocate the workspace");
     return HELM_ENOMEM;
@@ -996,10 +1001,12 @@ int multidot(int basis, const double2* V, int nvec, size_t npts, const double2* 
   double2* hcol = (double2*)take(bcol);
   double* vscale = (double*)take(bsc);
   OuterDev<float2>* od = (OuterDev<float2>*)take(bod);
+  unsigned* gcnt = (unsigned*)take(bct);
   const int df = basis == HELM_BASIS_DF;
   basis_store(V, Vb, (size_t)nvec * npts, df, st);
   basis_store(w, wb, npts, df, st);
   CUDA_TRY(cudaMemsetAsync(part, 0, bpart, st));
+  CUDA_TRY(cudaMemsetAsync(gcnt, 0, bct, st));
   OuterState s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.j = nvec - 1;
@@ -1015,6 +1022,7 @@ int multidot(int basis, const double2* V, int nvec, size_t npts, const double2* 
   o.hcol = hcol;
   o.vscale = vscale;
   o.part = part;
+  o.gcnt = gcnt;
   o.st = dst;
   // host staging lives on this frame: the stream is synchronised before it returns
   CUDA_TRY(cudaMemcpyAsync(dst, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
@@ -1448,6 +1456,7 @@ size_t estimate_handle_bytes(int dim, int n, int prec, int s, int restart, int m
   const size_t m = restart > 0 ? std::min(restart, maxit) : maxit;
   bytes += 3 * vs * sizeof(double2) + (m + 1) * vs * sizeof(double2) + m * vs * eb + (m + 1) * (m + 8) * 16;
   bytes += outer_part_doubles(outer_chunks(vs), (int)m) * sizeof(double);
+  bytes += (size_t)outer_dot_counters(outer_chunks(vs)) * sizeof(unsigned);
   return bytes;
 }
 

@@ -85,6 +85,7 @@ struct Handle {
   double2* hcol = nullptr;
   double* vscale = nullptr;
   double* opart = nullptr;
+  unsigned* dcnt = nullptr;   // the multi-dot's group counters
   OuterState* st = nullptr;
   int chunks = 1;
   int ntiles0 = 1;

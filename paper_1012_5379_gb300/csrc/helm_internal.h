@@ -141,6 +141,7 @@ struct OuterDev {
   double2* hcol;          // m+1 reduced dots of the current column
   double* vscale;         // m+1: v_i = vscale[i] * V[i] (V stored unnormalised)
   double* part;           // partial sums
+  unsigned* gcnt;         // the multi-dot's group counters (zero between calls)
   OuterState* st;
   SweepScalarsT<typename RealOf<C>::T>* sc0;  // level-0 sweep state (set by the kernel that writes b0)
 };
@@ -311,6 +312,7 @@ int vcycle_take_error();
 int vcycle_take_error_c128();
 int outer_chunks(size_t vs);
 size_t outer_part_doubles(int chunks, int m);
+int outer_dot_counters(int chunks);
 void basis_store(const double2* src, double2* dst, size_t n, int df, cudaStream_t st);
 template <typename C>
 void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t st);

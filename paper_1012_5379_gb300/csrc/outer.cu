@@ -488,7 +488,7 @@ k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
     const size_t ubeg = unit_begin(npts, unit, chunks), uend = unit_begin(npts, unit + 1, chunks);
     double* upart = O.part;                                   // [chunks][M1][2]
     double* gpart = O.part + (size_t)chunks * M1 * 2;         // [ngroups][M1][2]
-    unsigned* gcnt = reinterpret_cast<unsigned*>(gpart + (size_t)ngroups * M1 * 2);  // [ngroups]
+    unsigned* gcnt = O.gcnt;  // [ngroups], zero between calls (each group's last unit resets its own)
     double* wsum = sred + (size_t)warp * 2 * M1;
     __syncthreads();  // the previous unit's readers of sred are done
     const bool df = st->df;
@@ -559,11 +559,17 @@ int outer_chunks(size_t vs) {
 }
 
 // Doubles of the outer partial-sum buffer the passes need for `chunks` units and
-// restart length m (unit and group partials of the multi-dot, its group counters).
+// restart length m (unit and group partials of the multi-dot).  The buffer is scratch
+// shared by the outer passes, each overwriting the others' slots.
 size_t outer_part_doubles(int chunks, int m) {
   const int ng = dot_groups(chunks);
-  return (size_t)(chunks + ng) * (m + 1) * 2 + (size_t)ng + 1;
+  return (size_t)(chunks + ng) * (m + 1) * 2;
 }
+// Group counters of the multi-dot for `chunks` units.  They live in a buffer of their
+// own: a counter must read zero at the start of every call, and the partial-sum buffer
+// is overwritten by the other outer passes' partials in between (which, for short
+// restart lengths, once corrupted the counters and with them the inner products).
+int outer_dot_counters(int chunks) { return dot_groups(chunks); }
 
 // ------------------------------------------------------------------ new Arnoldi vector
 // Givens update of column j once h_{j+1,j} is known (last block of k_vnew, warp 0).
