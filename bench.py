@@ -7,7 +7,8 @@ relative residual 1e-6 (one V-cycle per outer iteration).  A step is one pass of
 whole hot path over one batch of synthetic input: the full FGMRES(40) solve of the 3D
 255^3 heterogeneous problem (unit cube, k(x) = 80 (1 + 0.3 g(x)) with 8 seeded Gaussian
 bumps, point source, theta_beta 0.4, ECS layers 1/8 at 0.5 rad; complex64 V(1,1)
-GMRES(3) V-cycle, FP64 outer), the largest single-GPU workload.  Extra keys of the same
+GMRES(3) V-cycle, outer FGMRES with the library's default arithmetic: double-float Krylov
+basis, binary64 least squares and true residual), the largest single-GPU workload.  Extra keys of the same
 line: the 2D 1023^2 theta_beta sweep (four solves batched), the 64-problem batch in
 solves/s, and a short Poisson serving run with p50/p99 latency.
 
@@ -378,7 +379,8 @@ def sweep_2d(args, dev):
     return {"value": float(N * N) * sum(iters) * 3 / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / 3,
             "iters_per_beta": dict(zip([str(t) for t in BETAS], iters)), "steps": 3,
             "workload": "2D 1023^2, k=160, random source (seed 1001), theta_beta {0.1,0.2,0.3,0.5} batched, "
-                        "complex64 V(1,1)-GMRES(3) / FP64 FGMRES to 1e-6; L2 flushed between steps"}
+                        "complex64 V(1,1)-GMRES(3) / FGMRES to 1e-6 (double-float basis, binary64 least squares and "
+                        "residual); L2 flushed between steps"}
 
 
 def batch_extra(args):
@@ -664,7 +666,9 @@ def run_gauss(args):
                 del h
     out = {"mode": "gauss", "config": {"workload": "Gaussian model (Sec. 5, Benchmark 3): (0,50)^2, phi = nu (e^-x^2 + "
                                                    "e^-y^2) + k^2, Dirichlet S/W, ECS layer nint/4 N/E at pi/6, "
-                                                   "theta_beta 10.3132 deg, FGMRES to 1e-7, c64 preconditioner"},
+                                                   "theta_beta 10.3132 deg, FGMRES to 1e-7, the library's automatic "
+                                                   "preconditioner precision and basis (complex128 and binary64 on "
+                                                   "the 64^2 column's 79^2 grid, complex64 and double-float above)"},
            "rows": rows}
     print(json.dumps(out), flush=True)
 
@@ -756,7 +760,8 @@ def run_batch(args):
             "vcycle_mpts_per_s": work / t / 1e6, "gpu_launches": int(launches), "clocks": clocks,
             "config": {"workload": f"{len(works)} independent 2D problems, sizes {sizes}, kh ~ U[0.1,0.3], "
                                    "theta_beta 0.3, unit-variance complex normal sources (seed 1003), "
-                                   "FGMRES(40) to 1e-6, complex64 V(1,1)-GMRES(3) / FP64 outer",
+                                   "FGMRES(40) to 1e-6, complex64 V(1,1)-GMRES(3) / default outer arithmetic "
+                                   "(double-float basis above 16384 unknowns, binary64 below)",
                        "l2": "flushed between steps"},
             "iters_total": sum(i.iters for i in infos), "max_rel_res_true": max(i.rel_res_true for i in infos),
             "sequential": seq,
@@ -865,7 +870,7 @@ def run_serve(args):
                        for k in stats},
             "config": {"workload": f"Poisson arrivals, mean {args.rate}/s, {len(stream)} requests, shapes uniform "
                                    f"over {shapes}, kh ~ U[0.1,0.3], theta_beta 0.3, FGMRES(40) to 1e-6, "
-                                   "complex64 V(1,1)-GMRES(3) / FP64 outer",
+                                   "complex64 V(1,1)-GMRES(3) / default outer arithmetic",
                        "budget_bytes": budget,
                        "sources": "two seeded unit-variance complex normal sources per shape (pinned), "
                                   "request i uses source i mod 2; solutions land in pinned buffers"},
