@@ -366,12 +366,14 @@ int helm_autotune(const helm_grid* grid, const float* phi, double k, double thet
  * or malformed (the current table is then kept). */
 int helm_tuning_load(const char* path);
 
-/* The tuned choice of pass "arnoldi", "restrict" or "prolong" on a level of dimension
- * dim and pitch P in precision prec (HELM_C64 / HELM_C128) for Arnoldi step J (0 for
- * the other passes): writes its 4 integers into v and returns 1, or returns 0 when the
- * table has none (the built-in default applies).  v: 2D passes {tiles per CTA}; 3D
- * Arnoldi {TMA-fed pass on, plane slots, z pieces per column (0: one share per resident
- * CTA), points per thread in y}.  Host only. */
+/* The tuned choice of pass "arnoldi", "restrict", "prolong", "persist" or "zplanes" on a
+ * level of dimension dim and pitch P in precision prec (HELM_C64 / HELM_C128) for Arnoldi
+ * step J (0 for the other passes): writes its 4 integers into v and returns 1, or
+ * returns 0 when the table has none (the built-in default applies).  v: 2D passes
+ * {tiles per CTA}; 3D Arnoldi {TMA-fed pass on, plane slots, z pieces per column (0: one
+ * share per resident CTA), points per thread in y}; "persist" {persistent segment on};
+ * "zplanes" (3D levels without the TMA-fed passes) {planes each CTA marches: 2, 4, 8 or
+ * 16}.  Host only. */
 int helm_tuning_get(const char* pass, int dim, int P, int prec, int J, int* v);
 
 /* Spin limit of the grid-wide barrier between the passes of the persistent V-cycle

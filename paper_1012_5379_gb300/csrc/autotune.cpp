@@ -7,6 +7,8 @@
 // keeps run-to-run noise from deciding.  Choices:
 //   2D levels: tiles per CTA of the Arnoldi passes (each step J), of the residual +
 //     restriction pass and of the prolongation pass (1, 2, 4, 8);
+//   3D levels without the TMA-fed passes (pitch below 128, or complex128): the planes
+//     each CTA of the plain passes marches (2, 4, 8, 16);
 //   3D complex64 levels of pitch 128..1024: the TMA-fed Arnoldi pass of each step J
 //     off, or on with 2..8 plane slots in flight, 2 or 4 points per thread in y, and
 //     the level shared as one piece per resident CTA or as 1, 2 or 4 z pieces per
@@ -120,6 +122,13 @@ int autotune(const helm_grid* grid, const float* phi, double k, double theta_bet
   for (const HostLevel& L : h->lev) {
     if (L.n <= thr) continue;
     const int P = L.P;
+    if (dim == 3 && !(eb == 8 && L.tm && P >= 128 && P <= 1024 && P % 32 == 0)) {
+      // plain 3D passes: planes per CTA march
+      Knob kz{TP_ZPLANES, 3, P, eb, 0, {}};
+      for (int z : {2, 4, 8, 16})
+        if (z <= P) kz.cands.push_back(tc(z));
+      knobs.push_back(kz);
+    }
     if (dim == 2) {
       for (int J = 1; J <= h->s; ++J) knobs.push_back({TP_ARNOLDI, 2, P, eb, J, {tc(1), tc(2), tc(4), tc(8)}});
       knobs.push_back({TP_RESTRICT, 2, P, eb, 0, {tc(1), tc(2), tc(4), tc(8)}});

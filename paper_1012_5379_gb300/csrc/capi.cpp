@@ -246,8 +246,9 @@ int helm_tuning_get(const char* pass, int dim, int P, int prec, int J, int* v) {
     if (!pass || !v) { helm::set_error("NULL argument"); return HELM_EINVAL; }
     const std::string p(pass);
     const int tp = p == "arnoldi" ? helm::TP_ARNOLDI : p == "restrict" ? helm::TP_RESTRICT
-                 : p == "prolong" ? helm::TP_PROLONG : -1;
-    if (tp < 0) { helm::set_error("pass must be arnoldi, restrict or prolong"); return HELM_EINVAL; }
+                 : p == "prolong" ? helm::TP_PROLONG : p == "persist" ? helm::TP_PERSIST
+                 : p == "zplanes" ? helm::TP_ZPLANES : -1;
+    if (tp < 0) { helm::set_error("pass must be arnoldi, restrict, prolong, persist or zplanes"); return HELM_EINVAL; }
     if (prec != HELM_C64 && prec != HELM_C128) { helm::set_error("prec must be HELM_C64 or HELM_C128"); return HELM_EINVAL; }
     helm::TuneChoice c;
     if (!helm::tune_get(tp, dim, P, prec == HELM_C128 ? 16 : 8, J, &c)) return 0;

@@ -264,7 +264,11 @@ int setup_handle(const helm_grid* grid, const float* phi, double k, double theta
     // partial slots: one per tile of the marching passes, per flat-pass CTA, and per
     // share of the 3D TMA-fed pass
     size_t nparts = std::max<size_t>(std::max(L.ntiles, L.nflat), 1);
-    if (h->dim == 3) nparts = std::max<size_t>(nparts, TMA3_MAX_UNITS);
+    if (h->dim == 3) {
+      TileCfg finest;  // the most tiles a tuned plane count (2) gives
+      finest.rows = 2;
+      nparts = std::max<size_t>(nparts, std::max<size_t>(TMA3_MAX_UNITS, tiles_per_problem(3, L.P, finest)));
+    }
     TRY(dev_alloc(h.get(), &L.part, nparts * NPART * sizeof(double)));
     // TMA maps of the raw vectors the complex64 Arnoldi passes stream
     // (3D: two sets, for column tiles of 16 and of 32 rows)
@@ -576,10 +580,10 @@ static int build_group(Handle* const* hs, int count, cudaStream_t st, Group<C>* 
       D.n = L.n;
       D.cnt += 1;
       D.tma = D.tma && L.tm != nullptr;
-      D.ntiles = L.ntiles;
       D.nflat = L.nflat;
-      D.cfg.rows = zchunk(L.P);
+      D.cfg.rows = g->dim == 3 ? tuned_zchunk(L.P, (int)sizeof(C)) : zchunk(L.P);
       D.cfg.P = L.P;
+      D.ntiles = g->dim == 3 ? tiles_per_problem(3, L.P, D.cfg) : L.ntiles;
     }
   }
   std::vector<LevelDev<C>> coarse;

@@ -263,7 +263,7 @@ bool encode_level_tmaps3(int P, int box_rows, const void* const* vectors, int co
 //   arnoldi / restrict / prolong, 2D: {tiles per CTA}
 //   persist, 2D/3D: {grid-wide level run inside the persistent segments (1) or by its
 //                    own launches (0)}
-enum TunePass { TP_ARNOLDI = 0, TP_RESTRICT = 1, TP_PROLONG = 2, TP_PERSIST = 3 };
+enum TunePass { TP_ARNOLDI = 0, TP_RESTRICT = 1, TP_PROLONG = 2, TP_PERSIST = 3, TP_ZPLANES = 4 };
 constexpr int TUNE_NV = 4;
 struct TuneChoice {
   int v[TUNE_NV];
@@ -280,6 +280,9 @@ int tune_entries();
 int tune_write(const char* path, const std::string& run_record, std::string* err);
 // 2D tiles per CTA of a pass: the tuned value, else the heuristic's.
 int tuned_tpc(int pass, int P, int prec_bytes, int J, int heuristic);
+// Planes each CTA of the plain 3D passes (Arnoldi, restriction, prolongation) marches on
+// a level of pitch P: the table's choice (2, 4, 8 or 16), else zchunk(P).
+int tuned_zchunk(int P, int prec_bytes);
 // Whether a grid-wide level of pitch P runs inside the persistent segments: only where
 // the tuning table switches it on, for 2D levels up to 511^2 and 3D levels up to 63^3.
 bool persist_level(int dim, int P, int prec_bytes);

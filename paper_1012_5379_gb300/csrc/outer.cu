@@ -122,34 +122,46 @@ __device__ __forceinline__ float4 hpoint_df(float4 dxy, float4 dz, float phih, f
   return make_float4(hr, lr, hi, li);
 }
 
-// 2D rows ybeg..yend-1 of one warp column; returns this thread's share of ||w||^2.
+// 2D rows ybeg..yend-1 of one warp column; returns this thread's share of ||w||^2.  The
+// next row's value, phi and the edge lanes' x neighbours are loaded one row ahead, as in
+// the 3D pass.
 __device__ double hstencil2_df(const OuterDev<float2>& O, const float2* u1, float2* zarch, int x, int ybeg,
                                int yend, int lane) {
   const int n = O.n, P = O.P;
   const float4 ax = ldh_df(O.cdf, 0, x, n), dx = ldh_df(O.cdf, 1, x, n), cxr = ldh_df(O.cdf, 2, x, n);
   const float2 pc = df_split(O.phic);
   const float4 zero = make_float4(0, 0, 0, 0);
+  const bool edge = lane == 0 || lane == 31;
+  const int xe = lane == 0 ? x - 1 : x + 1;  // the edge lane's neighbour outside the warp
+  auto ldphi = [&](int y) -> float {
+    return O.phi ? (x < n && y < n ? __ldg(O.phi + pidx(x, y, 0, P)) : 0.0f) : pc.x;
+  };
   float ns = 0.0f, nc = 0.0f;
   if (ybeg < P) {
     float2 vm = ldz(u1, x, ybeg - 1, 0, n, P), v0 = ldz(u1, x, ybeg, 0, n, P);
+    float ph0 = ldphi(ybeg);
+    float2 e0 = edge ? ldz(u1, xe, ybeg, 0, n, P) : make_float2(0, 0);
     for (int y = ybeg; y < yend; ++y) {
       const float2 vp = ldz(u1, x, y + 1, 0, n, P);
+      const float ph1 = ldphi(y + 1);
+      const float2 e1 = edge ? ldz(u1, xe, y + 1, 0, n, P) : make_float2(0, 0);
       float2 vl = shfl_f2(v0, 1, true), vr = shfl_f2(v0, 1, false);
-      if (lane == 0) vl = ldz(u1, x - 1, y, 0, n, P);
-      if (lane == 31) vr = ldz(u1, x + 1, y, 0, n, P);
+      if (lane == 0) vl = e0;
+      if (lane == 31) vr = e0;
       if (x < P) {
         float4 o = zero;
         if (x < n && y < n) {
           const float4 ay = ldh_df(O.cdf, 0, y, n), dy = ldh_df(O.cdf, 1, y, n), cyr = ldh_df(O.cdf, 2, y, n);
-          const float ph = O.phi ? __ldg(O.phi + pidx(x, y, 0, P)) : pc.x, pl = O.phi ? 0.0f : pc.y;
-          o = hpoint_df(df_cadd(dx, dy), zero, ph, pl, ax, cxr, ay, cyr, zero, zero, v0, vl, vr, vm, vp, vm, vp,
-                        false, ns, nc);
+          o = hpoint_df(df_cadd(dx, dy), zero, ph0, O.phi ? 0.0f : pc.y, ax, cxr, ay, cyr, zero, zero, v0, vl, vr,
+                        vm, vp, vm, vp, false, ns, nc);
         }
         reinterpret_cast<float4*>(O.w)[pidx(x, y, 0, P)] = o;
-        zarch[pidx(x, y, 0, P)] = u1[pidx(x, y, 0, P)];
+        zarch[pidx(x, y, 0, P)] = v0;
       }
       vm = v0;
       v0 = vp;
+      ph0 = ph1;
+      e0 = e1;
     }
   }
   return df_value(ns, nc);

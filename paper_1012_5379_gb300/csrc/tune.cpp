@@ -51,6 +51,7 @@ const char* pass_name(int pass) {
     case TP_RESTRICT: return "restrict";
     case TP_PROLONG: return "prolong";
     case TP_PERSIST: return "persist";
+    case TP_ZPLANES: return "zplanes";
     default: return "?";
   }
 }
@@ -59,6 +60,7 @@ int pass_of(const std::string& s) {
   if (s == "restrict") return TP_RESTRICT;
   if (s == "prolong") return TP_PROLONG;
   if (s == "persist") return TP_PERSIST;
+  if (s == "zplanes") return TP_ZPLANES;
   return -1;
 }
 
@@ -349,6 +351,15 @@ unsigned long long barrier_limit_ns() { return g_barrier_ns.load(); }
 void set_barrier_limit_ns(unsigned long long ns) {
   g_barrier_ns.store(ns);
   bump_launch_generation();  // captured graphs carry the limit as an argument
+}
+
+int tuned_zchunk(int P, int prec_bytes) {
+  TuneChoice c;
+  if (tune_get(TP_ZPLANES, 3, P, prec_bytes, 0, &c)) {
+    const int z = c.v[0];
+    if ((z == 2 || z == 4 || z == 8 || z == 16) && z <= P) return z;
+  }
+  return zchunk(P);
 }
 
 int tuned_tpc(int pass, int P, int prec_bytes, int J, int heuristic) {

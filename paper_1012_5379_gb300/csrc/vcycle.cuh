@@ -604,6 +604,12 @@ __device__ void coarse_cycle(Team& team, const LevelDev<C>* Ls, int nlev, const 
           int sx = src % n, sy = (src / n) % n, sz = dim == 3 ? src / (n * n) : 0;
           yv[i] = to_d(L.b[pidx(sx, sy, sz, P)]);
         }
+        // reciprocals of U's diagonal, all at once (a complex FP64 division is a long
+        // dependent chain on this part's 1/64-rate FP64 pipe; the backward sweep then
+        // multiplies instead of dividing m times in series)
+        double2* const inv = staged && m * m + m <= lu_cap ? lu_sm + (size_t)m * m : nullptr;
+        if (inv)
+          for (int i = tid; i < m; i += 32) inv[i] = ddiv(make_double2(1.0, 0.0), LUf[(size_t)i * m + i]);
         __syncwarp();
         for (int k = 0; k < m; ++k) {  // forward, unit lower
           const double2 yk = yv[k];
@@ -612,7 +618,7 @@ __device__ void coarse_cycle(Team& team, const LevelDev<C>* Ls, int nlev, const 
           __syncwarp();
         }
         for (int k = m - 1; k >= 0; --k) {  // backward
-          if (tid == 0) yv[k] = ddiv(yv[k], LUf[(size_t)k * m + k]);
+          if (tid == 0) yv[k] = inv ? cmul(yv[k], inv[k]) : ddiv(yv[k], LUf[(size_t)k * m + k]);
           __syncwarp();
           const double2 yk = yv[k];
           for (int i = tid; i < k; i += 32) yv[i] = csub(yv[i], cmul(LUf[(size_t)i * m + k], yk));

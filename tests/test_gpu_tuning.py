@@ -1,8 +1,8 @@
 """Tuned launch choices on the GPU.
 
 - Every launch variant of the 3D TMA-fed Arnoldi and residual passes the autotuner can
-  pick (points per thread in y, plane slots in flight, shares of the level), and the
-  plain passes, give a V-cycle that matches the FP64 oracle's point by point (tests/parity_check.py, c64 5e-5) on a
+  pick (points per thread in y, plane slots in flight, shares of the level), the plain
+  passes and their planes per CTA, give a V-cycle that matches the FP64 oracle's point by point (tests/parity_check.py, c64 5e-5) on a
   127^3 heterogeneous problem, whose finest level takes that pass, and 2D tiles-per-CTA
   choices on 255^2 do too.
 - helm_autotune on a small problem returns its default and tuned V-cycle times, writes a
@@ -83,6 +83,20 @@ def test_tma3_off_matches_oracle(helm, table, cube127):
     zt = torch.empty_like(rt)
     h.precond_apply(rt, zt)
     assert_parity(zt, want, ("vcycle", "c64"), "plain 3D pass")
+
+
+@pytest.mark.parametrize("zc", [2, 8, 16])
+def test_3d_plane_counts_match_oracle(helm, table, cube127, zc):
+    """The planes per CTA of the plain 3D passes (levels of pitch 64, 32 and 16 of the
+    127^3 problem) the autotuner can pick: the V-cycle matches the oracle point by point."""
+    w, r, want = cube127
+    table([{"pass": "zplanes", "dim": 3, "P": P, "prec": 8, "J": 0, "v": [zc, 0, 0, 0]} for P in (64, 32, 16)])
+    assert helm.tuning_get("zplanes", 3, 64, "c64", 0) == [zc, 0, 0, 0]
+    h = helm.Handle(3, 127, w.theta_beta, phi=torch.from_numpy(w.phi).cuda(), precision="c64", maxit=1)
+    rt = torch.from_numpy(r).cuda().to(torch.complex64)
+    zt = torch.empty_like(rt)
+    h.precond_apply(rt, zt)
+    assert_parity(zt, want, ("vcycle", "c64"), f"zplanes={zc}")
 
 
 @pytest.mark.parametrize("tpc", [1, 8])
