@@ -297,19 +297,26 @@ __device__ __forceinline__ void arnoldi_t3_body(const LevelDev<C>* __restrict__ 
   const bool halo = tid < HALO3;
   int hx = 0, hy = 0;
   if (halo) halo_coord<T3X, T3Y>(tid, hx, hy);
-  auto load_plane = [&](int z, C* raw) {
-    C v = czero<C>();
+  // A plane's raw values are fetched into registers one iteration before they are
+  // combined into v_J and stored to the ring, so the loads of plane z + 2 are in flight
+  // during iteration z's barrier and arithmetic (these levels are small and L2-resident:
+  // the pass is bound by the latency of its dependent plane steps, not by bandwidth).
+  auto fetch = [&](int z, C* raw, C* hraw) {
 #pragma unroll
     for (int k = 0; k < J; ++k) {
-      const C r = ldc<C, NC>(Rk[k], x, y, z, n, P);
-      if (raw) raw[k] = r;
-      v = cfma(cf[k], r, v);
+      raw[k] = ldc<C, NC>(Rk[k], x, y, z, n, P);
+      hraw[k] = halo ? ldc<C, NC>(Rk[k], x0 + hx, y0 + hy, z, n, P) : czero<C>();
     }
+  };
+  auto store_plane = [&](int z, const C* raw, const C* hraw) {
+    C v = czero<C>();
+#pragma unroll
+    for (int k = 0; k < J; ++k) v = cfma(cf[k], raw[k], v);
     vb[z & 3][ly + 1][lx + 1] = v;
     if (halo) {
       C w = czero<C>();
 #pragma unroll
-      for (int k = 0; k < J; ++k) w = cfma(cf[k], ldc<C, NC>(Rk[k], x0 + hx, y0 + hy, z, n, P), w);
+      for (int k = 0; k < J; ++k) w = cfma(cf[k], hraw[k], w);
       vb[z & 3][hy + 1][hx + 1] = w;
     }
   };
@@ -319,11 +326,15 @@ __device__ __forceinline__ void arnoldi_t3_body(const LevelDev<C>* __restrict__ 
   for (int k = 0; k < J; ++k) acc[k] = czero<C>();
   R accn = 0;
   if (zbeg < P) {
-    C rawc[J], rawn[J];
-    load_plane(zbeg - 1, nullptr);
-    load_plane(zbeg, rawc);
+    C rawc[J], rawn[J], rawnn[J], hc[J], hn[J], hnn[J];
+    fetch(zbeg - 1, rawc, hc);
+    store_plane(zbeg - 1, rawc, hc);
+    fetch(zbeg, rawc, hc);
+    store_plane(zbeg, rawc, hc);
+    fetch(zbeg + 1, rawn, hn);
     for (int z = zbeg; z < zend; ++z) {
-      load_plane(z + 1, rawn);
+      store_plane(z + 1, rawn, hn);
+      fetch(z + 2, rawnn, hnn);  // z + 2 <= P: in bounds, zero past n
       __syncthreads();
       const int s0 = z & 3;
       C p = czero<C>();
@@ -340,7 +351,11 @@ __device__ __forceinline__ void arnoldi_t3_body(const LevelDev<C>* __restrict__ 
       }
       if (store_p && x < P && y < P) L.p[J - 1][pidx(x, y, z, P)] = p;
 #pragma unroll
-      for (int k = 0; k < J; ++k) rawc[k] = rawn[k];
+      for (int k = 0; k < J; ++k) {
+        rawc[k] = rawn[k];
+        rawn[k] = rawnn[k];
+        hn[k] = hnn[k];
+      }
     }
   }
   R red[2 * J + 1];
