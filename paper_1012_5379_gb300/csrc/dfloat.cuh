@@ -97,6 +97,19 @@ __device__ __forceinline__ void df_cmac(DfAcc& a, float4 k, float2 v) {
     df_mac1(a.si, a.ci, k.z, k.w, v.x);
   }
 }
+// a = k v (the first term of a sum: the TwoSum against a zero accumulator is skipped)
+__device__ __forceinline__ DfAcc df_cmul_first(float4 k, float2 v) {
+  DfAcc a;
+  a.sr = __fmul_rn(k.x, v.x);
+  a.cr = fmaf(k.y, v.x, fmaf(k.x, v.x, -a.sr));
+  a.si = __fmul_rn(k.x, v.y);
+  a.ci = fmaf(k.y, v.y, fmaf(k.x, v.y, -a.si));
+  if (k.z != 0.0f || k.w != 0.0f) {
+    df_mac1(a.sr, a.cr, -k.z, -k.w, v.y);
+    df_mac1(a.si, a.ci, k.z, k.w, v.x);
+  }
+  return a;
+}
 // (ah + al) + (bh + bl), renormalised
 __device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl) {
   float s, r;

@@ -103,8 +103,7 @@ __device__ __forceinline__ float4 hpoint_df(float4 dxy, float4 dz, float phih, f
   const float2 dre = df_add(dg.x, dg.y, -phih, -phil);
   dg.x = dre.x;
   dg.y = dre.y;
-  DfAcc a{0.0f, 0.0f, 0.0f, 0.0f};
-  df_cmac(a, dg, v0);
+  DfAcc a = df_cmul_first(dg, v0);
   df_cmac(a, ax, vl);
   df_cmac(a, cxr, vr);
   df_cmac(a, ay, vs);
@@ -382,12 +381,12 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
 // grid nor on which other problems share the launch.  A unit sweeps its points once
 // per block of DOT_VB vectors with the DOT_VB complex sums in registers, so the FP64
 // pipe runs 4 DFMA per point and vector; the warp combines its 2 DOT_VB partial sums
-// with a transposed butterfly (about one add per value instead of five), the CTA
+// (padded to 32) with a transposed butterfly (about one add per value instead of five), the CTA
 // combines warps in fixed order.  Units are combined in two levels, so that no
 // single SM adds up every unit: the last unit of each group of DOT_GROUP units sums
 // the group, the last group sums the groups.
 constexpr int DOT_THREADS = 256;
-constexpr int DOT_VB = 8;      // vectors per register block
+constexpr int DOT_VB = 10;     // vectors per register block (w is re-read once per block)
 constexpr int DOT_GROUP = 16;  // units per first-level group
 
 HELM_HD inline int dot_groups(int chunks) { return (chunks + DOT_GROUP - 1) / DOT_GROUP; }
@@ -397,37 +396,21 @@ __device__ __forceinline__ size_t unit_begin(size_t n, int u, int chunks) {
   return (n * (size_t)u) / (size_t)chunks;
 }
 
-// Sum 16 per-lane values over the warp; lane L returns the total of value L >> 1
-// (fixed order: butterflies at offsets 16, 8, 4, 2, 1, halving the values kept).
-__device__ __forceinline__ double warp_transpose_sum16(double (&v)[16], int lane) {
+// Sum 32 per-lane values over the warp; lane L returns the total of value L (fixed
+// order: butterflies at offsets 16, 8, 4, 2, 1, halving the values kept, so about one
+// shuffle and one add per value instead of five).
+__device__ __forceinline__ double warp_transpose_sum32(double (&v)[32], int lane) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const bool hi = lane & 16;
-    const double send = hi ? v[k] : v[k + 8];
-    const double keep = hi ? v[k + 8] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
+  for (int c = 16; c >= 1; c >>= 1) {
+    const bool hi = lane & c;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const bool hi = lane & 8;
-    const double send = hi ? v[k] : v[k + 4];
-    const double keep = hi ? v[k + 4] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    for (int k = 0; k < c; ++k) {
+      const double send = hi ? v[k] : v[k + c];
+      const double keep = hi ? v[k + c] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, c);
+    }
   }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const bool hi = lane & 4;
-    const double send = hi ? v[k] : v[k + 2];
-    const double keep = hi ? v[k + 2] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  {
-    const bool hi = lane & 2;
-    const double send = hi ? v[0] : v[1];
-    const double keep = hi ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
 }
 
 // One thread's sums over its points of the DOT_VB vectors vb .. vb + nv - 1: acc[2 t]
@@ -509,8 +492,11 @@ k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
       double acc[2 * DOT_VB];
       if (df) dots_block_df(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
       else dots_block_f64(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
-      const double r = warp_transpose_sum16(acc, lane);
-      if ((lane & 1) == 0 && (lane >> 1) < 2 * nv) wsum[2 * vb + (lane >> 1)] = r;
+      double vals[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) vals[k] = k < 2 * DOT_VB ? acc[k < 2 * DOT_VB ? k : 0] : 0.0;
+      const double r = warp_transpose_sum32(vals, lane);
+      if (lane < 2 * nv) wsum[2 * vb + lane] = r;
     }
     __syncthreads();
     for (int k = tid; k < 2 * (j + 1); k += DOT_THREADS) {
