@@ -1034,7 +1034,7 @@ int multidot(int basis, const double2* V, int nvec, size_t npts, const double2* 
   CUDA_TRY(cudaMemcpyAsync(od, &o, sizeof(o), cudaMemcpyHostToDevice, st));
   {
     Launch L("out.dots", st, 0, 0);
-    outer_dots<float2>(od, 1, chunks, m, st);
+    outer_dots<float2>(od, 1, chunks, m, npts, st);
   }
   CUDA_TRY(cudaMemcpyAsync(h_host, hcol, (size_t)nvec * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -1072,7 +1072,7 @@ static int run_iteration(Group<C>& g, cudaStream_t st) {
   for (const auto& o : g.outer) {
     const double pts1 = sub_points<C>(o, g.dim) / o.cnt;
     Launch L("out.dots", st, pts1 * 16.0 * (o.sum_j1 + o.cnt), pts1 * 8.0 * o.sum_j1);
-    outer_dots<C>(o.d, o.cnt, o.chunks, o.m, st);
+    outer_dots<C>(o.d, o.cnt, o.chunks, o.m, (size_t)(sub_points<C>(o, g.dim) / o.cnt), st);
   }
   for (const auto& o : g.outer) {
     const double pts1 = sub_points<C>(o, g.dim) / o.cnt;

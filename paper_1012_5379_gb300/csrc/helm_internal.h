@@ -318,7 +318,7 @@ size_t outer_part_doubles(int chunks, int m);
 int outer_dot_counters(int chunks);
 void basis_store(const double2* src, double2* dst, size_t n, int df, cudaStream_t st);
 template <typename C>
-void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t st);
+void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, size_t vs, cudaStream_t st);
 template <typename C>
 void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start, cudaStream_t st);
 template <typename C>

@@ -381,12 +381,16 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
 // grid nor on which other problems share the launch.  A unit sweeps its points once
 // per block of DOT_VB vectors with the DOT_VB complex sums in registers, so the FP64
 // pipe runs 4 DFMA per point and vector; the warp combines its 2 DOT_VB partial sums
-// (padded to 32) with a transposed butterfly (about one add per value instead of five), the CTA
+// (padded to 16 or 32) with a transposed butterfly (about one add per value instead of five), the CTA
 // combines warps in fixed order.  Units are combined in two levels, so that no
 // single SM adds up every unit: the last unit of each group of DOT_GROUP units sums
 // the group, the last group sums the groups.
 constexpr int DOT_THREADS = 256;
-constexpr int DOT_VB = 10;     // vectors per register block (w is re-read once per block)
+// Vectors per register block (w is re-read once per block): ten where the basis streams
+// from HBM (a tenth fewer w reads than eight, 2% off the 255^3 multi-dot), eight on
+// smaller problems (fewer registers, no spills; 2-4% faster on the 1023^2 solves).
+constexpr int DOT_VB_MAX = 10;
+constexpr size_t DOT_VB10_MIN_POINTS = (size_t)1 << 22;
 constexpr int DOT_GROUP = 16;  // units per first-level group
 
 HELM_HD inline int dot_groups(int chunks) { return (chunks + DOT_GROUP - 1) / DOT_GROUP; }
@@ -396,25 +400,28 @@ __device__ __forceinline__ size_t unit_begin(size_t n, int u, int chunks) {
   return (n * (size_t)u) / (size_t)chunks;
 }
 
-// Sum 32 per-lane values over the warp; lane L returns the total of value L (fixed
-// order: butterflies at offsets 16, 8, 4, 2, 1, halving the values kept, so about one
-// shuffle and one add per value instead of five).
-__device__ __forceinline__ double warp_transpose_sum32(double (&v)[32], int lane) {
+// Sum NS (16 or 32) per-lane values over the warp; lane L returns the total of value
+// L (NS = 32) or L >> 1 (NS = 16) (fixed order: butterflies at offsets 16, 8, 4, ...,
+// halving the values kept, so about one shuffle and one add per value instead of five).
+template <int NS>
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[NS], int lane) {
+  int o = 16;
 #pragma unroll
-  for (int c = 16; c >= 1; c >>= 1) {
-    const bool hi = lane & c;
+  for (int c = NS / 2; c >= 1; c >>= 1, o >>= 1) {
+    const bool hi = lane & o;
 #pragma unroll
     for (int k = 0; k < c; ++k) {
       const double send = hi ? v[k] : v[k + c];
       const double keep = hi ? v[k + c] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, c);
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  return v[0];
+  return NS == 32 ? v[0] : v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 // One thread's sums over its points of the DOT_VB vectors vb .. vb + nv - 1: acc[2 t]
 // and acc[2 t + 1] the real and imaginary parts of <v_{vb+t}, w>.
+template <int DOT_VB>
 __device__ __forceinline__ void dots_block_f64(const double2* V, const double2* W, size_t npts, int vb, int nv,
                                                size_t beg, size_t end, double (&acc)[2 * DOT_VB]) {
   const double2* vbase = V + (size_t)vb * npts;
@@ -437,6 +444,7 @@ __device__ __forceinline__ void dots_block_f64(const double2* V, const double2* 
 }
 // The same sums with the basis and w in double-float (FP32 pipe), widened to binary64
 // at the end: conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr), four multiply-adds.
+template <int DOT_VB>
 __device__ __forceinline__ void dots_block_df(const double2* V, const double2* W, size_t npts, int vb, int nv,
                                               size_t beg, size_t end, double (&acc)[2 * DOT_VB]) {
   const float4* vbase = reinterpret_cast<const float4*>(V) + (size_t)vb * npts;
@@ -466,7 +474,7 @@ __device__ __forceinline__ void dots_block_df(const double2* V, const double2* W
   for (int k = 0; k < 2 * DOT_VB; ++k) acc[k] = df_value(s[k], c[k]);
 }
 
-template <typename C>
+template <typename C, int DOT_VB>
 __global__ void __launch_bounds__(DOT_THREADS, 2)
 k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
   extern __shared__ double sred[];  // [warp][2 (m + 1)] per-warp sums of the unit
@@ -490,13 +498,15 @@ k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
     for (int vb = 0; vb <= j; vb += DOT_VB) {
       const int nv = min(DOT_VB, j + 1 - vb);
       double acc[2 * DOT_VB];
-      if (df) dots_block_df(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
-      else dots_block_f64(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
-      double vals[32];
+      if (df) dots_block_df<DOT_VB>(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
+      else dots_block_f64<DOT_VB>(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
+      constexpr int NS = 2 * DOT_VB <= 16 ? 16 : 32;
+      double vals[NS];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) vals[k] = k < 2 * DOT_VB ? acc[k < 2 * DOT_VB ? k : 0] : 0.0;
-      const double r = warp_transpose_sum32(vals, lane);
-      if (lane < 2 * nv) wsum[2 * vb + lane] = r;
+      for (int k = 0; k < NS; ++k) vals[k] = k < 2 * DOT_VB ? acc[k < 2 * DOT_VB ? k : 0] : 0.0;
+      const double r = warp_transpose_sum<NS>(vals, lane);
+      const int vi = NS == 32 ? lane : lane >> 1;
+      if ((NS == 32 || (lane & 1) == 0) && vi < 2 * nv) wsum[2 * vb + vi] = r;
     }
     __syncthreads();
     for (int k = tid; k < 2 * (j + 1); k += DOT_THREADS) {
@@ -809,6 +819,67 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
   }
 }
 
+// The first basis vector of a cycle, v_0 = r / beta (w holds the true residual r): the
+// cycle-start case of k_vnew in a kernel of its own, so that its double-float form adds
+// no registers to the per-iteration pass.  With a double-float basis and a complex64
+// preconditioner r is split on the integer pipes and scaled by 1/beta in double-float
+// (no FP64 instruction per point); otherwise in binary64.  Writes the V-cycle input b0
+// and starts level 0's first sweep from its norm.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_vstart(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
+  __shared__ double sm[64];
+  const int tid = threadIdx.x;
+  for (int g = blockIdx.x; g < nprob * chunks; g += gridDim.x) {
+    const int prob = g / chunks, unit = g - prob * chunks;
+    const OuterDev<C>& O = ods[prob];
+    OuterState* st = O.st;
+    if (st->done || !st->fresh) continue;  // uniform
+    __syncthreads();  // the previous unit's block reduction is done
+    const bool df = st->df;
+    const double inv = 1.0 / st->beta;
+    double2* vout = O.V;
+    typename CT<C>::R accb = 0;
+    const size_t end = unit_begin(O.vs, unit + 1, chunks);
+    if (df && sizeof(C) == 8) {
+      const float2 sinv = df_split(inv);
+      for (size_t idx = unit_begin(O.vs, unit, chunks) + tid; idx < end; idx += blockDim.x) {
+        const double2 r = __ldcg(O.w + idx);
+        const float2 rr = df_split(r.x), ri = df_split(r.y);
+        const float pr = __fmul_rn(rr.x, sinv.x), pi = __fmul_rn(ri.x, sinv.x);
+        const float er = fmaf(rr.x, sinv.y, fmaf(rr.y, sinv.x, fmaf(rr.x, sinv.x, -pr)));
+        const float ei = fmaf(ri.x, sinv.y, fmaf(ri.y, sinv.x, fmaf(ri.x, sinv.x, -pi)));
+        float ur, lr, ui, li;
+        df_two_sum(pr, er, ur, lr);
+        df_two_sum(pi, ei, ui, li);
+        reinterpret_cast<float4*>(vout)[idx] = make_float4(ur, lr, ui, li);
+        const C c = CT<C>::make((typename CT<C>::R)__fadd_rn(ur, lr), (typename CT<C>::R)__fadd_rn(ui, li));
+        O.b0[idx] = c;
+        accb += cabs2(c);
+      }
+    } else {
+      for (size_t idx = unit_begin(O.vs, unit, chunks) + tid; idx < end; idx += blockDim.x) {
+        const double2 r = __ldcg(O.w + idx);
+        const double2 wv = make_double2(r.x * inv, r.y * inv);
+        if (df) reinterpret_cast<float4*>(vout)[idx] = df_split(wv);
+        else vout[idx] = wv;
+        const C c = from_d<C>(wv);
+        O.b0[idx] = c;
+        accb += cabs2(c);
+      }
+    }
+    double red[1] = {(double)accb}, tot[1];
+    if (grid_sum_last<1>(red, O.part, unit, chunks, &st->counter, sm, tot)) {
+      if (tid == 0) {
+        sweep_begin(O.sc0, (typename CT<C>::R)tot[0], O.s);
+        O.vscale[0] = 1.0;
+        st->fresh = 0;
+        st->j = 0;
+      }
+    }
+  }
+}
+
 // y = R^{-1} g over the current cycle's columns (one warp per problem).
 template <typename C>
 __global__ void k_backsolve(const OuterDev<C>* __restrict__ ods) {
@@ -925,16 +996,32 @@ static int resident_grid(K kernel, int threads, size_t smem) {
   return last;
 }
 
-template <typename C>
-void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t s) {
+template <typename C, int VB>
+static void launch_dots(const OuterDev<C>* od, int nprob, int chunks, int m, cudaStream_t s) {
   const size_t smem = (size_t)(DOT_THREADS / 32) * 2 * (m + 1) * sizeof(double);
-  thread_local size_t configured = 0;  // per host thread; setting the attribute again is harmless
+  thread_local size_t configured = 0;  // per host thread and block size; setting it again is harmless
   if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(k_dots<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_dots<C, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = smem;
   }
-  const int resident = resident_grid(k_dots<C>, DOT_THREADS, smem);
-  k_dots<C><<<std::min(nprob * chunks, resident), DOT_THREADS, smem, s>>>(od, nprob, chunks);
+  thread_local size_t res_smem = 0;
+  thread_local int resident = 0;
+  if (resident == 0 || res_smem != smem) {
+    int dev = 0, sms = 1, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dots<C, VB>, DOT_THREADS, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    resident = per_sm * std::max(sms, 1);
+    res_smem = smem;
+  }
+  k_dots<C, VB><<<std::min(nprob * chunks, resident), DOT_THREADS, smem, s>>>(od, nprob, chunks);
+}
+template <typename C>
+void outer_dots(const OuterDev<C>* od, int nprob, int chunks, int m, size_t vs, cudaStream_t s) {
+  if (vs >= DOT_VB10_MIN_POINTS) launch_dots<C, 10>(od, nprob, chunks, m, s);
+  else launch_dots<C, 8>(od, nprob, chunks, m, s);
 }
 template <typename C>
 void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start, cudaStream_t s) {
@@ -959,9 +1046,15 @@ void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start,
       configured = need;
     }
   }
+  if (start) {
+    thread_local int vres = 0;
+    if (vres == 0) vres = resident_grid(k_vstart<C>, 256, 0);
+    k_vstart<C><<<std::min(nprob * chunks, vres), 256, 0, s>>>(od, nprob, chunks);
+    return;
+  }
   const size_t smem = std::max<size_t>(need, pad);
   const int resident = resident_grid(k_vnew<C>, 256, smem);
-  k_vnew<C><<<std::min(nprob * chunks, resident), 256, smem, s>>>(od, nprob, chunks, start ? 1 : 0);
+  k_vnew<C><<<std::min(nprob * chunks, resident), 256, smem, s>>>(od, nprob, chunks, 0);
 }
 template <typename C>
 void outer_backsolve(const OuterDev<C>* od, int nprob, cudaStream_t s) {
@@ -1012,7 +1105,7 @@ void gather_states(OuterState* const* src, OuterState* dst, int count, cudaStrea
 #define HELM_OUTER_INST(C)                                                                              \
   template void outer_residual<C>(int, const OuterDev<C>*, int, int, TileCfg, cudaStream_t);           \
   template void outer_apply_h<C>(int, const OuterDev<C>*, int, int, TileCfg, cudaStream_t);            \
-  template void outer_dots<C>(const OuterDev<C>*, int, int, int, cudaStream_t);                        \
+  template void outer_dots<C>(const OuterDev<C>*, int, int, int, size_t, cudaStream_t);                \
   template void outer_vnew<C>(const OuterDev<C>*, int, int, int, bool, cudaStream_t);                  \
   template void outer_backsolve<C>(const OuterDev<C>*, int, cudaStream_t);                             \
   template void outer_solution<C>(const OuterDev<C>*, int, int, int, cudaStream_t);
