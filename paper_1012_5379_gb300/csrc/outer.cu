@@ -674,20 +674,25 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
     const int j = start ? -1 : st->j;
     const bool df = st->df;
     float4* shf = reinterpret_cast<float4*>(sh + (st->m + 1));  // the same column as double-floats
-    __syncthreads();  // the previous unit's readers of sh are done
+    __shared__ double s_scale[2];
+    __syncthreads();  // the previous unit's readers of sh and s_scale are done
     for (int i = tid; i <= j; i += blockDim.x) {
       const double sc = O.vscale[i];
       sh[i] = make_double2(O.hcol[i].x * sc, O.hcol[i].y * sc);
       shf[i] = df_split(sh[i]);
     }
-    __syncthreads();
-    const double inv = start ? 1.0 / st->beta : 1.0;
     // The next V-cycle's input is u / ||w|| (start: r / beta): the preconditioned
     // operator maps it back to O(1) norms, so its magnitude does not drift over a
     // cycle (an unscaled u shrinks geometrically and would underflow complex64).
     // FGMRES is exact for any scaling of z_j: w = H z_j and the Hessenberg column
-    // inherit it, and x = Z y cancels it.
-    const double bsc = start ? 1.0 : (st->wnorm2 > 0.0 ? 1.0 / sqrt(st->wnorm2) : 1.0);
+    // inherit it, and x = Z y cancels it.  One thread forms the two scales (an FP64
+    // square root and divisions are long sequences on this part's FP64 pipe).
+    if (tid == 0) {
+      s_scale[0] = start ? 1.0 / st->beta : 1.0;
+      s_scale[1] = start ? 1.0 : (st->wnorm2 > 0.0 ? 1.0 / sqrt(st->wnorm2) : 1.0);
+    }
+    __syncthreads();
+    const double inv = s_scale[0], bsc = s_scale[1];
     const int jn = j + 1;
     double2* vout = O.V + (size_t)jn * O.vs;
     double accu = 0.0;
@@ -835,9 +840,12 @@ k_vstart(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
     const OuterDev<C>& O = ods[prob];
     OuterState* st = O.st;
     if (st->done || !st->fresh) continue;  // uniform
-    __syncthreads();  // the previous unit's block reduction is done
+    __shared__ double s_inv;
+    __syncthreads();  // the previous unit's block reduction and s_inv readers are done
+    if (tid == 0) s_inv = 1.0 / st->beta;  // one thread: a long FP64 sequence on this part
+    __syncthreads();
     const bool df = st->df;
-    const double inv = 1.0 / st->beta;
+    const double inv = s_inv;
     double2* vout = O.V;
     typename CT<C>::R accb = 0;
     const size_t end = unit_begin(O.vs, unit + 1, chunks);
