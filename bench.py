@@ -66,15 +66,28 @@ def workload_config():
                   "so no step reuses the previous step's data from the 126 MB L2"}
 
 
+# Arm cores name themselves by implementer and part number in /proc/cpuinfo
+ARM_PARTS = {("0x41", "0xd4f"): "Arm Neoverse V2", ("0x41", "0xd40"): "Arm Neoverse V1",
+             ("0x41", "0xd0c"): "Arm Neoverse N1", ("0x41", "0xd49"): "Arm Neoverse N2"}
+
+
 def host_info():
     cpu = platform.processor() or platform.machine()
+    impl = part = None
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu model")):
+            low = line.lower()
+            if low.startswith(("model name", "cpu model")):
                 cpu = line.split(":", 1)[1].strip()
                 break
+            if low.startswith("cpu implementer") and impl is None:
+                impl = line.split(":", 1)[1].strip().lower()
+            if low.startswith("cpu part") and part is None:
+                part = line.split(":", 1)[1].strip().lower()
     except OSError:
         pass
+    if impl and part:
+        cpu = ARM_PARTS.get((impl, part), f"Arm implementer {impl} part {part}")
     return {"nproc": os.cpu_count(), "cpu": cpu, "machine": platform.machine()}
 
 
