@@ -127,6 +127,17 @@ def test_auto_basis_takes_the_f64_count_on_gaussian_nu7(helm, k, nint):
     assert infos["auto"].iters == infos["f64"].iters, (infos["auto"].iters, infos["f64"].iters)
 
 
+def test_df_basis_with_complex128_preconditioner(helm):
+    """The double-float basis under the complex128 V-cycle (z_j in binary64: H z_j is
+    formed in binary64 and split; the V-cycle input is formed from the double-float
+    vector in binary64): the binary64 basis's count on a 511^2 solve."""
+    n, tb = 511, 0.3
+    b = I.random_source(2, n, 1011)
+    its = solve_iters(helm, lambda basis: helm.Handle(2, n, tb, k=0.156 * (n + 1), precision="c128", maxit=300,
+                                                       basis=basis), b, 1e-6)
+    assert its["df"] == its["f64"], its
+
+
 def test_df_basis_takes_the_f64_count_on_cube_127(helm):
     w = I.cube_3d(127)
     phi = torch.from_numpy(w.phi).cuda()
