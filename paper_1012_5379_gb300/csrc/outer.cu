@@ -389,7 +389,6 @@ constexpr int DOT_THREADS = 256;
 // Vectors per register block (w is re-read once per block): ten where the basis streams
 // from HBM (a tenth fewer w reads than eight, 2% off the 255^3 multi-dot), eight on
 // smaller problems (fewer registers, no spills; 2-4% faster on the 1023^2 solves).
-constexpr int DOT_VB_MAX = 10;
 constexpr size_t DOT_VB10_MIN_POINTS = (size_t)1 << 22;
 constexpr int DOT_GROUP = 16;  // units per first-level group
 
@@ -655,14 +654,13 @@ HELM_HD constexpr size_t vnew_smem_bytes(int m) {
   return 2 * (size_t)(m + 1) * 16 + (size_t)(m + 1) * 16 + (size_t)m * 16 + (size_t)m * 8;
 }
 
-// start = 1: v_0 = w / beta (w holds the true residual).
-// start = 0: u = w - sum_{i<=j} h_i v_i stored as V[j+1] with ||u|| reduced here;
-// the last block sets h_{j+1,j} = ||u||, vscale[j+1] = 1/||u||, performs the Givens
-// update and decides whether the cycle ends.  Both write the next V-cycle input b0
-// (precision C) and start level 0's first sweep from its norm.
+// u = w - sum_{i<=j} h_i v_i stored as V[j+1] with ||u|| reduced here; the last block
+// sets h_{j+1,j} = ||u||, vscale[j+1] = 1/||u||, performs the Givens update and decides
+// whether the cycle ends.  Writes the next V-cycle input b0 (precision C) and starts
+// level 0's first sweep from its norm.  (A cycle's first vector: k_vstart.)
 template <typename C>
 __global__ void __launch_bounds__(256, 4)
-k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
+k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
   extern __shared__ double2 sh[];  // m+1
   __shared__ double sm[64];
   const int tid = threadIdx.x;
@@ -670,35 +668,32 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
     const int prob = g / chunks, unit = g - prob * chunks;
     const OuterDev<C>& O = ods[prob];
     OuterState* st = O.st;
-    if (st->done || (!start && st->cycle_end) || (start && !st->fresh)) continue;  // uniform
-    const int j = start ? -1 : st->j;
+    if (st->done || st->cycle_end) continue;  // uniform
+    const int j = st->j;
     const bool df = st->df;
     float4* shf = reinterpret_cast<float4*>(sh + (st->m + 1));  // the same column as double-floats
-    __shared__ double s_scale[2];
+    __shared__ double s_scale[1];
     __syncthreads();  // the previous unit's readers of sh and s_scale are done
     for (int i = tid; i <= j; i += blockDim.x) {
       const double sc = O.vscale[i];
       sh[i] = make_double2(O.hcol[i].x * sc, O.hcol[i].y * sc);
       shf[i] = df_split(sh[i]);
     }
-    // The next V-cycle's input is u / ||w|| (start: r / beta): the preconditioned
-    // operator maps it back to O(1) norms, so its magnitude does not drift over a
-    // cycle (an unscaled u shrinks geometrically and would underflow complex64).
-    // FGMRES is exact for any scaling of z_j: w = H z_j and the Hessenberg column
-    // inherit it, and x = Z y cancels it.  One thread forms the two scales (an FP64
-    // square root and divisions are long sequences on this part's FP64 pipe).
-    if (tid == 0) {
-      s_scale[0] = start ? 1.0 / st->beta : 1.0;
-      s_scale[1] = start ? 1.0 : (st->wnorm2 > 0.0 ? 1.0 / sqrt(st->wnorm2) : 1.0);
-    }
+    // The next V-cycle's input is u / ||w||: the preconditioned operator maps it back to
+    // O(1) norms, so its magnitude does not drift over a cycle (an unscaled u shrinks
+    // geometrically and would underflow complex64).  FGMRES is exact for any scaling of
+    // z_j: w = H z_j and the Hessenberg column inherit it, and x = Z y cancels it.  One
+    // thread forms the scale (an FP64 square root and division are long sequences on
+    // this part's FP64 pipe).
+    if (tid == 0) s_scale[0] = st->wnorm2 > 0.0 ? 1.0 / sqrt(st->wnorm2) : 1.0;
     __syncthreads();
-    const double inv = s_scale[0], bsc = s_scale[1];
+    const double bsc = s_scale[0];
     const int jn = j + 1;
     double2* vout = O.V + (size_t)jn * O.vs;
     double accu = 0.0;
     typename CT<C>::R accb = 0;
     const size_t end = unit_begin(O.vs, unit + 1, chunks);
-    if (df && !start) {
+    if (df) {
       // u = w - sum h_i v_i in double-float: four multiply-adds per vector on the FP32
       // pipe, eight vectors' loads in flight per step (the pass is bound by HBM: the
       // loads in flight per SM must cover its latency)
@@ -775,10 +770,8 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
         wb = cfms(sh[i + 1], v1, wb);
       }
       if (i <= j) wa = cfms(sh[i], __ldcs(vp + (size_t)i * O.vs), wa);
-      double2 wv = cadd(wa, wb);
-      wv = make_double2(wv.x * inv, wv.y * inv);
-      if (df) reinterpret_cast<float4*>(vout)[idx] = df_split(wv);  // v_0 of a double-float basis
-      else vout[idx] = wv;
+      const double2 wv = cadd(wa, wb);
+      vout[idx] = wv;
       accu += dabs2(wv);
       C c = from_d<C>(make_double2(wv.x * bsc, wv.y * bsc));
       O.b0[idx] = c;
@@ -790,7 +783,7 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
       double2* hc = sh + 2 * (mm + 1);
       double2* sn_prev = hc + (mm + 1);
       double* cs = reinterpret_cast<double*>(sn_prev + mm);
-      if (!start) {
+      {
         const double2* Hc = O.Hm + (size_t)j * (mm + 1);
         for (int i = tid; i <= j; i += blockDim.x) hc[i] = __ldcg(Hc + i);
         for (int i = tid; i < j; i += blockDim.x) {
@@ -800,25 +793,19 @@ k_vnew(const OuterDev<C>* __restrict__ ods, int nprob, int chunks, int start) {
         __syncthreads();
       }
       __shared__ double2 t_last;
-      if (!start && tid < 32) givens_step_warp(O, st, j, tid == 0 ? sqrt(tot[0]) : 0.0, hc, cs, sn_prev, &t_last);
+      if (tid < 32) givens_step_warp(O, st, j, tid == 0 ? sqrt(tot[0]) : 0.0, hc, cs, sn_prev, &t_last);
       if (tid == 0) {
         sweep_begin(O.sc0, (typename CT<C>::R)tot[1], O.s);
-        if (start) {
-          O.vscale[0] = 1.0;
-          st->fresh = 0;
-          st->j = 0;
-        } else {
-          const double hn = sqrt(tot[0]);
-          O.vscale[jn] = hn > 0.0 ? 1.0 / hn : 0.0;
-          st->iters += 1;
-          st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
-          // lucky breakdown: the new direction vanishes against H z_j (below the
-          // rounding level of the basis arithmetic: about 2^-46 j relative in double-float)
-          const bool breakdown = !(hn > (df ? 1e-12 : 1e-14) * sqrt(st->wnorm2));
-          if (!isfinite(st->rel_est)) { st->done = 3; st->status = -4; st->cycle_end = 1; }
-          else if (st->rel_est <= st->tol || st->iters >= st->maxit || j + 1 >= st->m || breakdown) st->cycle_end = 1;
-          else st->j = jn;
-        }
+        const double hn = sqrt(tot[0]);
+        O.vscale[jn] = hn > 0.0 ? 1.0 / hn : 0.0;
+        st->iters += 1;
+        st->rel_est = st->bnorm > 0.0 ? sqrt(dabs2(O.g[j + 1])) / st->bnorm : 0.0;
+        // lucky breakdown: the new direction vanishes against H z_j (below the rounding
+        // level of the basis arithmetic: about 2^-46 j relative in double-float)
+        const bool breakdown = !(hn > (df ? 1e-12 : 1e-14) * sqrt(st->wnorm2));
+        if (!isfinite(st->rel_est)) { st->done = 3; st->status = -4; st->cycle_end = 1; }
+        else if (st->rel_est <= st->tol || st->iters >= st->maxit || j + 1 >= st->m || breakdown) st->cycle_end = 1;
+        else st->j = jn;
       }
     }
   }
@@ -1062,7 +1049,7 @@ void outer_vnew(const OuterDev<C>* od, int nprob, int chunks, int m, bool start,
   }
   const size_t smem = std::max<size_t>(need, pad);
   const int resident = resident_grid(k_vnew<C>, 256, smem);
-  k_vnew<C><<<std::min(nprob * chunks, resident), 256, smem, s>>>(od, nprob, chunks, 0);
+  k_vnew<C><<<std::min(nprob * chunks, resident), 256, smem, s>>>(od, nprob, chunks);
 }
 template <typename C>
 void outer_backsolve(const OuterDev<C>* od, int nprob, cudaStream_t s) {
