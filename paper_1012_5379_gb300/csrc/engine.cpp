@@ -1043,7 +1043,7 @@ int multidot(int basis, const double2* V, int nvec, size_t npts, const double2* 
 }
 
 // ------------------------------------------------------------------ FGMRES driver
-// Outer FP64 kernels: bytes and flops per point of each pass (j+1 basis vectors).
+// Outer kernels: bytes and flops per point of each pass (j+1 basis vectors).
 template <typename C>
 static double sub_points(const typename Group<C>::Sub& o, int dim) {
   const double P = o.n + 1;
