@@ -2,7 +2,8 @@
  * helm.h -- C ABI of the GB300 (sm_103a) solver for the Helmholtz equation with
  * exterior-complex-scaled (ECS) absorbing layers, preconditioned by the complex
  * stretched grid (CSG) operator inverted with one GMRES(s)-smoothed multigrid
- * V-cycle, inside an outer FP64 flexible GMRES.
+ * V-cycle, inside an outer flexible GMRES (binary64 least squares, solution and true
+ * residual; the Krylov basis in binary64 or double-float, helm_opts.outer_basis).
  *
  * Method: B. Reps, W. Vanroose, H. bin Zubair, "GMRES-based multigrid for the complex
  * scaled preconditioner for the indefinite Helmholtz equation", arXiv:1012.5379.
