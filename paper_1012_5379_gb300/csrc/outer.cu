@@ -377,8 +377,9 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
 
 // ------------------------------------------------------------------ multi-dot
 // h_i = <v_i, w>, i = 0..j.  The points of a problem are split into `chunks` fixed
-// units (contiguous ranges of equal size, +-1); persistent CTAs take units in turn, so the partial sums, and hence the result, depend neither on the
-// grid nor on which other problems share the launch.  A unit sweeps its points once
+// units (contiguous ranges of equal size, each starting on a multiple of 32 points);
+// persistent CTAs take units in turn, so the partial sums, and hence the result, depend
+// neither on the grid nor on which other problems share the launch.  A unit sweeps its points once
 // per block of DOT_VB vectors with the DOT_VB complex sums in registers, so the FP64
 // pipe runs 4 DFMA per point and vector; the warp combines its 2 DOT_VB partial sums
 // (padded to 16 or 32) with a transposed butterfly (about one add per value instead of five), the CTA
@@ -394,9 +395,11 @@ constexpr int DOT_GROUP = 16;  // units per first-level group
 
 HELM_HD inline int dot_groups(int chunks) { return (chunks + DOT_GROUP - 1) / DOT_GROUP; }
 
-// First point of unit u of `chunks` equal contiguous units over n points.
+// First point of unit u of `chunks` contiguous units over n points: equal shares, each
+// starting on a multiple of 32 points, so that a warp's 16-byte loads and stores cover
+// whole 128-byte lines (unaligned starts split every warp access over one more line).
 __device__ __forceinline__ size_t unit_begin(size_t n, int u, int chunks) {
-  return (n * (size_t)u) / (size_t)chunks;
+  return u >= chunks ? n : ((n * (size_t)u) / (size_t)chunks) & ~(size_t)31;
 }
 
 // Sum NS (16 or 32) per-lane values over the warp; lane L returns the total of value
