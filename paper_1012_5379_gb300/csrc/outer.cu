@@ -377,10 +377,10 @@ k_hstencil3(const OuterDev<C>* __restrict__ ods, int ntiles, int rows) {
 
 // ------------------------------------------------------------------ multi-dot
 // h_i = <v_i, w>, i = 0..j.  The points of a problem are split into `chunks` fixed
-// units (contiguous ranges of equal size, each starting on a multiple of 32 points);
-// persistent CTAs take units in turn, so the partial sums, and hence the result, depend
-// neither on the grid nor on which other problems share the launch.  A unit sweeps its points once
-// per block of DOT_VB vectors with the DOT_VB complex sums in registers, so the FP64
+// units (contiguous ranges of equal size, dot_unit_begin); persistent CTAs take units
+// in turn, so the partial sums, and hence the result, depend neither on the grid nor on
+// which other problems share the launch.  A unit sweeps its points once per block of
+// DOT_VB vectors with the DOT_VB complex sums in registers, so the FP64
 // pipe runs 4 DFMA per point and vector; the warp combines its 2 DOT_VB partial sums
 // (padded to 16 or 32) with a transposed butterfly (about one add per value instead of five), the CTA
 // combines warps in fixed order.  Units are combined in two levels, so that no
@@ -400,6 +400,15 @@ HELM_HD inline int dot_groups(int chunks) { return (chunks + DOT_GROUP - 1) / DO
 // whole 128-byte lines (unaligned starts split every warp access over one more line).
 __device__ __forceinline__ size_t unit_begin(size_t n, int u, int chunks) {
   return u >= chunks ? n : ((n * (size_t)u) / (size_t)chunks) & ~(size_t)31;
+}
+
+// First point of unit u of the multi-dot: equal shares starting at any point.  On the
+// 255^3 basis (one GPU, ncu, both forms back to back) this ran 3-4% faster than 32-point
+// starts from j = 4 on, although it reads about 6% more from DRAM (lines that straddle
+// two warps' ranges are fetched twice); 32-point starts were faster only for j <= 2.
+// The new-vector pass, which writes as well, gains from 32-point starts (unit_begin).
+__device__ __forceinline__ size_t dot_unit_begin(size_t n, int u, int chunks) {
+  return (n * (size_t)u) / (size_t)chunks;
 }
 
 // Sum NS (16 or 32) per-lane values over the warp; lane L returns the total of value
@@ -490,7 +499,7 @@ k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
     if (st->done || st->cycle_end) continue;  // uniform over the CTA
     const int j = st->j, M1 = st->m + 1;
     const size_t npts = O.vs;
-    const size_t ubeg = unit_begin(npts, unit, chunks), uend = unit_begin(npts, unit + 1, chunks);
+    const size_t ubeg = dot_unit_begin(npts, unit, chunks), uend = dot_unit_begin(npts, unit + 1, chunks);
     double* upart = O.part;                                   // [chunks][M1][2]
     double* gpart = O.part + (size_t)chunks * M1 * 2;         // [ngroups][M1][2]
     unsigned* gcnt = O.gcnt;  // [ngroups], zero between calls (each group's last unit resets its own)
