@@ -434,12 +434,15 @@ __device__ __forceinline__ double warp_transpose_sum(double (&v)[NS], int lane) 
 // and acc[2 t + 1] the real and imaginary parts of <v_{vb+t}, w>.
 template <int DOT_VB>
 __device__ __forceinline__ void dots_block_f64(const double2* V, const double2* W, size_t npts, int vb, int nv,
-                                               size_t beg, size_t end, double (&acc)[2 * DOT_VB]) {
+                                               size_t beg, size_t end, bool rev, double (&acc)[2 * DOT_VB]) {
   const double2* vbase = V + (size_t)vb * npts;
 #pragma unroll
   for (int k = 0; k < 2 * DOT_VB; ++k) acc[k] = 0.0;
+  const int cnt = beg < end ? (int)((end - beg + DOT_THREADS - 1) / DOT_THREADS) : 0;
+  const int dk = rev ? -1 : 1;
 #pragma unroll 2
-  for (size_t idx = beg; idx < end; idx += DOT_THREADS) {
+  for (int q = 0, k = rev ? cnt - 1 : 0; q < cnt; ++q, k += dk) {
+    const size_t idx = beg + (size_t)k * DOT_THREADS;
     const double2 w = __ldcg(W + idx);
 #pragma unroll
     for (int t = 0; t < DOT_VB; ++t) {
@@ -457,13 +460,16 @@ __device__ __forceinline__ void dots_block_f64(const double2* V, const double2* 
 // at the end: conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr), four multiply-adds.
 template <int DOT_VB>
 __device__ __forceinline__ void dots_block_df(const double2* V, const double2* W, size_t npts, int vb, int nv,
-                                              size_t beg, size_t end, double (&acc)[2 * DOT_VB]) {
+                                              size_t beg, size_t end, bool rev, double (&acc)[2 * DOT_VB]) {
   const float4* vbase = reinterpret_cast<const float4*>(V) + (size_t)vb * npts;
   const float4* w4 = reinterpret_cast<const float4*>(W);
   float s[2 * DOT_VB], c[2 * DOT_VB];
 #pragma unroll
   for (int k = 0; k < 2 * DOT_VB; ++k) s[k] = c[k] = 0.0f;
-  for (size_t idx = beg; idx < end; idx += DOT_THREADS) {
+  const int cnt = beg < end ? (int)((end - beg + DOT_THREADS - 1) / DOT_THREADS) : 0;
+  const int dk = rev ? -1 : 1;
+  for (int q = 0, k = rev ? cnt - 1 : 0; q < cnt; ++q, k += dk) {
+    const size_t idx = beg + (size_t)k * DOT_THREADS;
     const float4 w = __ldcg(w4 + idx);
     float4 v[DOT_VB];
 #pragma unroll
@@ -509,8 +515,12 @@ k_dots(const OuterDev<C>* __restrict__ ods, int nprob, int chunks) {
     for (int vb = 0; vb <= j; vb += DOT_VB) {
       const int nv = min(DOT_VB, j + 1 - vb);
       double acc[2 * DOT_VB];
-      if (df) dots_block_df<DOT_VB>(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
-      else dots_block_f64<DOT_VB>(O.V, O.w, npts, vb, nv, ubeg + tid, uend, acc);
+      // where w streams from HBM (ten-vector blocks), odd blocks sweep the unit backwards:
+      // they start on the part of w the previous block read last, the part most likely
+      // still in L2
+      const bool rev = DOT_VB >= 10 && ((vb / DOT_VB) & 1);
+      if (df) dots_block_df<DOT_VB>(O.V, O.w, npts, vb, nv, ubeg + tid, uend, rev, acc);
+      else dots_block_f64<DOT_VB>(O.V, O.w, npts, vb, nv, ubeg + tid, uend, rev, acc);
       constexpr int NS = 2 * DOT_VB <= 16 ? 16 : 32;
       double vals[NS];
 #pragma unroll
