@@ -24,10 +24,14 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
 * ``restrict_fw`` / ``prolong``: pinned (P = 2^d R^T, exactness on linear fields).
 * ``gmres_sweep``: pinned (brute-force Krylov least squares, residual monotonicity).
 * ``coarse_solve``: pinned (independently assembled matrix times solution).
-* ``vcycle``: pinned as a stationary iteration converging to the direct solve and by
-  the paper's contraction bound (soft); the V-cycle output itself, cycle by cycle,
-  has no printed value to compare with: beyond those properties its parity is
-  unpinned.
+* ``vcycle``: pinned as a whole cycle by a dense brute-force restatement that shares
+  only the paper's reading with it (each level's matrix from quadrature nodes and
+  Lagrange weights, transfers as Kronecker products of the 1D full weighting and its
+  doubled transpose, phi sampled at the coincident coarse nodes, every GMRES(s) step
+  by brute-force Krylov least squares; 2D and 3D, constant and sampled phi, several
+  V(nu1, nu2) and s); as a stationary iteration converging to the direct solve and by
+  the paper's contraction bound (soft); and by its exactness on s eigenvectors.  The
+  paper prints no cycle output to compare with.
 * ``fgmres``: pinned (sparse direct solve, manufactured solution, paper Table 2
   iteration counts as a soft band).
 * ``polysmoother`` (the third-degree polynomial smoother of Sec. 4): pinned by the

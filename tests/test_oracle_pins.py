@@ -346,6 +346,79 @@ def test_vcycle_is_exact_on_s_eigenvectors(s):
     assert np.linalg.norm(got - exact) > 1e-6 * np.linalg.norm(exact)
 
 
+def _dense_vcycle(Ms, Rs, Ps, b, nu1, nu2, s, level=0):
+    """The V(nu1, nu2) cycle of Sec. 3.1 restated with dense matrices: every GMRES(s)
+    step by brute force (x + K c, K the monomial Krylov basis of the residual, c by
+    least squares), the coarsest level by a dense solve."""
+    M = Ms[level]
+    if level == len(Ms) - 1:
+        return np.linalg.solve(M, b)
+
+    def step(x):
+        r0 = b - M @ x
+        K = [r0]
+        for _ in range(s - 1):
+            K.append(M @ K[-1])
+        K = np.array(K).T
+        K = K / np.linalg.norm(K, axis=0)
+        return x + K @ np.linalg.lstsq(M @ K, r0, rcond=None)[0]
+
+    x = np.zeros_like(b)
+    for _ in range(nu1):
+        x = step(x)
+    ec = _dense_vcycle(Ms, Rs, Ps, Rs[level] @ (b - M @ x), nu1, nu2, s, level + 1)
+    x = x + Ps[level] @ ec
+    for _ in range(nu2):
+        x = step(x)
+    return x
+
+
+def _full_weighting_1d(n):
+    """(nc x n) rows (1/4, 1/2, 1/4) centred on the fine node under each coarse node."""
+    nc = (n + 1) // 2 - 1
+    R = np.zeros((nc, n))
+    for i in range(nc):
+        R[i, 2 * i:2 * i + 3] = (0.25, 0.5, 0.25)
+    return R
+
+
+@pytest.mark.parametrize("dim,n,hetero,cyc", [(2, 15, False, (1, 1, 3)), (2, 15, True, (1, 1, 3)),
+                                              (2, 15, False, (2, 1, 2)), (2, 15, True, (1, 0, 1)),
+                                              (2, 31, True, (0, 2, 3)), (3, 7, True, (1, 1, 3))])
+def test_vcycle_equals_dense_bruteforce_cycle(dim, n, hetero, cyc):
+    """The whole cycle against a restatement that shares nothing with the oracle but the
+    reading of the paper: each level's matrix assembled from quadrature nodes and Lagrange
+    weights, transfers as Kronecker products of the 1D full weighting and its doubled
+    transpose, phi sampled at the coincident coarse nodes, GMRES(s) by brute force.  A
+    wrong correction sign, a restricted right-hand side instead of the residual, a
+    post-sweep on the wrong system or a dropped level each fail it."""
+    nu1, nu2, s = cyc
+    tb, k = 0.3, 8.0
+    phi = k * k * (1.0 + 0.3 * np.tanh(crand((n,) * dim, 9).real)) if hetero else k * k
+    levels = (O.build_hierarchy(dim, n, tb, TG, WF, phi=phi) if hetero
+              else O.build_hierarchy(dim, n, tb, TG, WF, k=k))
+    Ms, Rs, Ps = [], [], []
+    nl, ph = n, phi
+    while True:
+        Ms.append(assemble(dim, nl, tb, TG, WF, phi=ph).toarray())
+        if nl <= 3:
+            break
+        R1 = _full_weighting_1d(nl)
+        R = R1
+        for _ in range(dim - 1):
+            R = np.kron(R, R1)
+        Rs.append(R)
+        Ps.append(2 ** dim * R.T)
+        if hetero:
+            ph = ph[tuple([slice(1, None, 2)] * dim)]
+        nl = (nl + 1) // 2 - 1
+    assert [lev.n for lev in levels] == [round(M.shape[0] ** (1 / dim)) for M in Ms]
+    b = crand((n,) * dim, 21)
+    want = _dense_vcycle(Ms, Rs, Ps, b.ravel(), nu1, nu2, s)
+    got = O.vcycle(levels, b, nu1, nu2, s).ravel()
+    assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want)
+
+
 def test_zero_rhs_sweep_and_vcycle():
     levels = O.build_hierarchy(2, 15, 0.3, TG, WF, k=5.0)
     z = np.zeros((15, 15), dtype=np.complex128)
