@@ -32,8 +32,10 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
   V(nu1, nu2) and s); as a stationary iteration converging to the direct solve and by
   the paper's contraction bound (soft); and by its exactness on s eigenvectors.  The
   paper prints no cycle output to compare with.
-* ``fgmres``: pinned (sparse direct solve, manufactured solution, paper Table 2
-  iteration counts as a soft band).
+* ``fgmres``: pinned (sparse direct solve, manufactured solution, every residual
+  estimate of a run with a fixed linear preconditioner against the brute-force
+  minimum over the Krylov space, plain and restarted; paper Table 2 iteration counts
+  as a soft band).
 * ``polysmoother`` (the third-degree polynomial smoother of Sec. 4): pinned by the
   paper's Fig. ex1 (which phi maps the spectrum inside the unit circle), the critical
   angle of Fig. critical_parameters and the stability of Fig. hierarchy_spectrum_smoother;

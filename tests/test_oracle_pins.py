@@ -473,6 +473,47 @@ def test_fgmres_matches_sparse_direct_solve():
     assert all(b2 <= a2 * (1 + 1e-12) for a2, b2 in zip(info.history, info.history[1:]))
 
 
+@pytest.mark.parametrize("restart", [0, 3])
+def test_fgmres_residual_history_equals_bruteforce_minimum(restart):
+    """With a fixed linear preconditioner P (a dense solve with M) flexible GMRES is GMRES
+    on H P (Sec. 5 uses FGMRES only because the GMRES-smoothed cycle is not linear): after
+    j iterations of a cycle started at x_c its residual is the minimum of ||b - H (x_c + P y)||
+    over y in the Krylov space K_j(H P, r_c).  Every estimate of the history is checked
+    against that minimum, computed by least squares over an orthonormalised Krylov basis
+    from a sparse matrix assembled without the oracle; restarted cycles start where the
+    previous one stopped."""
+    n, k, tb = 7, 6.0, 0.3
+    levels = O.build_hierarchy(2, n, tb, TG, WF, k=k)
+    H = assemble(2, n, 0.0, phi=k * k).toarray()
+    M = assemble(2, n, tb, phi=k * k).toarray()
+    HP = H @ np.linalg.inv(M)
+    b = crand((n, n), 31)
+    maxit = 9
+
+    def precond(v):
+        return np.linalg.solve(M, v.ravel()).reshape(v.shape)
+
+    _, info = O.fgmres(levels[0].apply_h, precond, b, tol=1e-14, restart=restart, maxit=maxit)
+    assert info.iters == maxit and len(info.history) == maxit
+    bn = np.linalg.norm(b)
+    r = b.ravel().copy()
+    cyc = restart if restart > 0 else maxit
+    want = []
+    for j in range(1, maxit + 1):
+        jj = (j - 1) % cyc + 1          # iterations into the current cycle
+        K = [r]
+        for _ in range(jj - 1):
+            K.append(HP @ K[-1])
+        Q = np.linalg.qr(np.array(K).T)[0]
+        y = np.linalg.lstsq(HP @ Q, r, rcond=None)[0]
+        res = r - HP @ (Q @ y)
+        want.append(np.linalg.norm(res) / bn)
+        if jj == cyc:
+            r = res                     # the next cycle starts from this residual
+    got = np.array(info.history)
+    assert np.all(np.abs(got - np.array(want)) <= 1e-7 * np.array(want) + 1e-13), (got, want)
+
+
 def test_fgmres_restarted_reaches_tolerance():
     n, k = 31, 20.0
     levels = O.build_hierarchy(2, n, 0.3, TG, WF, k=k)
