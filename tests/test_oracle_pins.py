@@ -514,6 +514,21 @@ def test_fgmres_residual_history_equals_bruteforce_minimum(restart):
     assert np.all(np.abs(got - np.array(want)) <= 1e-7 * np.array(want) + 1e-13), (got, want)
 
 
+def test_fgmres_with_the_exact_inverse_stops_after_one_iteration():
+    """With P = H^{-1} the preconditioned operator is the identity: the first Arnoldi
+    step breaks down (w - h v = 0) and x = H^{-1} b after one iteration (reading of the
+    breakdown rule, Sec. 5's FGMRES)."""
+    n, k = 7, 6.0
+    levels = O.build_hierarchy(2, n, 0.3, TG, WF, k=k)
+    H = assemble(2, n, 0.0, phi=k * k).toarray()
+    b = crand((n, n), 41)
+    x, info = O.fgmres(levels[0].apply_h, lambda v: np.linalg.solve(H, v.ravel()).reshape(v.shape), b,
+                       tol=1e-14, maxit=20)
+    assert info.iters == 1
+    xs = np.linalg.solve(H, b.ravel()).reshape(n, n)
+    assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
 def test_fgmres_restarted_reaches_tolerance():
     n, k = 31, 20.0
     levels = O.build_hierarchy(2, n, 0.3, TG, WF, k=k)
