@@ -185,7 +185,10 @@ int helm_solve(helm_handle* h, const double* b, double* x, double tol, helm_info
                void* stream);
 
 /* As helm_solve, but b and x are HOST arrays: b is copied to the device, the solve
- * runs from a zero initial guess, and the solution is copied back into x. */
+ * runs from a zero initial guess, and the solution is copied back into x.  Each call
+ * allocates two device buffers of n^dim complex128 values for the copies and frees them
+ * before it returns (HELM_ENOMEM if they cannot be allocated); page-locked host arrays
+ * make the copies asynchronous. */
 int helm_solve_host(helm_handle* h, const double* b_host, double* x_host, double tol,
                     helm_info* info, void* stream);
 
